@@ -1,0 +1,22 @@
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def pytest_configure(config):
+    config.addinivalue_line("markers", "gpu: needs a CUDA device (B300, sm_103a)")
+
+
+@pytest.fixture(scope="session")
+def cuda_device():
+    """The CUDA device for parity tests.  A GPU test without one is an error, not a skip."""
+    import torch
+
+    if not torch.cuda.is_available():
+        raise RuntimeError("GPU test selected but no CUDA device is visible")
+    return torch.device("cuda:0")

@@ -1,0 +1,288 @@
+"""Checks that pin the FP64 oracle to things other than itself.
+
+Each ``check_*`` returns an error figure; ``test_oracle_pins.py`` asserts the
+thresholds and ``test_oracle_mutants.py`` shows that oracle builds with planted
+mistakes (a dropped term, a flipped sign, a transposed operand, a swapped index)
+fail at least one of them.  Pins used:
+
+* exact rational values of the Appendix A uniform-sphere closed form, averaged
+  over each sample interval (``golden/pulse_worked_example.json``);
+* numerical quadrature of the same continuous pulse at random distances;
+* central finite differences of the pulse in the distance;
+* the point-sample flag against the closed form evaluated at the sample time;
+* voxel indexing and superposition: a few isolated voxels against the exact
+  single-voxel values at distances computed from the documented grid layout;
+* the adjoint identity <A x, y> = <x, A^T y>;
+* invariance of every signal when one rigid motion moves volume and array;
+* central finite differences of L = 1/2 |A(p0; poses) - S|^2 in the twist
+  components and in the element positions;
+* convergence of a voxelised ball to pi/6 times the ball's own closed-form pulse
+  (each voxel sphere fills pi/6 of its cell).
+"""
+from __future__ import annotations
+
+import importlib.util
+import json
+import math
+import os
+from fractions import Fraction as Fr
+
+import numpy as np
+import scipy.integrate
+import scipy.linalg
+import scipy.ndimage
+
+import oracle
+from paper_2604_09643_b300 import synth
+
+_GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def _golden_module():
+    spec = importlib.util.spec_from_file_location(
+        "make_pulse_worked_example", os.path.join(_GOLDEN, "make_pulse_worked_example.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def _scalar_geom(c, fs, a0, t0, n_samples=100000):
+    return synth.make_geom((1, 1, 1), 1.0, 1, 1, n_samples, fs=float(fs), c=float(c),
+                           a0=float(a0), t0=float(t0))
+
+
+def check_closed_form() -> float:
+    """Max |oracle - exact| / max|exact| over the golden worked example."""
+    with open(os.path.join(_GOLDEN, "pulse_worked_example.json")) as fh:
+        data = json.load(fh)
+    worst = 0.0
+    for case in data["cases"]:
+        geom = _scalar_geom(Fr(case["c_mm_per_us"]), Fr(case["fs_mhz"]), Fr(case["a0_mm"]),
+                            Fr(case["t0_us"]))
+        r = float(Fr(case["r_mm"]))
+        exact = {int(n): Fr(v[0]) for n, v in case["samples"].items()}
+        scale = float(max(abs(v) for v in exact.values()))
+        for n, v in exact.items():
+            worst = max(worst, abs(oracle.pulse(geom, r, n) - float(v)) / scale)
+    return worst
+
+
+def _quad_sample(r, n, c, fs, a0, t0):
+    """Average of the continuous closed-form pressure over sample n (quadrature in t)."""
+    def p(t):
+        tau = c * t
+        return (r - tau) / (2 * r) if (r - a0) <= tau <= (r + a0) else 0.0
+    ta, tb = t0 + (n - 0.5) / fs, t0 + (n + 0.5) / fs
+    pts = [x for x in ((r - a0) / c, (r + a0) / c) if ta < x < tb]
+    val, _ = scipy.integrate.quad(p, ta, tb, points=pts or None, epsabs=1e-14, epsrel=1e-12,
+                                  limit=200)
+    return val * fs
+
+
+def check_quadrature(seed=5) -> float:
+    rng = np.random.default_rng(seed)
+    worst = 0.0
+    for _ in range(12):
+        c, fs, a0, t0 = 1.5, 40.0, float(rng.choice([0.05, 0.1, 0.2])), float(rng.uniform(0, 0.5))
+        r = float(rng.uniform(3.0, 20.0))
+        geom = _scalar_geom(c, fs, a0, t0)
+        h = c / fs
+        n0 = int(math.floor((r - a0 - c * t0) / h)) - 2
+        n1 = int(math.ceil((r + a0 - c * t0) / h)) + 2
+        scale = a0 / (2 * r)
+        for n in range(n0, n1 + 1):
+            worst = max(worst, abs(oracle.pulse(geom, r, n) - _quad_sample(r, n, c, fs, a0, t0)) / scale)
+    return worst
+
+
+def check_pulse_dd(seed=6) -> float:
+    """Max relative gap between pulse_dd and a central difference of pulse."""
+    rng = np.random.default_rng(seed)
+    worst = 0.0
+    eps = 1e-7
+    for _ in range(20):
+        a0 = float(rng.choice([0.05, 0.1]))
+        geom = _scalar_geom(1.5, 40.0, a0, 0.0)
+        r = float(rng.uniform(3.0, 15.0))
+        h = 1.5 / 40.0
+        ns = range(int((r - a0) / h) - 1, int((r + a0) / h) + 2)
+        scale = max(abs(oracle.pulse_dd(geom, r, n)) for n in ns) + 1e-300
+        for n in ns:
+            fd = (oracle.pulse(geom, r + eps, n) - oracle.pulse(geom, r - eps, n)) / (2 * eps)
+            worst = max(worst, abs(fd - oracle.pulse_dd(geom, r, n)) / scale)
+    return worst
+
+
+def check_point_sampling() -> float:
+    geom = _scalar_geom(1.5, 40.0, 0.1, 0.0)
+    worst = 0.0
+    for r in (5.0, 6.31, 11.007):
+        for n in range(int((r - 0.2) / 0.0375), int((r + 0.2) / 0.0375) + 1):
+            tau = 1.5 * n / 40.0
+            ref = (r - tau) / (2 * r) if abs(tau - r) <= 0.1 else 0.0
+            worst = max(worst, abs(oracle.pulse(geom, r, n, point_sampling=True) - ref))
+    return worst / (0.1 / 10.0)
+
+
+def small_geom(shape=(5, 6, 7), spacing=0.25, m=2, n_frames=2, n_samples=256, a0=None, seed=0):
+    """Small volume with an m x m array 3 mm above it and slightly tilted frames."""
+    geom = synth.make_geom(shape, spacing, m * m, n_frames, n_samples, a0=a0)
+    rng = np.random.default_rng(seed)
+    elem = synth.planar_array(m, m, 0.7)
+    poses = np.zeros((n_frames, 3, 4))
+    for f in range(n_frames):
+        poses[f, :, :3] = synth.axis_angle_matrix(synth.random_unit(rng), rng.uniform(0, 0.3))
+        poses[f, :, 3] = [rng.uniform(-0.5, 0.5), rng.uniform(-0.5, 0.5),
+                          synth.top_face_z(geom) + 3.0]
+    return geom, elem, poses
+
+
+def check_superposition() -> float:
+    """Isolated voxels vs exact single-voxel values at independently computed distances."""
+    gm = _golden_module()
+    geom, elem, poses = small_geom(shape=(4, 5, 6), spacing=0.3, a0=0.15, n_samples=400)
+    p0 = np.zeros((4, 5, 6), dtype=np.float32)
+    picks = [((0, 0, 0), 1.0), ((3, 4, 5), 0.5), ((1, 3, 2), 0.75), ((2, 0, 5), 0.25)]
+    for (iz, iy, ix), a in picks:
+        p0[iz, iy, ix] = a
+    xw = oracle.element_positions(geom, elem, poses)
+    sig = oracle.forward(geom, p0, xw)
+    c, fs, a0, t0 = Fr(1.5), Fr(40), Fr(geom["a0_mm"]), Fr(0)
+    worst, scale = 0.0, 0.0
+    for f in range(geom["n_frames"]):
+        for j in range(geom["n_elem"]):
+            R, t = poses[f, :, :3], poses[f, :, 3]
+            x = R @ elem[j] + t
+            ref = np.zeros(geom["n_samples"])
+            for (iz, iy, ix), a in picks:
+                r = np.array([geom["ox"] + geom["dx"] * ix, geom["oy"] + geom["dy"] * iy,
+                              geom["oz"] + geom["dz"] * iz])
+                d = Fr(float(np.linalg.norm(x - r)))
+                for n in range(geom["n_samples"]):
+                    v = gm.exact_sample(d, n, c, fs, a0, t0)
+                    if v:
+                        ref[n] += a * float(v)
+            worst = max(worst, float(np.abs(sig[f, j] - ref).max()))
+            scale = max(scale, float(np.abs(ref).max()))
+    return worst / scale
+
+
+def check_adjoint_identity(seed=7) -> float:
+    geom, elem, poses = small_geom(shape=(6, 7, 8), spacing=0.2, m=3, n_frames=2, n_samples=320)
+    rng = np.random.default_rng(seed)
+    xw = oracle.element_positions(geom, elem, poses)
+    x = rng.uniform(0, 1, size=(6, 7, 8)).astype(np.float32)
+    x2 = rng.uniform(0, 1, size=(6, 7, 8)).astype(np.float32)
+    y = oracle.forward(geom, x2, xw) + rng.standard_normal((2, 9, 320))
+    Ax = oracle.forward(geom, x, xw)
+    Aty = oracle.adjoint(geom, y, xw)
+    lhs = math.fsum((Ax * y).ravel())
+    rhs = math.fsum((x.astype(np.float64) * Aty).ravel())
+    return abs(lhs - rhs) / max(abs(lhs), abs(rhs))
+
+
+def check_rigid_invariance(seed=8) -> float:
+    geom, elem, poses = small_geom(shape=(6, 6, 5), spacing=0.2, m=3, n_frames=2, n_samples=320)
+    rng = np.random.default_rng(seed)
+    p0 = rng.uniform(0, 1, size=(5, 6, 6)).astype(np.float32)
+    G = synth.axis_angle_matrix(synth.random_unit(rng), math.radians(rng.uniform(5, 30)))
+    gt = rng.uniform(-5, 5, size=3)
+    vol_pose = np.concatenate([G, gt[:, None]], axis=1)
+    moved = poses.copy()
+    for f in range(len(poses)):
+        moved[f, :, :3] = G @ poses[f, :, :3]
+        moved[f, :, 3] = G @ poses[f, :, 3] + gt
+    s0 = oracle.forward(geom, p0, oracle.element_positions(geom, elem, poses))
+    s1 = oracle.forward(geom, p0, oracle.element_positions(geom, elem, moved), vol_pose=vol_pose)
+    return float(np.linalg.norm(s1 - s0) / np.linalg.norm(s0))
+
+
+def _twist_pose(pose, xi):
+    E = scipy.linalg.expm(np.array([[0, -xi[2], xi[1]], [xi[2], 0, -xi[0]], [-xi[1], xi[0], 0]]))
+    out = np.empty((3, 4))
+    out[:, :3] = E @ pose[:, :3]
+    out[:, 3] = E @ pose[:, 3] + xi[3:]
+    return out
+
+
+def _loss_at(geom, p0, elem, poses, meas, mask=None):
+    xw = np.einsum("fab,jb->fja", poses[:, :, :3], elem) + poses[:, None, :, 3]
+    s = oracle.forward(geom, p0, xw)
+    r = s - meas
+    if mask is not None:
+        r = r * mask[:, :, None]
+    return 0.5 * math.fsum((r * r).ravel())
+
+
+def check_pose_fd(seed=9, eps=1e-6, use_mask=False):
+    """Returns (max rel err rotation block, translation block, element gradient)."""
+    geom, elem, poses = small_geom(shape=(4, 5, 5), spacing=0.25, m=2, n_frames=2, n_samples=256)
+    rng = np.random.default_rng(seed)
+    p0 = rng.uniform(0.2, 1, size=(4, 5, 5)).astype(np.float32)
+    meas = 0.02 * rng.standard_normal((2, 4, 256))
+    mask = np.array([[1, 0, 1, 1], [1, 1, 1, 0]], dtype=np.uint8) if use_mask else None
+    xw = oracle.element_positions(geom, elem, poses)
+    s = oracle.forward(geom, p0, xw)
+    _, g = oracle.loss(geom, s, meas)  # unmasked residual: the mask is applied by pose_grad
+    grad6, G = oracle.pose_grad(geom, p0, g, xw, mask)
+    errs = [0.0, 0.0]
+    for f in range(2):
+        fd = np.zeros(6)
+        for k in range(6):
+            xi = np.zeros(6)
+            xi[k] = eps
+            pp, pm = poses.copy(), poses.copy()
+            pp[f] = _twist_pose(poses[f], xi)
+            pm[f] = _twist_pose(poses[f], -xi)
+            fd[k] = (_loss_at(geom, p0, elem, pp, meas, mask)
+                     - _loss_at(geom, p0, elem, pm, meas, mask)) / (2 * eps)
+        for b, sl in enumerate((slice(0, 3), slice(3, 6))):
+            errs[b] = max(errs[b], float(np.linalg.norm(fd[sl] - grad6[f, sl]) / np.linalg.norm(fd[sl])))
+    # element positions directly: move one element of frame 0 along each axis
+    ge = 0.0
+    for j in range(geom["n_elem"]):
+        fdj = np.zeros(3)
+        for a in range(3):
+            xp, xm = xw.copy(), xw.copy()
+            xp[0, j, a] += eps
+            xm[0, j, a] -= eps
+            lp = 0.5 * np.sum(((oracle.forward(geom, p0, xp) - meas) * (1 if mask is None else mask[:, :, None])) ** 2)
+            lm = 0.5 * np.sum(((oracle.forward(geom, p0, xm) - meas) * (1 if mask is None else mask[:, :, None])) ** 2)
+            fdj[a] = (lp - lm) / (2 * eps)
+        denom = max(np.linalg.norm(fdj), 1e-300)
+        if np.linalg.norm(fdj) > 0 or np.linalg.norm(G[0, j]) > 0:
+            ge = max(ge, float(np.linalg.norm(fdj - G[0, j]) / max(denom, np.linalg.norm(G[0, j]))))
+    return errs[0], errs[1], ge
+
+
+def check_big_ball(spacing=0.1, radius=1.0, dist=10.0):
+    """Returns (ratio of projections, low-passed relative L2) of a voxelised ball
+    against pi/6 times the ball's closed-form pulse (quadrature)."""
+    n = int(round(2 * radius / spacing)) + 1
+    geom = synth.make_geom((n, n, n), spacing, 1, 1, 0, fs=40.0, c=1.5)
+    c, fs = 1.5, 40.0
+    t0 = (dist - radius - 0.5) / c
+    nt = int(math.ceil((2 * radius + 1.0) / (c / fs))) + 1
+    geom["t0_us"], geom["n_samples"] = t0, nt
+    x, y, z = synth.voxel_axes(geom)
+    zz, yy, xx = np.meshgrid(z, y, x, indexing="ij")
+    p0 = ((xx ** 2 + yy ** 2 + zz ** 2) <= radius ** 2).astype(np.float32)
+    xw = np.array([[[0.0, 0.0, dist]]])
+    s = oracle.forward(geom, p0, xw)[0, 0]
+    ball = np.array([_quad_sample(dist, k, c, fs, radius, t0) for k in range(nt)]) * math.pi / 6
+    ratio = float(np.dot(s, ball) / np.dot(ball, ball))
+    lp = lambda v: scipy.ndimage.gaussian_filter1d(v, 3.0)
+    l2 = float(np.linalg.norm(lp(s) - lp(ball)) / np.linalg.norm(lp(ball)))
+    return ratio, l2
+
+
+def check_loss(seed=10) -> float:
+    geom, _, _ = small_geom(n_samples=64)
+    rng = np.random.default_rng(seed)
+    s = rng.standard_normal((2, 4, 64))
+    S = rng.standard_normal((2, 4, 64))
+    mask = (rng.uniform(size=(2, 4)) > 0.3).astype(np.uint8)
+    L, g = oracle.loss(geom, s, S, mask)
+    ref_g = (s - S) * mask[:, :, None]
+    ref_L = 0.5 * math.fsum((ref_g ** 2).ravel())
+    return max(abs(L - ref_L) / ref_L, float(np.abs(g - ref_g).max()))

@@ -1,0 +1,74 @@
+"""Planted mistakes in copies of the oracle must each fail at least one pin (CPU).
+
+Each mutant is a textual edit of ``oracle/pasfm_oracle.c`` compiled into a
+temporary directory; the oracle package is pointed at it for the duration of
+the check and restored afterwards.  The committed oracle is never modified.
+"""
+import os
+import subprocess
+
+import pytest
+
+import oracle
+from tests import oracle_checks as oc
+
+SRC = os.path.join(os.path.dirname(oracle.__file__), "pasfm_oracle.c")
+
+MUTANTS = {
+    "pulse_sign_flipped": ("return (wl * wl - wh * wh) / (4.0 * d * h);",
+                           "return (wh * wh - wl * wl) / (4.0 * d * h);"),
+    "pulse_amplitude_drops_1_over_d": ("return (wl * wl - wh * wh) / (4.0 * d * h);",
+                                       "return (wl * wl - wh * wh) / (4.0 * 10.0 * h);"),
+    "sample_time_off_by_half": ("const double tau = g->c * (g->t0 + (double)n / g->fs);\n  if",
+                                "const double tau = g->c * (g->t0 + ((double)n + 0.5) / g->fs);\n  if"),
+    "derivative_drops_W_over_d": ("return (dl - dh) / (4.0 * d * h) - W / d;",
+                                  "return (dl - dh) / (4.0 * d * h);"),
+    "derivative_sign_flipped": ("return (dl - dh) / (4.0 * d * h) - W / d;",
+                                "return (dh - dl) / (4.0 * d * h) - W / d;"),
+    "rotation_transposed": ("x[a] = P[4 * a] * e[0] + P[4 * a + 1] * e[1] + P[4 * a + 2] * e[2] + P[4 * a + 3];",
+                            "x[a] = P[a] * e[0] + P[4 + a] * e[1] + P[8 + a] * e[2] + P[4 * a + 3];"),
+    "voxel_axes_swapped": ("g->ox + g->dx * ix, g->oy + g->dy * iy, g->oz + g->dz * iz",
+                           "g->ox + g->dx * iz, g->oy + g->dy * iy, g->oz + g->dz * ix"),
+    "cross_product_sign": ("w[0] += x[1] * Gj[2] - x[2] * Gj[1];",
+                           "w[0] += x[2] * Gj[1] - x[1] * Gj[2];"),
+    "adjoint_reads_reversed_samples": ("for (int n = lo; n <= hi; ++n) acc += gs[n] * oracle_pulse(g, d, n);",
+                                       "for (int n = lo; n <= hi; ++n) acc += gs[lo + hi - n] * oracle_pulse(g, d, n);"),
+    "sample_range_too_narrow": ("double a = floor((d - g->a0 - tau0) / h - 0.5) - 1.0;",
+                                "double a = floor((d - g->a0 - tau0) / h - 0.5) + 2.0;"),
+    "pose_grad_ignores_mask": ("if (!mask || mask[fj]) {", "if (1) {"),
+}
+
+
+def failing_pins():
+    out = []
+    if oc.check_closed_form() > 1e-12:
+        out.append("closed_form")
+    if oc.check_superposition() > 1e-12:
+        out.append("superposition")
+    if oc.check_adjoint_identity() > 1e-12:
+        out.append("adjoint")
+    if oc.check_rigid_invariance() > 1e-12:
+        out.append("rigid")
+    if oc.check_pulse_dd() > 1e-6:
+        out.append("pulse_dd")
+    if max(oc.check_pose_fd()) > 1e-6:
+        out.append("pose_fd")
+    if max(oc.check_pose_fd(use_mask=True, seed=11)) > 1e-6:
+        out.append("pose_fd_masked")
+    return out
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_mutant_is_caught(name, tmp_path, monkeypatch):
+    old, new = MUTANTS[name]
+    src = open(SRC).read()
+    assert src.count(old) >= 1, f"mutation anchor for {name} not found"
+    mutated = src.replace(old, new, 1)
+    csrc = tmp_path / "mut.c"
+    csrc.write_text(mutated)
+    so = tmp_path / "libmut.so"
+    subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11",
+                           str(csrc), "-o", str(so), "-lm"])
+    monkeypatch.setattr(oracle, "_lib", oracle.load(str(so)))
+    fails = failing_pins()
+    assert fails, f"mutant {name} passed every pin"

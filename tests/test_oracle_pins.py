@@ -1,0 +1,142 @@
+"""The FP64 oracle against closed forms, identities and finite differences (CPU)."""
+import math
+
+import numpy as np
+import scipy.linalg
+
+from oracle import adam, rigid
+from tests import oracle_checks as oc
+
+
+def test_pulse_exact_closed_form():
+    assert oc.check_closed_form() < 1e-12
+
+
+def test_pulse_quadrature():
+    assert oc.check_quadrature() < 1e-9
+
+
+def test_pulse_derivative_fd():
+    assert oc.check_pulse_dd() < 1e-6
+
+
+def test_point_sampling_flag():
+    assert oc.check_point_sampling() < 1e-13
+
+
+def test_voxel_layout_and_superposition():
+    assert oc.check_superposition() < 1e-12
+
+
+def test_adjoint_identity():
+    assert oc.check_adjoint_identity() < 1e-12
+
+
+def test_rigid_invariance():
+    assert oc.check_rigid_invariance() < 1e-12
+
+
+def test_pose_gradient_fd():
+    rot, trans, elem = oc.check_pose_fd()
+    assert rot < 1e-6 and trans < 1e-6 and elem < 1e-6, (rot, trans, elem)
+
+
+def test_pose_gradient_fd_masked():
+    rot, trans, elem = oc.check_pose_fd(use_mask=True, seed=11)
+    assert rot < 1e-6 and trans < 1e-6 and elem < 1e-6, (rot, trans, elem)
+
+
+def test_big_ball_converges_to_pi_over_6():
+    r2, l2_coarse = oc.check_big_ball(spacing=0.2)
+    r1, l2_fine = oc.check_big_ball(spacing=0.1)
+    assert abs(r1 - 1.0) < 0.02, r1
+    assert l2_fine < 0.06, l2_fine
+    assert l2_fine < l2_coarse, (l2_fine, l2_coarse)
+
+
+def test_loss_head():
+    assert oc.check_loss() < 1e-14
+
+
+# ---------------------------------------------------------------- rigid / Adam
+
+def test_so3_exp_matches_expm():
+    rng = np.random.default_rng(0)
+    for _ in range(20):
+        w = rng.normal(size=3) * rng.uniform(1e-9, 3.0)
+        ref = scipy.linalg.expm(rigid.skew(w))
+        assert np.abs(rigid.so3_exp(w) - ref).max() < 1e-13
+
+
+def _horn(P, Q):
+    """Quaternion (Horn 1987) least-squares rotation, independent of the SVD route."""
+    pc, qc = P.mean(0), Q.mean(0)
+    S = (P - pc).T @ (Q - qc)
+    Sxx, Sxy, Sxz, Syx, Syy, Syz, Szx, Szy, Szz = S.ravel()
+    N = np.array([[Sxx + Syy + Szz, Syz - Szy, Szx - Sxz, Sxy - Syx],
+                  [Syz - Szy, Sxx - Syy - Szz, Sxy + Syx, Szx + Sxz],
+                  [Szx - Sxz, Sxy + Syx, -Sxx + Syy - Szz, Syz + Szy],
+                  [Sxy - Syx, Szx + Sxz, Syz + Szy, -Sxx - Syy + Szz]])
+    w, V = np.linalg.eigh(N)
+    q0, qx, qy, qz = V[:, -1]
+    R = np.array([[q0 * q0 + qx * qx - qy * qy - qz * qz, 2 * (qx * qy - q0 * qz), 2 * (qx * qz + q0 * qy)],
+                  [2 * (qy * qx + q0 * qz), q0 * q0 - qx * qx + qy * qy - qz * qz, 2 * (qy * qz - q0 * qx)],
+                  [2 * (qz * qx - q0 * qy), 2 * (qz * qy + q0 * qx), q0 * q0 - qx * qx - qy * qy + qz * qz]])
+    return R, qc - R @ pc
+
+
+def test_kabsch_exact_and_matches_horn():
+    rng = np.random.default_rng(1)
+    P = rng.normal(size=(12, 3)) * 3
+    R = rigid.so3_exp(rng.normal(size=3))
+    t = rng.normal(size=3) * 5
+    Rk, tk = rigid.kabsch(P, P @ R.T + t)
+    assert np.abs(Rk - R).max() < 1e-12 and np.abs(tk - t).max() < 1e-12
+    Q = P @ R.T + t + 0.05 * rng.normal(size=P.shape)
+    Rk, tk = rigid.kabsch(P, Q)
+    Rh, th = _horn(P, Q)
+    assert np.abs(Rk - Rh).max() < 1e-10 and np.abs(tk - th).max() < 1e-10
+
+
+def test_ransac_rejects_outliers():
+    rng = np.random.default_rng(2)
+    tmpl = np.stack(np.meshgrid(np.arange(5), np.arange(5), indexing="ij"), -1).reshape(-1, 2) * 0.6
+    tmpl = np.concatenate([tmpl, np.zeros((25, 1))], axis=1)
+    R = rigid.so3_exp([0.1, -0.2, 0.3])
+    t = np.array([1.0, 2.0, 8.0])
+    obs = tmpl @ R.T + t
+    bad = rng.choice(25, size=6, replace=False)
+    obs[bad] += rng.normal(size=(6, 3)) * 2.0
+    subsets = [rng.choice(25, size=3, replace=False) for _ in range(200)]
+    Rr, tr, mask, k = rigid.ransac_consensus(tmpl, obs, subsets, edge_tol=0.05, inlier_tol=0.1)
+    truth = np.ones(25, dtype=bool)
+    truth[bad] = False
+    assert k >= 0 and np.array_equal(mask, truth)
+    assert np.abs(Rr - R).max() < 1e-12 and np.abs(tr - t).max() < 1e-12
+
+
+def test_adam_first_step_is_signed_lr():
+    rng = np.random.default_rng(3)
+    p = rng.normal(size=100)
+    g = rng.normal(size=100)
+    out, m, v = adam.adam_volume(p, g, np.zeros(100), np.zeros(100), 1, lr=0.01, eps=0.0)
+    assert np.abs(out - (p - 0.01 * np.sign(g))).max() < 1e-15
+    # projected variant clips at zero
+    out2, _, _ = adam.adam_volume(p, g, np.zeros(100), np.zeros(100), 1, lr=0.01, eps=0.0, nonneg=True)
+    assert np.all(out2 >= 0) and np.allclose(out2, np.maximum(out, 0))
+
+
+def test_adam_pose_first_step_moves_by_signed_lr():
+    poses = np.tile(np.eye(3, 4), (3, 1, 1))
+    poses[:, 2, 3] = 10.0
+    g6 = np.array([[1, -2, 3, -4, 5, -6], [0.5, 0.5, -0.5, 1, 1, 1], [1, 1, 1, 1, 1, 1]], float)
+    out, m, v, dxi = adam.adam_poses(poses, g6, np.zeros((3, 6)), np.zeros((3, 6)), 1,
+                                     lr_rot=1e-3, lr_trans=1e-2, eps=0.0,
+                                     fixed=np.array([0, 0, 1], bool))
+    expect = -np.sign(g6) * np.array([1e-3] * 3 + [1e-2] * 3)
+    assert np.abs(dxi - expect).max() < 1e-15
+    assert np.array_equal(out[2], poses[2])
+    E = scipy.linalg.expm(rigid.skew(expect[0, :3]))
+    assert np.abs(out[0][:, :3] - E).max() < 1e-14
+    assert np.abs(out[0][:, 3] - (E @ poses[0, :, 3] + expect[0, 3:])).max() < 1e-13
+    assert math.isclose(np.linalg.det(out[1][:, :3]), 1.0, rel_tol=1e-14)
