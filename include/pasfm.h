@@ -1,0 +1,193 @@
+/*
+ * pasfm.h -- C ABI of the B300 (sm_103a) differentiable acoustic radiation operator
+ * of PA-SFM (tracker-free freehand 3D photoacoustic imaging).
+ *
+ * The operator (paper, Section 2 "Differentiable Acoustic Radiation", Eq. 1, and
+ * Appendix A, Eq. gpu_forward_model with the uniform-spherical-source closed form):
+ * every voxel i of a grid P_c is a uniform sphere of radius a0 and amplitude
+ * p0_i; element j of frame f sits at x_fj = R_f e_j + t_f (the rigid model of
+ * Stage 4).  Seen from x_fj at distance d = |x_fj - r_i| the voxel radiates the
+ * N-shaped pulse p0_i (d - c t) / (2 d) for |c t - d| <= a0.  Sample n of a trace
+ * is that pulse averaged over the sample interval [t_n - 1/(2 fs), t_n + 1/(2 fs)],
+ * t_n = t0 + n / fs, so with h = c / fs, tau_n = c t_n and
+ *     W(d, n) = (w_lo^2 - w_hi^2) / (4 d h),
+ *     w_lo = clamp(tau_n - h/2 - d, -a0, a0),  w_hi = clamp(tau_n + h/2 - d, -a0, a0):
+ *   forward    s[f][j][n] = sum_i p0_i W(d_fji, n)
+ *   adjoint    v_i        = sum_{f,j,n} g[f][j][n] W(d_fji, n)            (exact transpose)
+ *   pose grad  G_fj = sum_i p0_i sum_n g[f][j][n] dW/dd (x_fj - r_i) / d,
+ *              dL/dv_f = sum_j G_fj,  dL/dw_f = sum_j x_fj x G_fj
+ *              for the left twist x -> Exp(w) x + v about the world origin.
+ *
+ * Conventions shared by every call
+ *  - Units: mm, microseconds, MHz.  Voxel (ix, iy, iz) has centre
+ *    (ox + dx ix, oy + dy iy, oz + dz iz); volumes are [nz][ny][nx], x fastest.
+ *  - Signals are [F][E][Nt], samples fastest.  Element templates are double
+ *    [E][3] in the array frame; poses are double [F][3][4] = [R | t], row-major.
+ *  - Every array argument is caller-owned DEVICE memory on the context's device,
+ *    unless stated otherwise.  Outputs are overwritten, never accumulated.
+ *  - Calls are asynchronous on `stream` (a cudaStream_t; NULL = legacy default
+ *    stream) and never synchronise the host, except pasfm_status() and
+ *    pasfm_timing_read().
+ *  - Return value: PASFM_OK or a negative code; pasfm_last_error() gives a
+ *    message for the calling thread.  Argument errors are detected on the host
+ *    before any launch.  Geometry errors that depend on device data (an element
+ *    within a0 of the voxel grid, a device wait that ran out) set the context's
+ *    device status word; read it with pasfm_status().  Outputs of a call that
+ *    set the status word are unspecified but every access stays in bounds.
+ *  - A context owns its workspace and may be used by one host thread and one
+ *    stream at a time; use one context per concurrently running stream.
+ *  - The library allocates device memory only in pasfm_create(), pasfm_reserve()
+ *    and, when the workspace must grow, in the first compute call for a larger
+ *    geometry (call pasfm_reserve() first to keep compute calls allocation-free).
+ */
+#ifndef PASFM_H
+#define PASFM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PASFM_OK 0
+#define PASFM_EINVAL (-1)       /* bad argument: NULL, negative size, non-positive scalar */
+#define PASFM_ENOMEM (-2)       /* workspace allocation failed */
+#define PASFM_ECUDA (-3)        /* a CUDA runtime call failed */
+#define PASFM_ETIMEOUT (-4)     /* a bounded device wait ran out (from pasfm_status) */
+#define PASFM_EDEVICE (-5)      /* device status word set: element inside the grid, etc. */
+#define PASFM_EUNSUPPORTED (-6) /* geometry outside the compiled kernel range */
+
+/* storage types of the volume and signal arrays */
+#define PASFM_F32 0
+#define PASFM_BF16 1
+#define PASFM_F16 2
+
+/* device status word bits (pasfm_status) */
+#define PASFM_STATUS_ELEMENT_INSIDE 1u /* an element lies within a0 of the voxel grid */
+#define PASFM_STATUS_TIMEOUT 2u        /* a bounded shared-memory barrier wait expired */
+#define PASFM_STATUS_INDEX_CLAMPED 4u  /* a sample index fell outside its window (clamped) */
+
+/* Acquisition geometry: the problem statement of the paper's Eq. 1 (voxel grid
+ * P_c in R^{Nx x Ny x Nz}, sensor positions x_s, time-resolved signals) plus
+ * the sampling of the time axis.  Host memory; read during the call only. */
+typedef struct pasfm_geom {
+  int32_t nx, ny, nz;                  /* voxel grid, x fastest                       */
+  int32_t n_elem, n_frames, n_samples; /* E elements, F frames, Nt samples per trace   */
+  double dx, dy, dz;                   /* voxel spacing (mm), > 0                      */
+  double ox, oy, oz;                   /* centre of voxel (0,0,0) (mm)                 */
+  double fs_mhz;                       /* sampling rate (MHz), > 0                     */
+  double t0_us;                        /* time of sample 0 (us); t_n = t0 + n / fs     */
+  double c_mm_per_us;                  /* speed of sound (mm/us), > 0                  */
+  double a0_mm;                        /* voxel sphere radius (mm); <= 0 means min(d)/2 */
+  int32_t dtype_vol;                   /* PASFM_F32 | PASFM_BF16 | PASFM_F16 (p0)       */
+  int32_t dtype_sig;                   /* PASFM_F32 | PASFM_BF16 | PASFM_F16 (meas, g)  */
+} pasfm_geom;
+
+typedef struct pasfm_ctx pasfm_ctx;
+
+/* Adam state for pasfm_step (paper: Adam for the Eq. 2 objective, Stage 1/5,
+ * and gradient steps on the rigid parameters, Stage 4).  Moment arrays are
+ * caller-owned device memory, zero before the first step. */
+typedef struct pasfm_adam {
+  float* m_vol;    /* [Nvox] first moment of the volume                          */
+  float* v_vol;    /* [Nvox] second moment of the volume                         */
+  double* m_pose;  /* [F][6] first moment of the frame twists (w, v)             */
+  double* v_pose;  /* [F][6] second moment of the frame twists                   */
+  int64_t step;    /* completed steps; pasfm_step uses step + 1 and increments it */
+  double lr_vol, lr_rot, lr_trans; /* learning rates (rad for w, mm for v)       */
+  double beta1, beta2, eps;
+  uint32_t flags;  /* PASFM_ADAM_* bits                                          */
+  uint32_t reserved;
+} pasfm_adam;
+
+#define PASFM_ADAM_NONNEG 1u        /* project p0 onto p0 >= 0 after the update      */
+#define PASFM_ADAM_FIX_FRAME0 2u    /* frame 0 is the gauge (known pose): not moved  */
+#define PASFM_ADAM_FREEZE_POSES 4u  /* no pose update (pure volume reconstruction)  */
+#define PASFM_ADAM_FREEZE_VOLUME 8u /* no volume update (pure pose refinement)      */
+
+/* Create a context on CUDA device `device` (allocates its status word).
+ * *out receives the context; returns PASFM_ECUDA if the device is unusable. */
+int pasfm_create(pasfm_ctx** out, int device);
+
+/* Free the context and its workspace.  NULL is accepted. */
+int pasfm_destroy(pasfm_ctx* ctx);
+
+/* Device bytes of workspace the calls need for `geom` (host-only, no CUDA call). */
+int pasfm_workspace_size(const pasfm_geom* geom, size_t* bytes);
+
+/* Grow the context's workspace to fit `geom` now, so later calls do not allocate. */
+int pasfm_reserve(pasfm_ctx* ctx, const pasfm_geom* geom);
+
+/* Cap the bytes used for per-cube partial results (default 4 GiB); larger
+ * problems are processed in frame chunks.  0 restores the default. */
+int pasfm_set_partial_budget(pasfm_ctx* ctx, size_t bytes);
+
+/* A1 -- element world positions x_fj = R_f e_j + t_f (Stage 4 rigid model).
+ * elem: double [E][3]; pose: double [F][3][4]; xw_out: double [F][E][3].
+ * Also checks every x_fj against the grid (status bit ELEMENT_INSIDE). */
+int pasfm_element_positions(pasfm_ctx* ctx, const pasfm_geom* geom, const double* elem,
+                            const double* pose, double* xw_out, void* stream);
+
+/* A2 -- forward radiation s = A(p0; poses) (Eq. 1 / Eq. gpu_forward_model).
+ * p0: [nz][ny][nx] of dtype_vol; sig_out: float [F][E][Nt]. */
+int pasfm_forward(pasfm_ctx* ctx, const pasfm_geom* geom, const void* p0, const double* elem,
+                  const double* pose, float* sig_out, void* stream);
+
+/* A4 -- adjoint v = A^T g (the gradient with respect to P_c, Section 2).
+ * g: [F][E][Nt] of dtype_sig; vol_out: float [nz][ny][nx]. */
+int pasfm_adjoint(pasfm_ctx* ctx, const pasfm_geom* geom, const double* elem, const double* pose,
+                  const void* g, float* vol_out, void* stream);
+
+/* A5 -- pose gradient (gradient with respect to the sensor coordinates x_s,
+ * Section 2, carried to the per-frame rigid parameters of Stage 4).
+ * g: [F][E][Nt] of dtype_sig; mask: uint8 [F][E] or NULL (0 drops a trace,
+ * the inlier mask of Eq. 4); grad6_out: double [F][6] ordered (w, v);
+ * gelem_out: double [F][E][3] element-position gradients, or NULL. */
+int pasfm_pose_grad(pasfm_ctx* ctx, const pasfm_geom* geom, const void* p0, const double* elem,
+                    const double* pose, const void* g, const uint8_t* mask, double* grad6_out,
+                    double* gelem_out, void* stream);
+
+/* A3 -- loss head of the Eq. 2 data term: g = mask (s - S), L = 1/2 sum g^2.
+ * sig: float [F][E][Nt]; meas: [F][E][Nt] of dtype_sig; mask: uint8 [F][E] or
+ * NULL; g_out: float [F][E][Nt] (may alias sig); loss_out: one device double. */
+int pasfm_loss(pasfm_ctx* ctx, const pasfm_geom* geom, const float* sig, const void* meas,
+               const uint8_t* mask, float* g_out, double* loss_out, void* stream);
+
+/* A6 -- one gradient step of L = 1/2 |mask (A(p0; poses) - S)|^2 jointly in p0
+ * and the frame twists (Algorithm 1, Stage 1 / 4 / 5 updates): forward, loss
+ * head, adjoint and pose gradient, then Adam on p0 and on the twists with a
+ * left retraction R <- Exp(dw) R, t <- Exp(dw) t + dv.
+ * p0 (dtype_vol) and pose are updated in place; elem, meas (dtype_sig) and
+ * mask (or NULL) are read; state->step is incremented on the host.
+ * loss_out: device double receiving L at the pre-update point, or NULL. */
+int pasfm_step(pasfm_ctx* ctx, const pasfm_geom* geom, void* p0, double* pose, const double* elem,
+               const void* meas, const uint8_t* mask, pasfm_adam* state, double* loss_out,
+               void* stream);
+
+/* Synchronise `stream` and read (then clear) the context's device status word.
+ * *bits receives the PASFM_STATUS_* bits seen (may be NULL).  Returns
+ * PASFM_OK, PASFM_ETIMEOUT or PASFM_EDEVICE. */
+int pasfm_status(pasfm_ctx* ctx, void* stream, uint32_t* bits);
+
+/* Per-kernel timing with CUDA events recorded around every launch of this
+ * context (off by default).  pasfm_timing_read() synchronises the recorded
+ * events and returns the summed milliseconds and launch count of kernels whose
+ * name is `kernel` ("fwd_cube", "fwd_reduce", "bwd_cube", ... or "*" for all). */
+int pasfm_timing_enable(pasfm_ctx* ctx, int enable);
+int pasfm_timing_reset(pasfm_ctx* ctx);
+int pasfm_timing_read(pasfm_ctx* ctx, const char* kernel, double* ms_total, int64_t* launches);
+
+/* Number of kernels this context launched since creation (all calls). */
+int64_t pasfm_launch_count(pasfm_ctx* ctx);
+
+/* Message describing the last error on the calling thread ("" if none). */
+const char* pasfm_last_error(void);
+
+/* ABI version of this header (incremented on any signature change). */
+int pasfm_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PASFM_H */

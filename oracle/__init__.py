@@ -61,6 +61,7 @@ def load(path: str):
     L.oracle_forward_rows.argtypes = [g, fp, dp, ctypes.c_void_p, ctypes.c_int64, dp]
     L.oracle_adjoint_voxels.argtypes = [g, dp, dp, ctypes.c_void_p, ctypes.c_int64, dp]
     L.oracle_pose_grad.argtypes = [g, fp, dp, dp, ctypes.c_void_p, dp, ctypes.c_void_p]
+    L.oracle_element_gradient_rows.argtypes = [g, fp, dp, dp, ctypes.c_void_p, ctypes.c_int64, dp]
     L.oracle_loss.argtypes = [g, dp, dp, ctypes.c_void_p, dp]
     L.oracle_loss.restype = ctypes.c_double
     return L
@@ -160,6 +161,16 @@ def pose_grad(geom, p0, gsig, xw, mask=None, **kw):
     lib().oracle_pose_grad(ctypes.byref(g), np.ascontiguousarray(p0, dtype=np.float32),
                            _f64(gsig), _f64(xw), mp, grad6, G.ctypes.data_as(ctypes.c_void_p))
     return grad6, G
+
+
+def element_gradient_rows(geom, p0, gsig, xw, rows):
+    """Element-position gradients [len(rows)][3] for flat (f*E + j) row indices."""
+    g = make_geom(geom)
+    r, rp = _opt_ptr(rows, np.int64)
+    out = np.zeros((len(r), 3))
+    lib().oracle_element_gradient_rows(ctypes.byref(g), np.ascontiguousarray(p0, dtype=np.float32),
+                                       _f64(gsig), _f64(xw), rp, len(r), out)
+    return out
 
 
 def loss(geom, sig, meas, mask=None):

@@ -194,6 +194,37 @@ void oracle_adjoint(const oracle_geom* g, const double* gsig, const double* xw, 
   oracle_adjoint_voxels(g, gsig, xw, NULL, 0, vol);
 }
 
+/* Element-position gradient of one (frame, element) trace:
+ * G = sum_i p0_i sum_n g[n] dW/dd (x - r_i) / d. */
+static void element_gradient(const oracle_geom* g, const float* p0, const double* gs, const double* x,
+                             double G[3]) {
+  double acc[3] = {0.0, 0.0, 0.0};
+  for (int iz = 0; iz < g->nz; ++iz)
+    for (int iy = 0; iy < g->ny; ++iy)
+      for (int ix = 0; ix < g->nx; ++ix) {
+        const double p = p0[((int64_t)iz * g->ny + iy) * g->nx + ix];
+        if (p == 0.0) continue;
+        double r[3];
+        voxel_centre(g, ix, iy, iz, r);
+        const double d = dist3(x, r);
+        int lo, hi;
+        if (!sample_range(g, d, &lo, &hi)) continue;
+        double s = 0.0;
+        for (int n = lo; n <= hi; ++n) s += gs[n] * oracle_pulse_dd(g, d, n);
+        for (int a = 0; a < 3; ++a) acc[a] += p * s * (x[a] - r[a]) / d;
+      }
+  for (int a = 0; a < 3; ++a) G[a] = acc[a];
+}
+
+/* Element gradients for the (frame, element) rows listed in rows[0..n_rows);
+ * gsig holds the full [F][E][Nt] residual; G is [n_rows][3]. */
+void oracle_element_gradient_rows(const oracle_geom* g, const float* p0, const double* gsig, const double* xw,
+                                  const int64_t* rows, int64_t n_rows, double* G) {
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t k = 0; k < n_rows; ++k)
+    element_gradient(g, p0, gsig + rows[k] * g->n_samples, xw + 3 * rows[k], G + 3 * k);
+}
+
 /* Element-position gradient G[f][j][3] and twist gradient grad6[f][6] = (w, v).
  * mask (may be NULL) zeroes whole (frame, element) traces of g. */
 void oracle_pose_grad(const oracle_geom* g, const float* p0, const double* gsig, const double* xw,
@@ -202,26 +233,11 @@ void oracle_pose_grad(const oracle_geom* g, const float* p0, const double* gsig,
   double* G = gelem ? gelem : (double*)malloc(sizeof(double) * 3 * (size_t)(nfj > 0 ? nfj : 1));
 #pragma omp parallel for schedule(dynamic, 1)
   for (int64_t fj = 0; fj < nfj; ++fj) {
-    const double* x = xw + 3 * fj;
-    const double* gs = gsig + fj * g->n_samples;
-    double acc[3] = {0.0, 0.0, 0.0};
     if (!mask || mask[fj]) {
-      for (int iz = 0; iz < g->nz; ++iz)
-        for (int iy = 0; iy < g->ny; ++iy)
-          for (int ix = 0; ix < g->nx; ++ix) {
-            const double p = p0[((int64_t)iz * g->ny + iy) * g->nx + ix];
-            if (p == 0.0) continue;
-            double r[3];
-            voxel_centre(g, ix, iy, iz, r);
-            const double d = dist3(x, r);
-            int lo, hi;
-            if (!sample_range(g, d, &lo, &hi)) continue;
-            double s = 0.0;
-            for (int n = lo; n <= hi; ++n) s += gs[n] * oracle_pulse_dd(g, d, n);
-            for (int a = 0; a < 3; ++a) acc[a] += p * s * (x[a] - r[a]) / d;
-          }
+      element_gradient(g, p0, gsig + fj * g->n_samples, xw + 3 * fj, G + 3 * fj);
+    } else {
+      G[3 * fj] = G[3 * fj + 1] = G[3 * fj + 2] = 0.0;
     }
-    for (int a = 0; a < 3; ++a) G[3 * fj + a] = acc[a];
   }
   for (int f = 0; f < g->n_frames; ++f) {
     double w[3] = {0, 0, 0}, v[3] = {0, 0, 0};

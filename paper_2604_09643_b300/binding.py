@@ -1,0 +1,305 @@
+"""ctypes binding of ``libpasfm.so`` (the C ABI in ``include/pasfm.h``).
+
+Argument marshalling only: every function here checks tensor placement, dtype
+and contiguity, passes ``data_ptr()`` and the current CUDA stream to the
+library, and turns a negative return code into :class:`PasfmError`.  No step
+of the operator runs in Python, and there is no CPU fallback: if the library
+cannot be loaded, every call raises.
+
+The low-level functions carry the ABI's names (``pasfm_forward`` ...).
+:class:`Context` wraps them with allocation of outputs for convenience.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "lib", "libpasfm.so")
+
+PASFM_F32, PASFM_BF16, PASFM_F16 = 0, 1, 2
+ADAM_NONNEG, ADAM_FIX_FRAME0, ADAM_FREEZE_POSES, ADAM_FREEZE_VOLUME = 1, 2, 4, 8
+STATUS_ELEMENT_INSIDE, STATUS_TIMEOUT, STATUS_INDEX_CLAMPED = 1, 2, 4
+
+_DTYPE_CODE = {torch.float32: PASFM_F32, torch.bfloat16: PASFM_BF16, torch.float16: PASFM_F16}
+
+
+class PasfmError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"pasfm error {code}: {msg}")
+        self.code = code
+
+
+class PasfmGeom(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+                ("n_elem", ctypes.c_int32), ("n_frames", ctypes.c_int32), ("n_samples", ctypes.c_int32),
+                ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("dz", ctypes.c_double),
+                ("ox", ctypes.c_double), ("oy", ctypes.c_double), ("oz", ctypes.c_double),
+                ("fs_mhz", ctypes.c_double), ("t0_us", ctypes.c_double),
+                ("c_mm_per_us", ctypes.c_double), ("a0_mm", ctypes.c_double),
+                ("dtype_vol", ctypes.c_int32), ("dtype_sig", ctypes.c_int32)]
+
+
+class PasfmAdam(ctypes.Structure):
+    _fields_ = [("m_vol", ctypes.c_void_p), ("v_vol", ctypes.c_void_p),
+                ("m_pose", ctypes.c_void_p), ("v_pose", ctypes.c_void_p),
+                ("step", ctypes.c_int64),
+                ("lr_vol", ctypes.c_double), ("lr_rot", ctypes.c_double), ("lr_trans", ctypes.c_double),
+                ("beta1", ctypes.c_double), ("beta2", ctypes.c_double), ("eps", ctypes.c_double),
+                ("flags", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+
+_lib = None
+_VP, _I, _SZ = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t
+_G = ctypes.POINTER(PasfmGeom)
+_SIGS = {
+    "pasfm_create": ([ctypes.POINTER(_VP), _I], _I),
+    "pasfm_destroy": ([_VP], _I),
+    "pasfm_workspace_size": ([_G, ctypes.POINTER(_SZ)], _I),
+    "pasfm_reserve": ([_VP, _G], _I),
+    "pasfm_set_partial_budget": ([_VP, _SZ], _I),
+    "pasfm_element_positions": ([_VP, _G, _VP, _VP, _VP, _VP], _I),
+    "pasfm_forward": ([_VP, _G, _VP, _VP, _VP, _VP, _VP], _I),
+    "pasfm_adjoint": ([_VP, _G, _VP, _VP, _VP, _VP, _VP], _I),
+    "pasfm_pose_grad": ([_VP, _G, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP], _I),
+    "pasfm_loss": ([_VP, _G, _VP, _VP, _VP, _VP, _VP, _VP], _I),
+    "pasfm_step": ([_VP, _G, _VP, _VP, _VP, _VP, _VP, ctypes.POINTER(PasfmAdam), _VP, _VP], _I),
+    "pasfm_status": ([_VP, _VP, ctypes.POINTER(ctypes.c_uint32)], _I),
+    "pasfm_timing_enable": ([_VP, _I], _I),
+    "pasfm_timing_reset": ([_VP], _I),
+    "pasfm_timing_read": ([_VP, ctypes.c_char_p, ctypes.POINTER(ctypes.c_double),
+                           ctypes.POINTER(ctypes.c_int64)], _I),
+    "pasfm_launch_count": ([_VP], ctypes.c_int64),
+    "pasfm_last_error": ([], ctypes.c_char_p),
+    "pasfm_abi_version": ([], _I),
+}
+
+
+def lib():
+    """Load libpasfm.so (raises if it was not built: there is no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: run `python -m paper_2604_09643_b300.build`")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (args, res) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = L
+    return _lib
+
+
+def symbols():
+    """Names of the ABI functions this binding declares."""
+    return sorted(_SIGS)
+
+
+def _check(rc):
+    if rc != 0:
+        raise PasfmError(rc, lib().pasfm_last_error().decode(errors="replace"))
+    return rc
+
+
+def make_geom(geom: dict, dtype_vol=torch.float32, dtype_sig=torch.float32) -> PasfmGeom:
+    g = PasfmGeom()
+    for k in ("nx", "ny", "nz", "n_elem", "n_frames", "n_samples"):
+        setattr(g, k, int(geom[k]))
+    for k in ("dx", "dy", "dz", "ox", "oy", "oz", "fs_mhz", "t0_us", "c_mm_per_us", "a0_mm"):
+        setattr(g, k, float(geom[k]))
+    g.dtype_vol = _DTYPE_CODE[dtype_vol]
+    g.dtype_sig = _DTYPE_CODE[dtype_sig]
+    return g
+
+
+def _ptr(t, dtype=None, name="tensor", allow_none=False):
+    if t is None:
+        if allow_none:
+            return None
+        raise ValueError(f"{name} is required")
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if dtype is not None and t.dtype not in (dtype if isinstance(dtype, tuple) else (dtype,)):
+        raise ValueError(f"{name} has dtype {t.dtype}, expected {dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream, device):
+    if stream is None:
+        stream = torch.cuda.current_stream(device)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+_VOL = (torch.float32, torch.bfloat16, torch.float16)
+
+
+# ----------------------------------------------------------------------------- ABI-named calls
+
+def pasfm_element_positions(ctx, geom, elem, pose, xw_out, stream=None):
+    g = make_geom(geom)
+    _check(lib().pasfm_element_positions(ctx, ctypes.byref(g), _ptr(elem, torch.float64, "elem"),
+                                         _ptr(pose, torch.float64, "pose"), _ptr(xw_out, torch.float64, "xw_out"),
+                                         _stream(stream, xw_out.device)))
+
+
+def pasfm_forward(ctx, geom, p0, elem, pose, sig_out, stream=None):
+    g = make_geom(geom, dtype_vol=p0.dtype)
+    _check(lib().pasfm_forward(ctx, ctypes.byref(g), _ptr(p0, _VOL, "p0"), _ptr(elem, torch.float64, "elem"),
+                               _ptr(pose, torch.float64, "pose"), _ptr(sig_out, torch.float32, "sig_out"),
+                               _stream(stream, sig_out.device)))
+
+
+def pasfm_adjoint(ctx, geom, elem, pose, g_sig, vol_out, stream=None):
+    g = make_geom(geom, dtype_sig=g_sig.dtype)
+    _check(lib().pasfm_adjoint(ctx, ctypes.byref(g), _ptr(elem, torch.float64, "elem"),
+                               _ptr(pose, torch.float64, "pose"), _ptr(g_sig, _VOL, "g"),
+                               _ptr(vol_out, torch.float32, "vol_out"), _stream(stream, vol_out.device)))
+
+
+def pasfm_pose_grad(ctx, geom, p0, elem, pose, g_sig, mask, grad6_out, gelem_out=None, stream=None):
+    g = make_geom(geom, dtype_vol=p0.dtype, dtype_sig=g_sig.dtype)
+    _check(lib().pasfm_pose_grad(ctx, ctypes.byref(g), _ptr(p0, _VOL, "p0"), _ptr(elem, torch.float64, "elem"),
+                                 _ptr(pose, torch.float64, "pose"), _ptr(g_sig, _VOL, "g"),
+                                 _ptr(mask, torch.uint8, "mask", allow_none=True),
+                                 _ptr(grad6_out, torch.float64, "grad6_out"),
+                                 _ptr(gelem_out, torch.float64, "gelem_out", allow_none=True),
+                                 _stream(stream, grad6_out.device)))
+
+
+def pasfm_loss(ctx, geom, sig, meas, mask, g_out, loss_out, stream=None):
+    g = make_geom(geom, dtype_sig=meas.dtype)
+    _check(lib().pasfm_loss(ctx, ctypes.byref(g), _ptr(sig, torch.float32, "sig"), _ptr(meas, _VOL, "meas"),
+                            _ptr(mask, torch.uint8, "mask", allow_none=True), _ptr(g_out, torch.float32, "g_out"),
+                            _ptr(loss_out, torch.float64, "loss_out"), _stream(stream, loss_out.device)))
+
+
+def pasfm_step(ctx, geom, p0, pose, elem, meas, mask, adam: PasfmAdam, loss_out=None, stream=None):
+    g = make_geom(geom, dtype_vol=p0.dtype, dtype_sig=meas.dtype)
+    _check(lib().pasfm_step(ctx, ctypes.byref(g), _ptr(p0, _VOL, "p0"), _ptr(pose, torch.float64, "pose"),
+                            _ptr(elem, torch.float64, "elem"), _ptr(meas, _VOL, "meas"),
+                            _ptr(mask, torch.uint8, "mask", allow_none=True), ctypes.byref(adam),
+                            _ptr(loss_out, torch.float64, "loss_out", allow_none=True),
+                            _stream(stream, p0.device)))
+
+
+def pasfm_status(ctx, stream=None, device=None):
+    bits = ctypes.c_uint32(0)
+    rc = lib().pasfm_status(ctx, _stream(stream, device), ctypes.byref(bits))
+    return rc, int(bits.value)
+
+
+# ----------------------------------------------------------------------------- convenience
+
+class Context:
+    """Owns one ``pasfm_ctx`` (workspace + status word) on one device.
+
+    Use one Context per concurrently running stream."""
+
+    def __init__(self, device=0):
+        if isinstance(device, torch.device):
+            device = device.index or 0
+        self.device = torch.device("cuda", int(device))
+        h = ctypes.c_void_p()
+        _check(lib().pasfm_create(ctypes.byref(h), int(device)))
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().pasfm_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- calls -----------------------------------------------------------------
+    def reserve(self, geom, dtype_vol=torch.float32, dtype_sig=torch.float32):
+        g = make_geom(geom, dtype_vol, dtype_sig)
+        _check(lib().pasfm_reserve(self.handle, ctypes.byref(g)))
+
+    def set_partial_budget(self, nbytes):
+        _check(lib().pasfm_set_partial_budget(self.handle, int(nbytes)))
+
+    def element_positions(self, geom, elem, pose, out=None, stream=None):
+        F, E = geom["n_frames"], geom["n_elem"]
+        out = torch.empty((F, E, 3), dtype=torch.float64, device=self.device) if out is None else out
+        pasfm_element_positions(self.handle, geom, elem, pose, out, stream)
+        return out
+
+    def forward(self, geom, p0, elem, pose, out=None, stream=None):
+        shape = (geom["n_frames"], geom["n_elem"], geom["n_samples"])
+        out = torch.empty(shape, dtype=torch.float32, device=self.device) if out is None else out
+        pasfm_forward(self.handle, geom, p0, elem, pose, out, stream)
+        return out
+
+    def adjoint(self, geom, elem, pose, g_sig, out=None, stream=None):
+        shape = (geom["nz"], geom["ny"], geom["nx"])
+        out = torch.empty(shape, dtype=torch.float32, device=self.device) if out is None else out
+        pasfm_adjoint(self.handle, geom, elem, pose, g_sig, out, stream)
+        return out
+
+    def pose_grad(self, geom, p0, elem, pose, g_sig, mask=None, want_elem=False, stream=None):
+        F, E = geom["n_frames"], geom["n_elem"]
+        g6 = torch.empty((F, 6), dtype=torch.float64, device=self.device)
+        ge = torch.empty((F, E, 3), dtype=torch.float64, device=self.device) if want_elem else None
+        pasfm_pose_grad(self.handle, geom, p0, elem, pose, g_sig, mask, g6, ge, stream)
+        return (g6, ge) if want_elem else g6
+
+    def loss(self, geom, sig, meas, mask=None, g_out=None, stream=None):
+        g_out = torch.empty_like(sig) if g_out is None else g_out
+        L = torch.empty((), dtype=torch.float64, device=self.device)
+        pasfm_loss(self.handle, geom, sig, meas, mask, g_out, L, stream)
+        return L, g_out
+
+    def step(self, geom, p0, pose, elem, meas, adam: "AdamState", mask=None, loss_out=None, stream=None):
+        pasfm_step(self.handle, geom, p0, pose, elem, meas, mask, adam.c, loss_out, stream)
+
+    def status(self, stream=None):
+        return pasfm_status(self.handle, stream, self.device)
+
+    def timing(self, enable=True):
+        _check(lib().pasfm_timing_enable(self.handle, int(bool(enable))))
+
+    def timing_reset(self):
+        _check(lib().pasfm_timing_reset(self.handle))
+
+    def timing_read(self, kernel="*"):
+        ms, n = ctypes.c_double(0.0), ctypes.c_int64(0)
+        _check(lib().pasfm_timing_read(self.handle, kernel.encode(), ctypes.byref(ms), ctypes.byref(n)))
+        return float(ms.value), int(n.value)
+
+    def launch_count(self):
+        return int(lib().pasfm_launch_count(self.handle))
+
+
+class AdamState:
+    """Device-resident Adam moments for a volume and F frame twists."""
+
+    def __init__(self, geom, device, lr_vol=1e-2, lr_rot=1e-3, lr_trans=1e-2, beta1=0.9, beta2=0.999,
+                 eps=1e-8, nonneg=False, fix_frame0=False, freeze_poses=False, freeze_volume=False):
+        nvox = geom["nx"] * geom["ny"] * geom["nz"]
+        F = geom["n_frames"]
+        self.m_vol = torch.zeros(nvox, dtype=torch.float32, device=device)
+        self.v_vol = torch.zeros(nvox, dtype=torch.float32, device=device)
+        self.m_pose = torch.zeros((F, 6), dtype=torch.float64, device=device)
+        self.v_pose = torch.zeros((F, 6), dtype=torch.float64, device=device)
+        flags = ((ADAM_NONNEG if nonneg else 0) | (ADAM_FIX_FRAME0 if fix_frame0 else 0)
+                 | (ADAM_FREEZE_POSES if freeze_poses else 0) | (ADAM_FREEZE_VOLUME if freeze_volume else 0))
+        self.c = PasfmAdam(self.m_vol.data_ptr(), self.v_vol.data_ptr(), self.m_pose.data_ptr(),
+                           self.v_pose.data_ptr(), 0, lr_vol, lr_rot, lr_trans, beta1, beta2, eps, flags, 0)
+
+    @property
+    def step(self):
+        return int(self.c.step)

@@ -1,0 +1,89 @@
+"""Build ``lib/libpasfm.so`` (sm_103a) from ``csrc/`` with nvcc.
+
+The hot kernels are instantiated once per sample-slot count S (2..16) from
+``kernels_s.cu``; those translation units compile in parallel.  The library is
+built in-tree so that it travels with the source tree.
+
+    python -m paper_2604_09643_b300.build [--force]
+"""
+from __future__ import annotations
+
+import argparse
+import concurrent.futures as cf
+import glob
+import os
+import shutil
+import subprocess
+import sys
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+CSRC = os.path.join(HERE, "csrc")
+OBJ = os.path.join(HERE, "_build")
+LIB = os.path.join(HERE, "lib", "libpasfm.so")
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+S_VALUES = range(2, 17)
+
+
+def nvcc() -> str:
+    for cand in (shutil.which("nvcc"), "/usr/local/cuda/bin/nvcc"):
+        if cand and os.path.exists(cand):
+            return cand
+    raise RuntimeError("nvcc not found: the CUDA toolkit is required to build libpasfm")
+
+
+def _flags():
+    return ["-std=c++17", "-O3", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
+            f"-I{os.path.join(ROOT, 'include')}"]
+
+
+def _sources():
+    return glob.glob(os.path.join(CSRC, "*")) + [os.path.join(ROOT, "include", "pasfm.h")]
+
+
+def _stale() -> bool:
+    if not os.path.exists(LIB):
+        return True
+    t = os.path.getmtime(LIB)
+    return any(os.path.getmtime(p) > t for p in _sources())
+
+
+def _compile(job):
+    src, obj, extra = job
+    cmd = [nvcc(), *_flags(), *extra, "-c", src, "-o", obj]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"nvcc failed for {os.path.basename(obj)}:\n{r.stderr}")
+    return obj
+
+
+def build(force: bool = False, jobs: int | None = None, verbose: bool = False) -> str:
+    """Compile every CUDA translation unit for sm_103a and link libpasfm.so."""
+    if not force and not _stale():
+        return LIB
+    os.makedirs(OBJ, exist_ok=True)
+    os.makedirs(os.path.dirname(LIB), exist_ok=True)
+    work = [(os.path.join(CSRC, "kernels_s.cu"), os.path.join(OBJ, f"kernels_s{s}.o"), [f"-DPASFM_S={s}"])
+            for s in S_VALUES]
+    work += [(os.path.join(CSRC, "aux.cu"), os.path.join(OBJ, "aux.o"), []),
+             (os.path.join(CSRC, "pasfm.cu"), os.path.join(OBJ, "pasfm.o"), [])]
+    jobs = jobs or max(1, min(len(work), os.cpu_count() or 1))
+    with cf.ThreadPoolExecutor(jobs) as ex:
+        objs = list(ex.map(_compile, work))
+    tmp = LIB + ".tmp"
+    cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-Xcompiler", "-fPIC"]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"link failed:\n{r.stderr}")
+    os.replace(tmp, LIB)
+    if verbose:
+        print("built", LIB)
+    return LIB
+
+
+if __name__ == "__main__":
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--force", action="store_true")
+    a = ap.parse_args()
+    build(force=a.force, verbose=True)
+    sys.exit(0)

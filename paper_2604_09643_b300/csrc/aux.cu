@@ -1,0 +1,292 @@
+// Auxiliary sm_103a kernels: element positions (A1), the fixed-order reduction
+// of per-cube forward partials with the fused loss head (A2/A3), the pose-
+// gradient reductions (A5), and Adam on the volume and on the frame twists (A6).
+// All reductions visit their terms in a fixed order, so repeated calls give
+// bit-identical results.
+#include <climits>
+
+#include "aux.cuh"
+#include "pasfm_dev.cuh"
+
+namespace pasfm {
+
+// x_fj = R_f e_j + t_f in FP64; flag elements closer than a0 to the grid box.
+__global__ void elem_pos_kernel(const double* __restrict__ elem, const double* __restrict__ pose,
+                                double* __restrict__ xw, int F, int E, double lox, double loy, double loz,
+                                double hix, double hiy, double hiz, double a0, unsigned* status) {
+  const int64_t k = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (k >= static_cast<int64_t>(F) * E) return;
+  const int f = static_cast<int>(k / E), j = static_cast<int>(k % E);
+  const double* P = pose + 12 * static_cast<int64_t>(f);
+  const double e0 = elem[3 * j], e1 = elem[3 * j + 1], e2 = elem[3 * j + 2];
+  double x[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) x[a] = fma(P[4 * a], e0, fma(P[4 * a + 1], e1, fma(P[4 * a + 2], e2, P[4 * a + 3])));
+  xw[3 * k] = x[0];
+  xw[3 * k + 1] = x[1];
+  xw[3 * k + 2] = x[2];
+  const double bx = fmax(fmax(lox - x[0], x[0] - hix), 0.0);
+  const double by = fmax(fmax(loy - x[1], x[1] - hiy), 0.0);
+  const double bz = fmax(fmax(loz - x[2], x[2] - hiz), 0.0);
+  if (bx * bx + by * by + bz * bz <= a0 * a0) atomicOr(status, PASFM_STATUS_ELEMENT_INSIDE);
+}
+
+// Emit sample n of a trace: signal and/or masked residual with its square.
+struct Emitter {
+  float* sig;
+  float* g;
+  const void* meas;
+  int dtype;
+  bool keep;
+  double lsum;
+  __device__ __forceinline__ void operator()(int64_t off, float s) {
+    if (sig) sig[off] = s;
+    if (g) {
+      const float r = keep ? s - load_elem(meas, off, dtype) : 0.f;
+      g[off] = r;
+      lsum = fma(static_cast<double>(r), static_cast<double>(r), lsum);
+    }
+  }
+};
+
+__device__ __forceinline__ void block_loss(double lsum, double* out, int warp, int lane) {
+  __shared__ double wsum[8];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
+  if (lane == 0) wsum[warp] = lsum;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (blockDim.x >> 5); ++w) t += wsum[w];
+    *out = 0.5 * t;
+  }
+}
+
+// One warp per trace: sum the per-cube partial windows in cube order.
+__global__ void __launch_bounds__(256) fwd_reduce_kernel(const RedParams P) {
+  extern __shared__ float racc[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int row = blockIdx.x * 8 + warp;
+  float* acc = racc + warp * kRedChunk;
+  Emitter em{P.sig_out, P.g_out, P.meas, P.dtype_sig, true, 0.0};
+  if (row < P.n_rows) {
+    const int* n0 = P.n0tab + static_cast<int64_t>(row) * P.ncubes;
+    const float* part = P.part + static_cast<int64_t>(row) * P.ncubes * P.W;
+    int nmin = INT_MAX, nmax = INT_MIN;
+    for (int cc = lane; cc < P.ncubes; cc += 32) {
+      const int v = n0[cc];
+      nmin = min(nmin, v);
+      nmax = max(nmax, v);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      nmin = min(nmin, __shfl_xor_sync(0xffffffffu, nmin, o));
+      nmax = max(nmax, __shfl_xor_sync(0xffffffffu, nmax, o));
+    }
+    const int lo = max(nmin, 0);
+    const int hi = min(nmax + P.W, P.Nt);
+    const int64_t grow = static_cast<int64_t>(P.f_begin) * P.E + row;
+    em.keep = P.mask ? (P.mask[grow] != 0) : true;
+    const int64_t base = grow * P.Nt;
+    for (int n = lane; n < P.Nt; n += 32)
+      if (n < lo || n >= hi) em(base + n, 0.f);
+    for (int cs = lo; cs < hi; cs += kRedChunk) {
+      const int len = min(kRedChunk, hi - cs);
+      for (int k = lane; k < len; k += 32) acc[k] = 0.f;
+      __syncwarp();
+      for (int cc = 0; cc < P.ncubes; cc += kRedUnroll) {
+        int o[kRedUnroll];
+        float v[kRedUnroll][kRedLanes];
+#pragma unroll
+        for (int u = 0; u < kRedUnroll; ++u) {
+          const bool okc = cc + u < P.ncubes;
+          o[u] = okc ? n0[cc + u] - cs : INT_MIN / 2;
+          const float* src = part + static_cast<int64_t>(cc + u) * P.W;
+#pragma unroll
+          for (int m = 0; m < kRedLanes; ++m) {
+            const int k = lane + 32 * m;
+            v[u][m] = (okc && k < P.W) ? src[k] : 0.f;
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < kRedUnroll; ++u) {
+#pragma unroll
+          for (int m = 0; m < kRedLanes; ++m) {
+            const int k = lane + 32 * m;
+            const int pos = o[u] + k;
+            if (k < P.W && pos >= 0 && pos < len) acc[pos] += v[u][m];
+          }
+          __syncwarp();
+        }
+      }
+      for (int k = lane; k < len; k += 32) em(base + cs + k, acc[k]);
+      __syncwarp();
+    }
+  }
+  if (P.loss_part) block_loss(em.lsum, P.loss_part + P.loss_offset + blockIdx.x, warp, lane);
+}
+
+// Standalone loss head: one warp per trace.
+__global__ void __launch_bounds__(256) loss_rows_kernel(const float* __restrict__ sig, const void* meas,
+                                                        int dtype, const uint8_t* __restrict__ mask,
+                                                        float* g, double* loss_part, int n_rows, int Nt) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int row = blockIdx.x * 8 + warp;
+  Emitter em{nullptr, g, meas, dtype, true, 0.0};
+  if (row < n_rows) {
+    em.keep = mask ? (mask[row] != 0) : true;
+    const int64_t base = static_cast<int64_t>(row) * Nt;
+    for (int n = lane; n < Nt; n += 32) em(base + n, sig[base + n]);
+  }
+  block_loss(em.lsum, loss_part + blockIdx.x, warp, lane);
+}
+
+// Sum block partials in a fixed order (one block).
+__global__ void __launch_bounds__(256) sum_kernel(const double* __restrict__ part, int n, double* out) {
+  __shared__ double s[256];
+  double t = 0.0;
+  for (int i = threadIdx.x; i < n; i += 256) t += part[i];
+  s[threadIdx.x] = t;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) s[threadIdx.x] += s[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = s[0];
+}
+
+// Element gradients: one warp per trace sums its per-cube partials (cube order).
+__global__ void __launch_bounds__(256) pose_rows_kernel(const double* __restrict__ gpart, int ncubes,
+                                                        int n_rows, int64_t row0, double* __restrict__ G) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int row = blockIdx.x * 8 + warp;
+  if (row >= n_rows) return;
+  const double* src = gpart + static_cast<int64_t>(row) * ncubes * 3;
+  double a = 0.0, b = 0.0, c = 0.0;
+  for (int k = lane; k < ncubes; k += 32) {
+    a += src[3 * k];
+    b += src[3 * k + 1];
+    c += src[3 * k + 2];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+    c += __shfl_xor_sync(0xffffffffu, c, o);
+  }
+  if (lane == 0) {
+    double* dst = G + (row0 + row) * 3;
+    dst[0] = a;
+    dst[1] = b;
+    dst[2] = c;
+  }
+}
+
+// grad6[f] = (sum_j x_fj x G_fj, sum_j G_fj): one block per frame.
+__global__ void __launch_bounds__(256) grad6_kernel(const double* __restrict__ xw, const double* __restrict__ G,
+                                                    int E, double* __restrict__ grad6) {
+  __shared__ double s[6][256];
+  const int f = blockIdx.x;
+  double w0 = 0, w1 = 0, w2 = 0, v0 = 0, v1 = 0, v2 = 0;
+  for (int j = threadIdx.x; j < E; j += 256) {
+    const double* x = xw + (static_cast<int64_t>(f) * E + j) * 3;
+    const double* g = G + (static_cast<int64_t>(f) * E + j) * 3;
+    w0 += x[1] * g[2] - x[2] * g[1];
+    w1 += x[2] * g[0] - x[0] * g[2];
+    w2 += x[0] * g[1] - x[1] * g[0];
+    v0 += g[0];
+    v1 += g[1];
+    v2 += g[2];
+  }
+  const int t = threadIdx.x;
+  s[0][t] = w0;
+  s[1][t] = w1;
+  s[2][t] = w2;
+  s[3][t] = v0;
+  s[4][t] = v1;
+  s[5][t] = v2;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (t < w)
+      for (int q = 0; q < 6; ++q) s[q][t] += s[q][t + w];
+    __syncthreads();
+  }
+  if (t < 6) grad6[6 * f + t] = s[t][0];
+}
+
+// Adam on the volume in its storage type; moments in FP32.
+__global__ void adam_vol_kernel(void* p0, int dtype, const float* __restrict__ grad, float* __restrict__ m,
+                                float* __restrict__ v, int64_t n, float b1, float b2, float lr_t,
+                                float inv_sqrt_bc2, float eps, int nonneg) {
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float g = grad[i];
+  const float mi = fmaf(b1, m[i], (1.f - b1) * g);
+  const float vi = fmaf(b2, v[i], (1.f - b2) * g * g);
+  m[i] = mi;
+  v[i] = vi;
+  float p = load_elem(p0, i, dtype);
+  p -= lr_t * mi / (sqrtf(vi) * inv_sqrt_bc2 + eps);
+  if (nonneg) p = fmaxf(p, 0.f);
+  if (dtype == PASFM_BF16) {
+    static_cast<__nv_bfloat16*>(p0)[i] = __float2bfloat16_rn(p);
+  } else if (dtype == PASFM_F16) {
+    static_cast<__half*>(p0)[i] = __float2half_rn(p);
+  } else {
+    static_cast<float*>(p0)[i] = p;
+  }
+}
+
+// Adam on the frame twists (FP64), then the left retraction
+// R <- Exp(dw) R, t <- Exp(dw) t + dv (Rodrigues).
+__global__ void adam_pose_kernel(double* __restrict__ pose, const double* __restrict__ grad6,
+                                 double* __restrict__ m, double* __restrict__ v, int F, double b1, double b2,
+                                 double bc1, double bc2, double lr_rot, double lr_trans, double eps, int fix0,
+                                 int freeze) {
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= F) return;
+  double dxi[6];
+  for (int k = 0; k < 6; ++k) {
+    const double g = grad6[6 * f + k];
+    const double mk = b1 * m[6 * f + k] + (1.0 - b1) * g;
+    const double vk = b2 * v[6 * f + k] + (1.0 - b2) * g * g;
+    m[6 * f + k] = mk;
+    v[6 * f + k] = vk;
+    const double lr = k < 3 ? lr_rot : lr_trans;
+    dxi[k] = -lr * (mk / bc1) / (sqrt(vk / bc2) + eps);
+  }
+  if (freeze || (fix0 && f == 0)) return;
+  const double w0 = dxi[0], w1 = dxi[1], w2 = dxi[2];
+  const double th2 = w0 * w0 + w1 * w1 + w2 * w2;
+  const double th = sqrt(th2);
+  double A, B;
+  if (th < 1e-12) {
+    A = 1.0;
+    B = 0.5;
+  } else {
+    A = sin(th) / th;
+    B = (1.0 - cos(th)) / th2;
+  }
+  // Exp = I + A K + B K^2 with K = skew(w)
+  const double K[3][3] = {{0, -w2, w1}, {w2, 0, -w0}, {-w1, w0, 0}};
+  double Ex[3][3];
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c) {
+      double k2 = 0.0;
+      for (int q = 0; q < 3; ++q) k2 += K[r][q] * K[q][c];
+      Ex[r][c] = (r == c ? 1.0 : 0.0) + A * K[r][c] + B * k2;
+    }
+  double* P = pose + 12 * static_cast<int64_t>(f);
+  double out[12];
+  for (int r = 0; r < 3; ++r) {
+    for (int c = 0; c < 4; ++c) {
+      double s = 0.0;
+      for (int q = 0; q < 3; ++q) s += Ex[r][q] * P[4 * q + c];
+      out[4 * r + c] = s;
+    }
+    out[4 * r + 3] += dxi[3 + r];
+  }
+  for (int k = 0; k < 12; ++k) P[k] = out[k];
+}
+
+}  // namespace pasfm

@@ -1,0 +1,56 @@
+// Declarations of the auxiliary kernels (aux.cu) and the per-S launchers of the
+// hot kernels (kernels_s.cu, compiled once per slot count S).
+#pragma once
+
+#include "pasfm_dev.cuh"
+
+namespace pasfm {
+
+constexpr int kRedChunk = 2048;  // samples per warp accumulator in fwd_reduce_kernel
+constexpr int kRedUnroll = 4;    // cubes loaded per step
+constexpr int kRedLanes = 8;     // ceil(W_max / 32), W_max = 256
+constexpr int kMinS = 2, kMaxS = 16;
+
+__global__ void elem_pos_kernel(const double* elem, const double* pose, double* xw, int F, int E, double lox,
+                                double loy, double loz, double hix, double hiy, double hiz, double a0,
+                                unsigned* status);
+__global__ void fwd_reduce_kernel(const RedParams P);
+__global__ void loss_rows_kernel(const float* sig, const void* meas, int dtype, const uint8_t* mask, float* g,
+                                 double* loss_part, int n_rows, int Nt);
+__global__ void sum_kernel(const double* part, int n, double* out);
+__global__ void pose_rows_kernel(const double* gpart, int ncubes, int n_rows, int64_t row0, double* G);
+__global__ void grad6_kernel(const double* xw, const double* G, int E, double* grad6);
+__global__ void adam_vol_kernel(void* p0, int dtype, const float* grad, float* m, float* v, int64_t n, float b1,
+                                float b2, float lr_t, float inv_sqrt_bc2, float eps, int nonneg);
+__global__ void adam_pose_kernel(double* pose, const double* grad6, double* m, double* v, int F, double b1,
+                                 double b2, double bc1, double bc2, double lr_rot, double lr_trans, double eps,
+                                 int fix0, int freeze);
+
+using FwdLaunch = cudaError_t (*)(int C, const CUtensorMap& map, const FwdParams& P, dim3 grid, int threads,
+                                  size_t smem, cudaStream_t st);
+using BwdLaunch = cudaError_t (*)(int C, int mode, const CUtensorMap& map, const BwdParams& P, dim3 grid,
+                                  size_t smem, cudaStream_t st);
+
+#define PASFM_DECL_S(S)                                                                              \
+  cudaError_t fwd_launch_s##S(int C, const CUtensorMap& map, const FwdParams& P, dim3 grid, int threads, \
+                              size_t smem, cudaStream_t st);                                           \
+  cudaError_t bwd_launch_s##S(int C, int mode, const CUtensorMap& map, const BwdParams& P, dim3 grid,  \
+                              size_t smem, cudaStream_t st);
+PASFM_DECL_S(2)
+PASFM_DECL_S(3)
+PASFM_DECL_S(4)
+PASFM_DECL_S(5)
+PASFM_DECL_S(6)
+PASFM_DECL_S(7)
+PASFM_DECL_S(8)
+PASFM_DECL_S(9)
+PASFM_DECL_S(10)
+PASFM_DECL_S(11)
+PASFM_DECL_S(12)
+PASFM_DECL_S(13)
+PASFM_DECL_S(14)
+PASFM_DECL_S(15)
+PASFM_DECL_S(16)
+#undef PASFM_DECL_S
+
+}  // namespace pasfm

@@ -1,0 +1,447 @@
+// Hot kernels of the radiation operator (sm_103a, FP32 pair arithmetic).
+//
+//   fwd_cube_kernel  -- forward s = A(p0; poses).  Element-stationary: lane =
+//                       element, a warp owns 32 elements, a CTA owns one cube of
+//                       C^3 voxels (staged by a 3-D TMA load) for one frame.
+//                       Each lane scatters its pulse samples into a private
+//                       column of a shared-memory time window laid out
+//                       [slot][32 lanes], so any per-lane offset is
+//                       bank-conflict free and no atomics are needed.  The
+//                       window (the cube's distance range for that element) is
+//                       flushed as a per-cube partial trace; fwd_reduce_kernel
+//                       sums the partials in a fixed order.
+//   bwd_cube_kernel  -- adjoint v = A^T g and/or pose gradient.  Voxel-
+//                       stationary: a thread owns a row of C voxels along x; the
+//                       CTA walks all (frame, element) traces in batches of 32
+//                       whose sample windows are staged by 2-D TMA loads into a
+//                       double buffer.  The adjoint is an atomic-free gather; the
+//                       pose gradient is reduced per element with warp shuffles
+//                       and a fixed-order block reduction, then carried to FP64.
+//
+// Sample slots: a voxel-element pair touches at most S = floor(2 a0 / h) + 2
+// consecutive samples.  With psi = (d - a0 - tau0) / h + 1/2 and first slot
+// n_s = floor(psi), the slot boundaries beta_k = (n_s - psi) h - a0 + k h satisfy
+// beta_0 <= -a0 and beta_S > a0, boundaries 1..S-2 lie inside [-a0, a0] and only
+// boundary S-1 needs a clamp.  Sample n_s + k then gets
+//     W = (b_k - b_{k+1}) / (4 d h),  b_k = clamp(beta_k)^2,  b_0 = b_S = a0^2,
+// which is the interval average of the uniform-sphere pulse (Appendix A).
+#pragma once
+
+#include "pasfm_dev.cuh"
+
+namespace pasfm {
+
+// ------------------------------------------------------------------------
+// per-pair slot math
+// ------------------------------------------------------------------------
+struct PairMath {
+  float rs;     // 1 / d
+  float ns;     // first slot relative to N_c (float)
+  int nsi;      // first slot relative to N_c
+  float beta0;  // lower boundary of the first slot (mm), <= -a0
+};
+
+__device__ __forceinline__ PairMath pair_math(float A, float dc2, float dcf, float phim, float inv_h, float h,
+                                              float cb) {
+  PairMath m;
+  const float D2 = dc2 + A;
+  m.rs = rsqrtf(D2);
+  const float d = D2 * m.rs;
+  const float del = __fdividef(A, d + dcf);  // d - d_c without cancellation
+  const float psi = fmaf(del, inv_h, phim);  // psi_c - N_c - 1/2 + delta / h
+  const float t = psi + kMagic;              // round to nearest = floor(psi + 1/2)
+  m.ns = t - kMagic;
+  m.nsi = __float_as_int(t) - kMagicBits;
+  m.beta0 = fmaf(m.ns - psi, h, cb);         // (n_s - psi_full) h - a0
+  return m;
+}
+
+// ------------------------------------------------------------------------
+// forward
+// ------------------------------------------------------------------------
+template <int C>
+__host__ __device__ constexpr int fwd_tile_bytes() { return C * C * C * 4; }
+template <int C>
+__host__ __device__ constexpr int fwd_win_offset() {
+  return ((fwd_tile_bytes<C>() + C * C + 16 + 127) / 128) * 128;
+}
+
+template <int C, int S>
+__global__ void __launch_bounds__(256, 2)
+    fwd_cube_kernel(const __grid_constant__ CUtensorMap p0map, const FwdParams P) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  float* tile = reinterpret_cast<float*>(smem);
+  uint8_t* rowflag = smem + fwd_tile_bytes<C>();
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + ((fwd_tile_bytes<C>() + C * C + 7) / 8) * 8);
+  float* win = reinterpret_cast<float*>(smem + fwd_win_offset<C>());
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int nwarps = blockDim.x >> 5;
+  const int c = blockIdx.x;
+  const int ncubes = gridDim.x;
+  const int cx = c % P.ncx, cy = (c / P.ncx) % P.ncy, cz = c / (P.ncx * P.ncy);
+  const int fl = blockIdx.y, f = P.f_begin + fl;
+  const int j = (blockIdx.z * nwarps + warp) * kWarp + lane;
+  const bool valid = j < P.E;
+  const int jj = valid ? j : P.E - 1;
+
+  // 1. stage the p0 cube (zero outside the grid)
+  if (P.use_tma) {
+    if (tid == 0) {
+      mbar_init(bar, 1);
+      fence_mbar_init();
+    }
+    __syncthreads();
+    if (tid == 0) {
+      mbar_arrive_expect_tx(bar, fwd_tile_bytes<C>());
+      tma_load_3d(tile, &p0map, bar, cx * C, cy * C, cz * C);
+    }
+  } else {
+    for (int k = tid; k < C * C * C; k += blockDim.x) {
+      const int lx = k % C, ly = (k / C) % C, lz = k / (C * C);
+      const int ix = cx * C + lx, iy = cy * C + ly, iz = cz * C + lz;
+      float v = 0.f;
+      if (ix < P.nx && iy < P.ny && iz < P.nz)
+        v = load_elem(P.p0, (static_cast<int64_t>(iz) * P.ny + iy) * P.nx + ix, P.dtype_vol);
+      tile[k] = v;
+    }
+  }
+
+  // 2. zero this lane's window column
+  float* col = win + warp * P.W * kWarp + lane;
+  for (int k = 0; k < P.W; ++k) col[k * kWarp] = 0.f;
+
+  // 3. per-(cube, element) reference in FP64
+  const double* xp = P.xw + (static_cast<int64_t>(f) * P.E + jj) * 3;
+  const double hc = 0.5 * (C - 1);
+  const PairRef R = make_ref(xp[0], xp[1], xp[2], P.ox + P.dx * (cx * C + hc), P.oy + P.dy * (cy * C + hc),
+                             P.oz + P.dz * (cz * C + hc), P.a0, P.tau0, P.inv_h);
+  const int nb_rel = static_cast<int>(floorf(R.phim - P.nb_shift)) - 1;
+  const float dxf = static_cast<float>(P.dx), dyf = static_cast<float>(P.dy), dzf = static_cast<float>(P.dz);
+  float Pix[C];
+#pragma unroll
+  for (int ix = 0; ix < C; ++ix) {
+    const float qx = (ix - 0.5f * (C - 1)) * dxf;
+    Pix[ix] = qx * (qx + R.m2ux);
+  }
+
+  // 4. wait for the tile; flag rows that hold any nonzero voxel
+  bool ok = true;
+  if (P.use_tma) ok = mbar_wait_bounded(bar, 0, P.status);
+  if (__syncthreads_or(!ok)) {
+    if (tid == 0) mbar_wait_bounded(bar, 0, P.status);  // let the copy land before exit
+    return;
+  }
+  for (int r = tid; r < C * C; r += blockDim.x) {
+    bool nz = false;
+#pragma unroll
+    for (int ix = 0; ix < C; ++ix) nz |= tile[r * C + ix] != 0.f;
+    rowflag[r] = nz ? 1 : 0;
+  }
+  __syncthreads();
+
+  // 5. pair loop: every voxel of the cube against this lane's element
+  const unsigned max_idx = static_cast<unsigned>(P.W - S);
+  bool clamped = false;
+  for (int lz = 0; lz < C; ++lz) {
+    const float qz = (lz - 0.5f * (C - 1)) * dzf;
+    const float Cz = qz * (qz + R.m2uz);
+    for (int ly = 0; ly < C; ++ly) {
+      if (!rowflag[lz * C + ly]) continue;
+      const float qy = (ly - 0.5f * (C - 1)) * dyf;
+      const float Crow = fmaf(qy, qy + R.m2uy, Cz);
+      const float* prow = tile + (lz * C + ly) * C;
+#pragma unroll
+      for (int i4 = 0; i4 < C; i4 += 4) {
+        const float4 pv4 = *reinterpret_cast<const float4*>(prow + i4);
+        const float pv[4] = {pv4.x, pv4.y, pv4.z, pv4.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const PairMath m = pair_math(Pix[i4 + u] + Crow, R.dc2, R.dcf, R.phim, P.inv_hf, P.h, P.cb);
+          unsigned idx = static_cast<unsigned>(m.nsi - nb_rel);
+          clamped |= idx > max_idx;
+          idx = min(idx, max_idx);
+          float* slot = col + idx * kWarp;
+          const float s = pv[u] * m.rs;
+          float beta = m.beta0;
+          float bprev = P.a0sq;
+#pragma unroll
+          for (int k = 0; k < S; ++k) {
+            float bk;
+            if (k == S - 1) {
+              bk = P.a0sq;
+            } else {
+              beta += P.h;
+              const float bc = (k == S - 2) ? fminf(beta, P.a0f) : beta;
+              bk = bc * bc;
+            }
+            slot[k * kWarp] = fmaf(s, bprev - bk, slot[k * kWarp]);
+            bprev = bk;
+          }
+        }
+      }
+    }
+  }
+  if (clamped) atomicOr(P.status, PASFM_STATUS_INDEX_CLAMPED);
+
+  // 6. flush the window as this cube's partial trace (scaled by 1 / (4 h))
+  __syncwarp();
+  if (valid) {
+    const int64_t row = static_cast<int64_t>(fl) * P.E + j;
+    float* dst = P.part + (row * ncubes + c) * P.W;
+    for (int k = 0; k < P.W; k += 4) {
+      float4 v;
+      v.x = col[(k + 0) * kWarp] * P.p0_scale;
+      v.y = col[(k + 1) * kWarp] * P.p0_scale;
+      v.z = col[(k + 2) * kWarp] * P.p0_scale;
+      v.w = col[(k + 3) * kWarp] * P.p0_scale;
+      *reinterpret_cast<float4*>(dst + k) = v;
+    }
+    P.n0tab[row * ncubes + c] = R.Nc + nb_rel;
+  }
+}
+
+// ------------------------------------------------------------------------
+// backward (adjoint gather + pose-gradient reduction)
+// ------------------------------------------------------------------------
+constexpr int kBatch = 32;  // traces staged per batch
+
+template <int C>
+struct BwdLayout {
+  static constexpr int NT = C * C;
+  static constexpr int NW = NT / kWarp;
+  // offsets in bytes, given the staged window length WP (floats)
+  __host__ __device__ static int win_bytes(int WP) { return 2 * kBatch * WP * 4; }
+  __host__ __device__ static int refa_off(int WP) { return win_bytes(WP); }
+  __host__ __device__ static int refb_off(int WP) { return refa_off(WP) + 2 * kBatch * 16; }
+  __host__ __device__ static int refu_off(int WP) { return refb_off(WP) + 2 * kBatch * 16; }
+  __host__ __device__ static int red_off(int WP) { return refu_off(WP) + 2 * kBatch * 24; }
+  __host__ __device__ static int bar_off(int WP) { return red_off(WP) + NW * kBatch * 16; }
+  __host__ __device__ static int total(int WP) { return bar_off(WP) + 16; }
+};
+
+template <int C>
+__device__ __forceinline__ void bwd_thread_row(int tid, int& ty, int& tz) {
+  const int w = tid >> 5, l = tid & 31;
+  if (C == 16) {  // a warp covers 4 (y) x 8 (z) rows
+    ty = 4 * (w & 3) + (l & 3);
+    tz = 8 * (w >> 2) + (l >> 2);
+  } else {        // C == 8: a warp covers 8 (y) x 4 (z) rows
+    ty = l & 7;
+    tz = 4 * w + (l >> 3);
+  }
+}
+
+template <int C, int S, bool ADJ, bool POSE>
+__global__ void __launch_bounds__(C* C, (C == 16 ? 2 : 8))
+    bwd_cube_kernel(const __grid_constant__ CUtensorMap gmap, const BwdParams P) {
+  using L = BwdLayout<C>;
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int WP = P.WP;
+  float* win = reinterpret_cast<float*>(smem);
+  float4* refa = reinterpret_cast<float4*>(smem + L::refa_off(WP));
+  float4* refb = reinterpret_cast<float4*>(smem + L::refb_off(WP));
+  double* refu = reinterpret_cast<double*>(smem + L::refu_off(WP));
+  float4* red = reinterpret_cast<float4*>(smem + L::red_off(WP));
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L::bar_off(WP));
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int c = blockIdx.x, ncubes = gridDim.x;
+  const int cx = c % P.ncx, cy = (c / P.ncx) % P.ncy, cz = c / (P.ncx * P.ncy);
+  int ty, tz;
+  bwd_thread_row<C>(tid, ty, tz);
+  const int iy = cy * C + ty, iz = cz * C + tz;
+  const bool row_in = iy < P.ny && iz < P.nz;
+
+  const float dxf = static_cast<float>(P.dx);
+  const float qy = (ty - 0.5f * (C - 1)) * static_cast<float>(P.dy);
+  const float qz = (tz - 0.5f * (C - 1)) * static_cast<float>(P.dz);
+  float qx[C];
+#pragma unroll
+  for (int k = 0; k < C; ++k) qx[k] = (k - 0.5f * (C - 1)) * dxf;
+
+  float p0s[POSE ? C : 1];
+  if (POSE) {
+#pragma unroll
+    for (int k = 0; k < C; ++k) {
+      const int ix = cx * C + k;
+      p0s[k] = (row_in && ix < P.nx)
+                   ? load_elem(P.p0, (static_cast<int64_t>(iz) * P.ny + iy) * P.nx + ix, P.dtype_vol) * P.scale
+                   : 0.f;
+    }
+  }
+  float acc[ADJ ? C : 1], comp[ADJ ? C : 1], bacc[ADJ ? C : 1];
+  if (ADJ) {
+#pragma unroll
+    for (int k = 0; k < C; ++k) acc[k] = comp[k] = bacc[k] = 0.f;
+  }
+
+  const double hc = 0.5 * (C - 1);
+  const double rcx = P.ox + P.dx * (cx * C + hc), rcy = P.oy + P.dy * (cy * C + hc),
+               rcz = P.oz + P.dz * (cz * C + hc);
+  const int nb = (P.n_items + kBatch - 1) / kBatch;
+
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+
+  // producer: warp 0 stages batch b into buffer buf
+  auto issue = [&](int b, int buf) {
+    const int it = b * kBatch + lane;
+    const int cnt = min(kBatch, P.n_items - b * kBatch);
+    float* wdst = win + (buf * kBatch + lane) * WP;
+    int x0 = 0, row = 0;
+    if (it < P.n_items) {
+      const int fl = it / P.E, j = it % P.E;
+      const int f = P.f_begin + fl;
+      row = f * P.E + j;
+      const double* xp = P.xw + static_cast<int64_t>(row) * 3;
+      const PairRef R = make_ref(xp[0], xp[1], xp[2], rcx, rcy, rcz, P.a0, P.tau0, P.inv_h);
+      const int n0 = R.Nc + static_cast<int>(floorf(R.phim - P.nb_shift)) - 1;
+      x0 = n0 & ~3;
+      const float mk = (POSE && P.mask) ? (P.mask[row] ? 1.f : 0.f) : 1.f;
+      refa[buf * kBatch + lane] = make_float4(R.m2ux, R.m2uy, R.m2uz, R.dc2);
+      refb[buf * kBatch + lane] = make_float4(R.dcf, R.phim, __int_as_float(R.Nc - x0), mk);
+      if (POSE) {
+        refu[(buf * kBatch + lane) * 3 + 0] = R.ux;
+        refu[(buf * kBatch + lane) * 3 + 1] = R.uy;
+        refu[(buf * kBatch + lane) * 3 + 2] = R.uz;
+      }
+      if (!P.use_tma) {  // plain loads with zero fill outside [0, Nt)
+        const int64_t base = static_cast<int64_t>(row) * P.Nt;
+        for (int k = 0; k < WP; ++k) {
+          const int n = x0 + k;
+          wdst[k] = (n >= 0 && n < P.Nt) ? load_elem(P.g, base + n, P.dtype_sig) : 0.f;
+        }
+      }
+    }
+    if (P.use_tma) {
+      if (lane == 0) mbar_arrive_expect_tx(&bar[buf], static_cast<uint32_t>(cnt * WP * 4));
+      __syncwarp();
+      if (it < P.n_items) tma_load_2d(wdst, &gmap, &bar[buf], x0, row);
+    } else {
+      __threadfence_block();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&bar[buf]);
+    }
+  };
+
+  if (warp == 0) {
+    issue(0, 0);
+    if (nb > 1) issue(1, 1);
+  }
+
+  const unsigned max_idx = static_cast<unsigned>(WP - S);
+  bool clamped = false;
+  for (int b = 0; b < nb; ++b) {
+    const int buf = b & 1;
+    const bool ok = mbar_wait_bounded(&bar[buf], (b >> 1) & 1, P.status);
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) {  // let copies in flight land before the CTA exits
+        mbar_wait_bounded(&bar[buf], (b >> 1) & 1, P.status);
+        if (b + 1 < nb) mbar_wait_bounded(&bar[buf ^ 1], ((b + 1) >> 1) & 1, P.status);
+      }
+      return;
+    }
+    const int cnt = min(kBatch, P.n_items - b * kBatch);
+    const float* wb = win + buf * kBatch * WP;
+    for (int e = 0; e < cnt; ++e) {
+      const float4 ra = refa[buf * kBatch + e];
+      const float4 rb = refb[buf * kBatch + e];
+      const int offs = __float_as_int(rb.z);
+      const float* wv = wb + e * WP;
+      const float Crow = fmaf(qy, qy + ra.y, qz * (qz + ra.z));
+      float R0 = 0.f, R1 = 0.f;
+#pragma unroll
+      for (int k = 0; k < C; ++k) {
+        const float A = fmaf(qx[k], qx[k] + ra.x, Crow);
+        const PairMath m = pair_math(A, ra.w, rb.x, rb.y, P.inv_hf, P.h, P.cb);
+        unsigned idx = static_cast<unsigned>(m.nsi + offs);
+        clamped |= idx > max_idx;
+        idx = min(idx, max_idx);
+        float g[S];
+#pragma unroll
+        for (int s = 0; s < S; ++s) g[s] = wv[idx + s];
+        float beta = m.beta0;
+        float S1 = P.a0sq * (g[0] - g[S - 1]);
+        float S2 = 0.f;
+#pragma unroll
+        for (int s = 1; s < S; ++s) {
+          beta += P.h;
+          const float dg = g[s] - g[s - 1];
+          const float bc = (s == S - 1) ? fminf(beta, P.a0f) : beta;
+          S1 = fmaf(bc * bc, dg, S1);
+          if (POSE) {
+            const float D = (s == S - 1) ? (beta < P.a0f ? beta : 0.f) : beta;
+            S2 = fmaf(-D, dg, S2);
+          }
+        }
+        const float t1 = m.rs * S1;
+        if (ADJ) bacc[k] += t1;
+        if (POSE) {
+          const float coef = p0s[k] * (m.rs * m.rs) * fmaf(2.f, S2, -t1);
+          R0 += coef;
+          R1 = fmaf(coef, qx[k], R1);
+        }
+      }
+      if (POSE) {
+        float R2 = qy * R0, R3 = qz * R0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          R0 += __shfl_xor_sync(0xffffffffu, R0, o);
+          R1 += __shfl_xor_sync(0xffffffffu, R1, o);
+          R2 += __shfl_xor_sync(0xffffffffu, R2, o);
+          R3 += __shfl_xor_sync(0xffffffffu, R3, o);
+        }
+        if (lane == 0) red[warp * kBatch + e] = make_float4(R0, R1, R2, R3);
+      }
+    }
+    if (ADJ) {  // fold the batch into a compensated per-voxel sum
+#pragma unroll
+      for (int k = 0; k < C; ++k) {
+        const float y = bacc[k] - comp[k];
+        const float t = acc[k] + y;
+        comp[k] = (t - acc[k]) - y;
+        acc[k] = t;
+        bacc[k] = 0.f;
+      }
+    }
+    __syncthreads();
+    if (POSE && tid < cnt) {
+      double r0 = 0.0, r1 = 0.0, r2 = 0.0, r3 = 0.0;
+      for (int w = 0; w < L::NW; ++w) {
+        const float4 v = red[w * kBatch + tid];
+        r0 += v.x;
+        r1 += v.y;
+        r2 += v.z;
+        r3 += v.w;
+      }
+      const float mk = refb[buf * kBatch + tid].w;
+      const double* u = refu + (buf * kBatch + tid) * 3;
+      double* gp = P.gpart + (static_cast<int64_t>(b * kBatch + tid) * ncubes + c) * 3;
+      gp[0] = mk * (u[0] * r0 - r1);
+      gp[1] = mk * (u[1] * r0 - r2);
+      gp[2] = mk * (u[2] * r0 - r3);
+    }
+    __syncthreads();
+    if (warp == 0 && b + 2 < nb) issue(b + 2, buf);
+  }
+  if (clamped) atomicOr(P.status, PASFM_STATUS_INDEX_CLAMPED);
+
+  if (ADJ && row_in) {
+    float* out = P.vol + (static_cast<int64_t>(iz) * P.ny + iy) * P.nx;
+#pragma unroll
+    for (int k = 0; k < C; ++k) {
+      const int ix = cx * C + k;
+      if (ix < P.nx) {
+        const float v = (acc[k] - comp[k]) * P.scale;
+        out[ix] = P.accumulate ? out[ix] + v : v;
+      }
+    }
+  }
+}
+
+}  // namespace pasfm

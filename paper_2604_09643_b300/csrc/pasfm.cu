@@ -1,0 +1,774 @@
+// Host side of libpasfm: the C ABI declared in include/pasfm.h.
+//
+// Planning (cube size, sample slots, window lengths, frame chunks), workspace
+// ownership, TMA descriptor encoding, launch sequencing on the caller's stream,
+// argument validation and per-launch CUDA-event timing.  Every compute step of
+// the operator runs in the kernels of kernels.cuh / aux.cu; nothing here
+// touches array contents on the host.
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "aux.cuh"
+#include "kernels.cuh"
+
+using namespace pasfm;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+#define CUDA_TRY(expr)                                                                        \
+  do {                                                                                        \
+    cudaError_t e_ = (expr);                                                                  \
+    if (e_ != cudaSuccess) return fail(PASFM_ECUDA, "%s: %s", #expr, cudaGetErrorString(e_)); \
+  } while (0)
+
+#define TRY(expr)                  \
+  do {                             \
+    int r_ = (expr);               \
+    if (r_ != PASFM_OK) return r_; \
+  } while (0)
+
+struct Buf {
+  void* p = nullptr;
+  size_t n = 0;
+};
+
+struct Rec {
+  const char* name;
+  cudaEvent_t a, b;
+};
+
+const FwdLaunch kFwd[kMaxS + 1] = {nullptr,        nullptr,        fwd_launch_s2,  fwd_launch_s3,
+                                   fwd_launch_s4,  fwd_launch_s5,  fwd_launch_s6,  fwd_launch_s7,
+                                   fwd_launch_s8,  fwd_launch_s9,  fwd_launch_s10, fwd_launch_s11,
+                                   fwd_launch_s12, fwd_launch_s13, fwd_launch_s14, fwd_launch_s15,
+                                   fwd_launch_s16};
+const BwdLaunch kBwd[kMaxS + 1] = {nullptr,        nullptr,        bwd_launch_s2,  bwd_launch_s3,
+                                   bwd_launch_s4,  bwd_launch_s5,  bwd_launch_s6,  bwd_launch_s7,
+                                   bwd_launch_s8,  bwd_launch_s9,  bwd_launch_s10, bwd_launch_s11,
+                                   bwd_launch_s12, bwd_launch_s13, bwd_launch_s14, bwd_launch_s15,
+                                   bwd_launch_s16};
+
+constexpr size_t kDefaultPartialBudget = size_t(4) << 30;
+constexpr int kFwdWmax16 = 128;  // forward window cap for 16^3 cubes (8 warps x W x 128 B)
+constexpr int kFwdWmax8 = 200;   // forward window cap for 8^3 cubes
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    cudaGetLastError();
+  });
+  return fn;
+}
+
+struct Geo {  // validated geometry with defaults applied
+  pasfm_geom g;
+  double a0;
+  int64_t nvox;
+  int64_t n_rows;  // F * E
+};
+
+int check_geom(const pasfm_geom* g, Geo* out) {
+  if (!g) return fail(PASFM_EINVAL, "geom is NULL");
+  if (g->nx < 0 || g->ny < 0 || g->nz < 0 || g->n_elem < 0 || g->n_frames < 0 || g->n_samples < 0)
+    return fail(PASFM_EINVAL, "negative size in geom");
+  if (!(g->dx > 0) || !(g->dy > 0) || !(g->dz > 0)) return fail(PASFM_EINVAL, "voxel spacing must be > 0");
+  if (!(g->fs_mhz > 0) || !(g->c_mm_per_us > 0)) return fail(PASFM_EINVAL, "fs and c must be > 0");
+  if (!std::isfinite(g->t0_us) || !std::isfinite(g->ox) || !std::isfinite(g->oy) || !std::isfinite(g->oz))
+    return fail(PASFM_EINVAL, "non-finite origin or t0");
+  for (int d : {g->dtype_vol, g->dtype_sig})
+    if (d != PASFM_F32 && d != PASFM_BF16 && d != PASFM_F16) return fail(PASFM_EINVAL, "unknown dtype %d", d);
+  out->g = *g;
+  out->a0 = g->a0_mm > 0 ? g->a0_mm : 0.5 * std::min(g->dx, std::min(g->dy, g->dz));
+  out->nvox = int64_t(g->nx) * g->ny * g->nz;
+  out->n_rows = int64_t(g->n_frames) * g->n_elem;
+  if (out->n_rows > INT32_MAX / 2) return fail(PASFM_EUNSUPPORTED, "F * E too large");
+  return PASFM_OK;
+}
+
+int make_plan(const Geo& G, Plan* pl) {
+  const pasfm_geom& g = G.g;
+  pl->h = g.c_mm_per_us / g.fs_mhz;
+  pl->inv_h = 1.0 / pl->h;
+  pl->tau0 = g.c_mm_per_us * g.t0_us;
+  const double L = 2.0 * G.a0 / pl->h;
+  pl->S = static_cast<int>(std::floor(L)) + 2;
+  if (pl->S > kMaxS)
+    return fail(PASFM_EUNSUPPORTED, "a0 / h = %.3f: a pair spans %d samples, more than the %d compiled", L / 2,
+                pl->S, kMaxS);
+  const double diag = std::sqrt(g.dx * g.dx + g.dy * g.dy + g.dz * g.dz);
+  auto window = [&](int C) {
+    const double rho = 0.5 * (C - 1) * diag;
+    int W = static_cast<int>(std::ceil(2.0 * rho / pl->h)) + pl->S + 3;
+    return (W + 3) & ~3;
+  };
+  int C = 16, W = window(16);
+  if (W > kFwdWmax16) {
+    C = 8;
+    W = window(8);
+    if (W > kFwdWmax8)
+      return fail(PASFM_EUNSUPPORTED, "voxel spacing %.3g mm spans too many samples (window %d)", diag, W);
+  }
+  pl->C = C;
+  pl->W = W;
+  pl->rho = 0.5 * (C - 1) * diag;
+  pl->nb_shift = static_cast<float>(pl->rho / pl->h);
+  pl->WP = ((W + 4) + 31) & ~31;
+  pl->ncx = (g.nx + C - 1) / C;
+  pl->ncy = (g.ny + C - 1) / C;
+  pl->ncz = (g.nz + C - 1) / C;
+  pl->ncubes = pl->ncx * pl->ncy * pl->ncz;
+  pl->fwd_warps = std::max(1, std::min(8, (g.n_elem + 31) / 32));
+  pl->n_egroups = std::max(1, (g.n_elem + 32 * pl->fwd_warps - 1) / (32 * pl->fwd_warps));
+  return PASFM_OK;
+}
+
+size_t fwd_per_frame(const Geo& G, const Plan& pl) {
+  return size_t(G.g.n_elem) * pl.ncubes * (size_t(pl.W) * 4 + 4);
+}
+size_t bwd_per_frame(const Geo& G, const Plan& pl) { return size_t(G.g.n_elem) * pl.ncubes * 24; }
+
+int frames_per_chunk(size_t per_frame, size_t budget, int F) {
+  if (per_frame == 0) return std::max(F, 1);
+  size_t k = budget / per_frame;
+  if (k < 1) k = 1;
+  return static_cast<int>(std::min<size_t>(k, std::max(F, 1)));
+}
+
+}  // namespace
+
+struct pasfm_ctx {
+  int device = 0;
+  unsigned* status = nullptr;
+  Buf xw, part, n0, gres, vgrad, gpart, G, grad6, lpart, lscalar;
+  size_t budget = kDefaultPartialBudget;
+  bool timing = false;
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> pool;
+  int64_t launches = 0;
+
+  int ensure(Buf& b, size_t bytes) {
+    if (b.n >= bytes) return PASFM_OK;
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.n = 0;
+    if (bytes == 0) return PASFM_OK;
+    if (cudaMalloc(&b.p, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      b.p = nullptr;
+      return fail(PASFM_ENOMEM, "workspace allocation of %zu bytes failed", bytes);
+    }
+    b.n = bytes;
+    return PASFM_OK;
+  }
+  cudaEvent_t event() {
+    if (!pool.empty()) {
+      cudaEvent_t e = pool.back();
+      pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+  }
+  // begin/end bracket one kernel launch for timing and launch counting
+  cudaEvent_t begin(cudaStream_t st) {
+    ++launches;
+    if (!timing) return nullptr;
+    cudaEvent_t a = event();
+    cudaEventRecord(a, st);
+    return a;
+  }
+  void end(const char* name, cudaEvent_t a, cudaStream_t st) {
+    if (!a) return;
+    cudaEvent_t b = event();
+    cudaEventRecord(b, st);
+    recs.push_back({name, a, b});
+  }
+};
+
+namespace {
+
+int check_launch(const char* what) {
+  cudaError_t e = cudaPeekAtLastError();
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(PASFM_ECUDA, "%s launch failed: %s", what, cudaGetErrorString(e));
+  }
+  return PASFM_OK;
+}
+
+int set_device(pasfm_ctx* ctx) {
+  int cur = -1;
+  CUDA_TRY(cudaGetDevice(&cur));
+  if (cur != ctx->device) CUDA_TRY(cudaSetDevice(ctx->device));
+  return PASFM_OK;
+}
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+// A1: element positions into `out`.
+int run_elem_pos(pasfm_ctx* ctx, const Geo& G, const double* elem, const double* pose, double* out,
+                 cudaStream_t st) {
+  const pasfm_geom& g = G.g;
+  const int64_t n = G.n_rows;
+  if (n == 0) return PASFM_OK;
+  const double lox = g.ox, loy = g.oy, loz = g.oz;
+  const double hix = g.ox + g.dx * std::max(g.nx - 1, 0), hiy = g.oy + g.dy * std::max(g.ny - 1, 0),
+               hiz = g.oz + g.dz * std::max(g.nz - 1, 0);
+  // an empty grid has no voxel an element could be inside
+  const double a0chk = G.nvox > 0 ? G.a0 : -1.0;
+  cudaEvent_t t = ctx->begin(st);
+  elem_pos_kernel<<<static_cast<unsigned>((n + 255) / 256), 256, 0, st>>>(
+      elem, pose, out, g.n_frames, g.n_elem, lox, loy, loz, hix, hiy, hiz, a0chk, ctx->status);
+  ctx->end("elem_pos", t, st);
+  return check_launch("elem_pos");
+}
+
+// Forward over all frames: per-cube kernels then the ordered reduction.
+// Writes sig_out (may be null) and/or the masked residual g_out with loss.
+int run_forward(pasfm_ctx* ctx, const Geo& G, const Plan& pl, const void* p0, const double* xw, float* sig_out,
+                float* g_out, const void* meas, const uint8_t* mask, double* loss_out, cudaStream_t st) {
+  const pasfm_geom& g = G.g;
+  const int F = g.n_frames, E = g.n_elem, Nt = g.n_samples;
+  const int Fc = frames_per_chunk(fwd_per_frame(G, pl), ctx->budget, F);
+  TRY(ctx->ensure(ctx->part, size_t(Fc) * E * pl.ncubes * pl.W * 4));
+  TRY(ctx->ensure(ctx->n0, size_t(Fc) * E * pl.ncubes * 4));
+  const int n_chunks = (F + Fc - 1) / Fc;
+  const int blocks_total = static_cast<int>((G.n_rows + 7) / 8) + n_chunks;
+  if (g_out) {
+    TRY(ctx->ensure(ctx->lpart, size_t(blocks_total) * 8));
+    TRY(ctx->ensure(ctx->lscalar, 8));
+  }
+
+  CUtensorMap map;
+  std::memset(&map, 0, sizeof map);
+  int use_tma = 0;
+  auto enc = encode_fn();
+  if (enc && g.dtype_vol == PASFM_F32 && g.nx % 4 == 0 && aligned16(p0)) {
+    cuuint64_t dims[3] = {cuuint64_t(g.nx), cuuint64_t(g.ny), cuuint64_t(g.nz)};
+    cuuint64_t strides[2] = {cuuint64_t(g.nx) * 4, cuuint64_t(g.nx) * g.ny * 4};
+    cuuint32_t box[3] = {cuuint32_t(pl.C), cuuint32_t(pl.C), cuuint32_t(pl.C)};
+    cuuint32_t es[3] = {1, 1, 1};
+    if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(p0), dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS)
+      use_tma = 1;
+  }
+
+  FwdParams P{};
+  P.xw = xw;
+  P.p0 = p0;
+  P.part = static_cast<float*>(ctx->part.p);
+  P.n0tab = static_cast<int*>(ctx->n0.p);
+  P.dtype_vol = g.dtype_vol;
+  P.nx = g.nx;
+  P.ny = g.ny;
+  P.nz = g.nz;
+  P.ncx = pl.ncx;
+  P.ncy = pl.ncy;
+  P.E = E;
+  P.W = pl.W;
+  P.ox = g.ox;
+  P.oy = g.oy;
+  P.oz = g.oz;
+  P.dx = g.dx;
+  P.dy = g.dy;
+  P.dz = g.dz;
+  P.tau0 = pl.tau0;
+  P.inv_h = pl.inv_h;
+  P.a0 = G.a0;
+  P.h = static_cast<float>(pl.h);
+  P.a0f = static_cast<float>(G.a0);
+  P.a0sq = P.a0f * P.a0f;
+  P.nb_shift = pl.nb_shift;
+  P.p0_scale = static_cast<float>(0.25 / pl.h);
+  P.inv_hf = static_cast<float>(pl.inv_h);
+  P.cb = static_cast<float>(-G.a0 - 0.5 * pl.h);
+  P.use_tma = use_tma;
+  P.status = ctx->status;
+
+  const int threads = 32 * pl.fwd_warps;
+  const size_t smem = size_t(pl.C == 16 ? fwd_win_offset<16>() : fwd_win_offset<8>()) +
+                      size_t(pl.fwd_warps) * pl.W * 32 * 4;
+  const size_t rsmem = size_t(8) * kRedChunk * 4;
+  CUDA_TRY(cudaFuncSetAttribute(fwd_reduce_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                static_cast<int>(rsmem)));
+  int loss_off = 0;
+  for (int fb = 0; fb < F; fb += Fc) {
+    const int fc = std::min(Fc, F - fb);
+    P.f_begin = fb;
+    dim3 grid(pl.ncubes, fc, pl.n_egroups);
+    cudaEvent_t t = ctx->begin(st);
+    cudaError_t e = kFwd[pl.S](pl.C, map, P, grid, threads, smem, st);
+    ctx->end("fwd_cube", t, st);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(PASFM_ECUDA, "fwd_cube launch: %s", cudaGetErrorString(e));
+    }
+
+    RedParams R{};
+    R.part = P.part;
+    R.n0tab = P.n0tab;
+    R.E = E;
+    R.f_begin = fb;
+    R.n_rows = fc * E;
+    R.ncubes = pl.ncubes;
+    R.W = pl.W;
+    R.Nt = Nt;
+    R.sig_out = sig_out;
+    R.g_out = g_out;
+    R.meas = meas;
+    R.dtype_sig = g.dtype_sig;
+    R.mask = mask;
+    R.loss_part = g_out ? static_cast<double*>(ctx->lpart.p) : nullptr;
+    R.loss_offset = loss_off;
+    const int rblocks = (R.n_rows + 7) / 8;
+    t = ctx->begin(st);
+    fwd_reduce_kernel<<<rblocks, 256, rsmem, st>>>(R);
+    ctx->end("fwd_reduce", t, st);
+    TRY(check_launch("fwd_reduce"));
+    loss_off += rblocks;
+  }
+  if (g_out) {
+    double* dst = loss_out ? loss_out : static_cast<double*>(ctx->lscalar.p);
+    cudaEvent_t t = ctx->begin(st);
+    sum_kernel<<<1, 256, 0, st>>>(static_cast<double*>(ctx->lpart.p), loss_off, dst);
+    ctx->end("loss_sum", t, st);
+    TRY(check_launch("loss_sum"));
+  }
+  return PASFM_OK;
+}
+
+// Backward: mode 1 adjoint into vol, 2 pose gradient into G rows, 3 both.
+int run_backward(pasfm_ctx* ctx, const Geo& G, const Plan& pl, int mode, const void* p0, const double* xw,
+                 const void* gsig, int dtype_sig, const uint8_t* mask, float* vol, double* Gout,
+                 cudaStream_t st) {
+  const pasfm_geom& g = G.g;
+  const int F = g.n_frames, E = g.n_elem, Nt = g.n_samples;
+  const bool pose = mode & 2;
+  const int Fc = pose ? frames_per_chunk(bwd_per_frame(G, pl), ctx->budget, F) : std::max(F, 1);
+  if (pose) TRY(ctx->ensure(ctx->gpart, size_t(Fc) * E * pl.ncubes * 24));
+
+  CUtensorMap map;
+  std::memset(&map, 0, sizeof map);
+  int use_tma = 0;
+  auto enc = encode_fn();
+  if (enc && dtype_sig == PASFM_F32 && Nt % 4 == 0 && aligned16(gsig) && pl.WP <= 256) {
+    cuuint64_t dims[2] = {cuuint64_t(Nt), cuuint64_t(G.n_rows)};
+    cuuint64_t strides[1] = {cuuint64_t(Nt) * 4};
+    cuuint32_t box[2] = {cuuint32_t(pl.WP), 1};
+    cuuint32_t es[2] = {1, 1};
+    if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(gsig), dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS)
+      use_tma = 1;
+  }
+
+  BwdParams P{};
+  P.xw = xw;
+  P.p0 = p0;
+  P.g = gsig;
+  P.mask = mask;
+  P.vol = vol;
+  P.gpart = static_cast<double*>(ctx->gpart.p);
+  P.dtype_vol = g.dtype_vol;
+  P.dtype_sig = dtype_sig;
+  P.nx = g.nx;
+  P.ny = g.ny;
+  P.nz = g.nz;
+  P.ncx = pl.ncx;
+  P.ncy = pl.ncy;
+  P.E = E;
+  P.Nt = Nt;
+  P.WP = pl.WP;
+  P.ox = g.ox;
+  P.oy = g.oy;
+  P.oz = g.oz;
+  P.dx = g.dx;
+  P.dy = g.dy;
+  P.dz = g.dz;
+  P.tau0 = pl.tau0;
+  P.inv_h = pl.inv_h;
+  P.a0 = G.a0;
+  P.h = static_cast<float>(pl.h);
+  P.a0f = static_cast<float>(G.a0);
+  P.a0sq = P.a0f * P.a0f;
+  P.nb_shift = pl.nb_shift;
+  P.scale = static_cast<float>(0.25 / pl.h);
+  P.inv_hf = static_cast<float>(pl.inv_h);
+  P.cb = static_cast<float>(-G.a0 - 0.5 * pl.h);
+  P.use_tma = use_tma;
+  P.status = ctx->status;
+  const size_t smem = pl.C == 16 ? BwdLayout<16>::total(pl.WP) : BwdLayout<8>::total(pl.WP);
+
+  for (int fb = 0; fb < F; fb += Fc) {
+    const int fc = std::min(Fc, F - fb);
+    P.f_begin = fb;
+    P.n_items = fc * E;
+    P.accumulate = fb > 0;
+    cudaEvent_t t = ctx->begin(st);
+    cudaError_t e = kBwd[pl.S](pl.C, mode, map, P, dim3(pl.ncubes), smem, st);
+    ctx->end("bwd_cube", t, st);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(PASFM_ECUDA, "bwd_cube launch: %s", cudaGetErrorString(e));
+    }
+    if (pose) {
+      const int rows = fc * E;
+      t = ctx->begin(st);
+      pose_rows_kernel<<<(rows + 7) / 8, 256, 0, st>>>(P.gpart, pl.ncubes, rows, int64_t(fb) * E, Gout);
+      ctx->end("pose_rows", t, st);
+      TRY(check_launch("pose_rows"));
+    }
+  }
+  return PASFM_OK;
+}
+
+int run_grad6(pasfm_ctx* ctx, const Geo& G, const double* xw, const double* Gm, double* grad6, cudaStream_t st) {
+  if (G.g.n_frames == 0) return PASFM_OK;
+  cudaEvent_t t = ctx->begin(st);
+  grad6_kernel<<<G.g.n_frames, 256, 0, st>>>(xw, Gm, G.g.n_elem, grad6);
+  ctx->end("grad6", t, st);
+  return check_launch("grad6");
+}
+
+int prepare(pasfm_ctx* ctx, const pasfm_geom* geom, Geo* G, Plan* pl) {
+  if (!ctx) return fail(PASFM_EINVAL, "ctx is NULL");
+  TRY(check_geom(geom, G));
+  TRY(make_plan(*G, pl));
+  TRY(set_device(ctx));
+  return PASFM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pasfm_abi_version(void) { return 1; }
+
+const char* pasfm_last_error(void) { return g_err.c_str(); }
+
+int pasfm_create(pasfm_ctx** out, int device) {
+  if (!out) return fail(PASFM_EINVAL, "out is NULL");
+  *out = nullptr;
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) {
+    cudaGetLastError();
+    return fail(PASFM_ECUDA, "CUDA device %d is not available (%d visible)", device, n);
+  }
+  CUDA_TRY(cudaSetDevice(device));
+  pasfm_ctx* ctx = new pasfm_ctx();
+  ctx->device = device;
+  if (cudaMalloc(&ctx->status, sizeof(unsigned)) != cudaSuccess ||
+      cudaMemset(ctx->status, 0, sizeof(unsigned)) != cudaSuccess) {
+    cudaGetLastError();
+    delete ctx;
+    return fail(PASFM_ECUDA, "status word allocation failed");
+  }
+  *out = ctx;
+  return PASFM_OK;
+}
+
+int pasfm_destroy(pasfm_ctx* ctx) {
+  if (!ctx) return PASFM_OK;
+  cudaSetDevice(ctx->device);
+  for (Buf* b : {&ctx->xw, &ctx->part, &ctx->n0, &ctx->gres, &ctx->vgrad, &ctx->gpart, &ctx->G, &ctx->grad6,
+                 &ctx->lpart, &ctx->lscalar})
+    if (b->p) cudaFree(b->p);
+  for (auto& r : ctx->recs) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  for (auto e : ctx->pool) cudaEventDestroy(e);
+  if (ctx->status) cudaFree(ctx->status);
+  delete ctx;
+  return PASFM_OK;
+}
+
+int pasfm_set_partial_budget(pasfm_ctx* ctx, size_t bytes) {
+  if (!ctx) return fail(PASFM_EINVAL, "ctx is NULL");
+  ctx->budget = bytes ? bytes : kDefaultPartialBudget;
+  return PASFM_OK;
+}
+
+int pasfm_workspace_size(const pasfm_geom* geom, size_t* bytes) {
+  if (!bytes) return fail(PASFM_EINVAL, "bytes is NULL");
+  Geo G;
+  Plan pl;
+  TRY(check_geom(geom, &G));
+  TRY(make_plan(G, &pl));
+  const int F = G.g.n_frames;
+  const size_t budget = kDefaultPartialBudget;
+  const int Ff = frames_per_chunk(fwd_per_frame(G, pl), budget, F);
+  const int Fb = frames_per_chunk(bwd_per_frame(G, pl), budget, F);
+  size_t b = size_t(G.n_rows) * 24;                                         // xw
+  b += size_t(Ff) * fwd_per_frame(G, pl);                                   // part + n0
+  b += size_t(Fb) * bwd_per_frame(G, pl);                                   // gpart
+  b += size_t(G.n_rows) * G.g.n_samples * 4;                                // residual (step)
+  b += size_t(G.nvox) * 4;                                                  // volume gradient (step)
+  b += size_t(G.n_rows) * 24 + size_t(F) * 48;                              // G, grad6
+  b += (size_t(G.n_rows + 7) / 8 + (F + Ff - 1) / std::max(Ff, 1) + 2) * 8;  // loss partials
+  *bytes = b;
+  return PASFM_OK;
+}
+
+int pasfm_reserve(pasfm_ctx* ctx, const pasfm_geom* geom) {
+  Geo G;
+  Plan pl;
+  TRY(prepare(ctx, geom, &G, &pl));
+  const int F = G.g.n_frames;
+  const int Ff = frames_per_chunk(fwd_per_frame(G, pl), ctx->budget, F);
+  const int Fb = frames_per_chunk(bwd_per_frame(G, pl), ctx->budget, F);
+  TRY(ctx->ensure(ctx->xw, size_t(G.n_rows) * 24));
+  TRY(ctx->ensure(ctx->part, size_t(Ff) * G.g.n_elem * pl.ncubes * pl.W * 4));
+  TRY(ctx->ensure(ctx->n0, size_t(Ff) * G.g.n_elem * pl.ncubes * 4));
+  TRY(ctx->ensure(ctx->gpart, size_t(Fb) * G.g.n_elem * pl.ncubes * 24));
+  TRY(ctx->ensure(ctx->gres, size_t(G.n_rows) * G.g.n_samples * 4));
+  TRY(ctx->ensure(ctx->vgrad, size_t(G.nvox) * 4));
+  TRY(ctx->ensure(ctx->G, size_t(G.n_rows) * 24));
+  TRY(ctx->ensure(ctx->grad6, size_t(F) * 48));
+  TRY(ctx->ensure(ctx->lpart, (size_t(G.n_rows + 7) / 8 + (F + Ff - 1) / std::max(Ff, 1) + 2) * 8));
+  TRY(ctx->ensure(ctx->lscalar, 8));
+  return PASFM_OK;
+}
+
+int pasfm_element_positions(pasfm_ctx* ctx, const pasfm_geom* geom, const double* elem, const double* pose,
+                            double* xw_out, void* stream) {
+  Geo G;
+  Plan pl;
+  TRY(prepare(ctx, geom, &G, &pl));
+  if (G.n_rows > 0 && (!elem || !pose || !xw_out)) return fail(PASFM_EINVAL, "NULL array argument");
+  return run_elem_pos(ctx, G, elem, pose, xw_out, static_cast<cudaStream_t>(stream));
+}
+
+int pasfm_forward(pasfm_ctx* ctx, const pasfm_geom* geom, const void* p0, const double* elem, const double* pose,
+                  float* sig_out, void* stream) {
+  Geo G;
+  Plan pl;
+  TRY(prepare(ctx, geom, &G, &pl));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t sig_bytes = size_t(G.n_rows) * G.g.n_samples * 4;
+  if (sig_bytes == 0) return PASFM_OK;
+  if (!sig_out || !elem || !pose || (G.nvox > 0 && !p0)) return fail(PASFM_EINVAL, "NULL array argument");
+  if (G.nvox == 0) {
+    CUDA_TRY(cudaMemsetAsync(sig_out, 0, sig_bytes, st));
+    return PASFM_OK;
+  }
+  TRY(ctx->ensure(ctx->xw, size_t(G.n_rows) * 24));
+  double* xw = static_cast<double*>(ctx->xw.p);
+  TRY(run_elem_pos(ctx, G, elem, pose, xw, st));
+  return run_forward(ctx, G, pl, p0, xw, sig_out, nullptr, nullptr, nullptr, nullptr, st);
+}
+
+int pasfm_adjoint(pasfm_ctx* ctx, const pasfm_geom* geom, const double* elem, const double* pose, const void* g,
+                  float* vol_out, void* stream) {
+  Geo G;
+  Plan pl;
+  TRY(prepare(ctx, geom, &G, &pl));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (G.nvox == 0) return PASFM_OK;
+  if (!vol_out) return fail(PASFM_EINVAL, "vol_out is NULL");
+  if (G.n_rows == 0 || G.g.n_samples == 0) {
+    CUDA_TRY(cudaMemsetAsync(vol_out, 0, size_t(G.nvox) * 4, st));
+    return PASFM_OK;
+  }
+  if (!elem || !pose || !g) return fail(PASFM_EINVAL, "NULL array argument");
+  TRY(ctx->ensure(ctx->xw, size_t(G.n_rows) * 24));
+  double* xw = static_cast<double*>(ctx->xw.p);
+  TRY(run_elem_pos(ctx, G, elem, pose, xw, st));
+  return run_backward(ctx, G, pl, 1, nullptr, xw, g, G.g.dtype_sig, nullptr, vol_out, nullptr, st);
+}
+
+int pasfm_pose_grad(pasfm_ctx* ctx, const pasfm_geom* geom, const void* p0, const double* elem,
+                    const double* pose, const void* g, const uint8_t* mask, double* grad6_out,
+                    double* gelem_out, void* stream) {
+  Geo G;
+  Plan pl;
+  TRY(prepare(ctx, geom, &G, &pl));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (G.g.n_frames == 0) return PASFM_OK;
+  if (!grad6_out) return fail(PASFM_EINVAL, "grad6_out is NULL");
+  if (G.n_rows == 0 || G.nvox == 0 || G.g.n_samples == 0) {
+    CUDA_TRY(cudaMemsetAsync(grad6_out, 0, size_t(G.g.n_frames) * 48, st));
+    if (gelem_out && G.n_rows) CUDA_TRY(cudaMemsetAsync(gelem_out, 0, size_t(G.n_rows) * 24, st));
+    return PASFM_OK;
+  }
+  if (!elem || !pose || !g || !p0) return fail(PASFM_EINVAL, "NULL array argument");
+  TRY(ctx->ensure(ctx->xw, size_t(G.n_rows) * 24));
+  double* xw = static_cast<double*>(ctx->xw.p);
+  double* Gm = gelem_out;
+  if (!Gm) {
+    TRY(ctx->ensure(ctx->G, size_t(G.n_rows) * 24));
+    Gm = static_cast<double*>(ctx->G.p);
+  }
+  TRY(run_elem_pos(ctx, G, elem, pose, xw, st));
+  TRY(run_backward(ctx, G, pl, 2, p0, xw, g, G.g.dtype_sig, mask, nullptr, Gm, st));
+  return run_grad6(ctx, G, xw, Gm, grad6_out, st);
+}
+
+int pasfm_loss(pasfm_ctx* ctx, const pasfm_geom* geom, const float* sig, const void* meas, const uint8_t* mask,
+               float* g_out, double* loss_out, void* stream) {
+  Geo G;
+  if (!ctx) return fail(PASFM_EINVAL, "ctx is NULL");
+  TRY(check_geom(geom, &G));
+  TRY(set_device(ctx));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int64_t rows = G.n_rows;
+  if (!loss_out) return fail(PASFM_EINVAL, "loss_out is NULL");
+  if (rows == 0 || G.g.n_samples == 0) {
+    CUDA_TRY(cudaMemsetAsync(loss_out, 0, 8, st));
+    return PASFM_OK;
+  }
+  if (!sig || !meas || !g_out) return fail(PASFM_EINVAL, "NULL array argument");
+  const int blocks = static_cast<int>((rows + 7) / 8);
+  TRY(ctx->ensure(ctx->lpart, size_t(blocks) * 8));
+  cudaEvent_t t = ctx->begin(st);
+  loss_rows_kernel<<<blocks, 256, 0, st>>>(sig, meas, G.g.dtype_sig, mask, g_out,
+                                           static_cast<double*>(ctx->lpart.p), static_cast<int>(rows),
+                                           G.g.n_samples);
+  ctx->end("loss_rows", t, st);
+  TRY(check_launch("loss_rows"));
+  t = ctx->begin(st);
+  sum_kernel<<<1, 256, 0, st>>>(static_cast<double*>(ctx->lpart.p), blocks, loss_out);
+  ctx->end("loss_sum", t, st);
+  return check_launch("loss_sum");
+}
+
+int pasfm_step(pasfm_ctx* ctx, const pasfm_geom* geom, void* p0, double* pose, const double* elem,
+               const void* meas, const uint8_t* mask, pasfm_adam* state, double* loss_out, void* stream) {
+  Geo G;
+  Plan pl;
+  TRY(prepare(ctx, geom, &G, &pl));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (!state) return fail(PASFM_EINVAL, "state is NULL");
+  if (G.nvox == 0 || G.n_rows == 0 || G.g.n_samples == 0)
+    return fail(PASFM_EINVAL, "pasfm_step needs a non-empty volume, array and record");
+  if (!p0 || !pose || !elem || !meas) return fail(PASFM_EINVAL, "NULL array argument");
+  const bool upd_vol = !(state->flags & PASFM_ADAM_FREEZE_VOLUME);
+  const bool upd_pose = !(state->flags & PASFM_ADAM_FREEZE_POSES);
+  if ((upd_vol && (!state->m_vol || !state->v_vol)) || (upd_pose && (!state->m_pose || !state->v_pose)))
+    return fail(PASFM_EINVAL, "Adam moment array is NULL");
+  if (!(state->beta1 >= 0 && state->beta1 < 1 && state->beta2 >= 0 && state->beta2 < 1 && state->eps >= 0))
+    return fail(PASFM_EINVAL, "Adam betas must lie in [0, 1) and eps >= 0");
+
+  TRY(ctx->ensure(ctx->xw, size_t(G.n_rows) * 24));
+  TRY(ctx->ensure(ctx->gres, size_t(G.n_rows) * G.g.n_samples * 4));
+  TRY(ctx->ensure(ctx->vgrad, size_t(G.nvox) * 4));
+  TRY(ctx->ensure(ctx->G, size_t(G.n_rows) * 24));
+  TRY(ctx->ensure(ctx->grad6, size_t(G.g.n_frames) * 48));
+  double* xw = static_cast<double*>(ctx->xw.p);
+  float* gres = static_cast<float*>(ctx->gres.p);
+
+  TRY(run_elem_pos(ctx, G, elem, pose, xw, st));
+  TRY(run_forward(ctx, G, pl, p0, xw, nullptr, gres, meas, mask, loss_out, st));
+  const int mode = (upd_vol ? 1 : 0) | (upd_pose ? 2 : 0);
+  const int64_t k = state->step + 1;
+  if (mode == 0) {
+    state->step = k;
+    return PASFM_OK;
+  }
+  TRY(run_backward(ctx, G, pl, mode, p0, xw, gres, PASFM_F32, nullptr, static_cast<float*>(ctx->vgrad.p),
+                   static_cast<double*>(ctx->G.p), st));
+  const double bc1 = 1.0 - std::pow(state->beta1, double(k));
+  const double bc2 = 1.0 - std::pow(state->beta2, double(k));
+  if (upd_pose) {
+    TRY(run_grad6(ctx, G, xw, static_cast<double*>(ctx->G.p), static_cast<double*>(ctx->grad6.p), st));
+    cudaEvent_t t = ctx->begin(st);
+    adam_pose_kernel<<<(G.g.n_frames + 63) / 64, 64, 0, st>>>(
+        pose, static_cast<double*>(ctx->grad6.p), state->m_pose, state->v_pose, G.g.n_frames, state->beta1,
+        state->beta2, bc1, bc2, state->lr_rot, state->lr_trans, state->eps,
+        (state->flags & PASFM_ADAM_FIX_FRAME0) ? 1 : 0, 0);
+    ctx->end("adam_pose", t, st);
+    TRY(check_launch("adam_pose"));
+  }
+  if (upd_vol) {
+    cudaEvent_t t = ctx->begin(st);
+    adam_vol_kernel<<<static_cast<unsigned>((G.nvox + 255) / 256), 256, 0, st>>>(
+        p0, G.g.dtype_vol, static_cast<float*>(ctx->vgrad.p), state->m_vol, state->v_vol, G.nvox,
+        static_cast<float>(state->beta1), static_cast<float>(state->beta2),
+        static_cast<float>(state->lr_vol / bc1), static_cast<float>(1.0 / std::sqrt(bc2)),
+        static_cast<float>(state->eps), (state->flags & PASFM_ADAM_NONNEG) ? 1 : 0);
+    ctx->end("adam_vol", t, st);
+    TRY(check_launch("adam_vol"));
+  }
+  state->step = k;
+  return PASFM_OK;
+}
+
+int pasfm_status(pasfm_ctx* ctx, void* stream, uint32_t* bits) {
+  if (!ctx) return fail(PASFM_EINVAL, "ctx is NULL");
+  TRY(set_device(ctx));
+  CUDA_TRY(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+  unsigned v = 0;
+  CUDA_TRY(cudaMemcpy(&v, ctx->status, sizeof v, cudaMemcpyDeviceToHost));
+  CUDA_TRY(cudaMemset(ctx->status, 0, sizeof v));
+  if (bits) *bits = v;
+  if (v & PASFM_STATUS_TIMEOUT) return fail(PASFM_ETIMEOUT, "a bounded device wait expired (status 0x%x)", v);
+  if (v) return fail(PASFM_EDEVICE, "device status 0x%x (element inside the grid or index clamped)", v);
+  return PASFM_OK;
+}
+
+int pasfm_timing_enable(pasfm_ctx* ctx, int enable) {
+  if (!ctx) return fail(PASFM_EINVAL, "ctx is NULL");
+  ctx->timing = enable != 0;
+  return PASFM_OK;
+}
+
+int pasfm_timing_reset(pasfm_ctx* ctx) {
+  if (!ctx) return fail(PASFM_EINVAL, "ctx is NULL");
+  for (auto& r : ctx->recs) {
+    cudaEventSynchronize(r.b);
+    ctx->pool.push_back(r.a);
+    ctx->pool.push_back(r.b);
+  }
+  ctx->recs.clear();
+  return PASFM_OK;
+}
+
+int pasfm_timing_read(pasfm_ctx* ctx, const char* kernel, double* ms_total, int64_t* launches) {
+  if (!ctx || !kernel) return fail(PASFM_EINVAL, "NULL argument");
+  double ms = 0.0;
+  int64_t n = 0;
+  for (auto& r : ctx->recs) {
+    if (std::strcmp(kernel, "*") != 0 && std::strcmp(kernel, r.name) != 0) continue;
+    CUDA_TRY(cudaEventSynchronize(r.b));
+    float t = 0.f;
+    CUDA_TRY(cudaEventElapsedTime(&t, r.a, r.b));
+    ms += t;
+    ++n;
+  }
+  if (ms_total) *ms_total = ms;
+  if (launches) *launches = n;
+  return PASFM_OK;
+}
+
+int64_t pasfm_launch_count(pasfm_ctx* ctx) { return ctx ? ctx->launches : -1; }
+
+}  // extern "C"
