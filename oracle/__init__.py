@@ -62,6 +62,8 @@ def load(path: str):
     L.oracle_adjoint_voxels.argtypes = [g, dp, dp, ctypes.c_void_p, ctypes.c_int64, dp]
     L.oracle_pose_grad.argtypes = [g, fp, dp, dp, ctypes.c_void_p, dp, ctypes.c_void_p]
     L.oracle_element_gradient_rows.argtypes = [g, fp, dp, dp, ctypes.c_void_p, ctypes.c_int64, dp]
+    L.oracle_element_gradient_bounds.argtypes = [g, fp, dp, dp, ctypes.c_void_p, ctypes.c_int64,
+                                                 ctypes.c_double, dp, dp]
     L.oracle_loss.argtypes = [g, dp, dp, ctypes.c_void_p, dp]
     L.oracle_loss.restype = ctypes.c_double
     return L
@@ -171,6 +173,18 @@ def element_gradient_rows(geom, p0, gsig, xw, rows):
     lib().oracle_element_gradient_rows(ctypes.byref(g), np.ascontiguousarray(p0, dtype=np.float32),
                                        _f64(gsig), _f64(xw), rp, len(r), out)
     return out
+
+
+def element_gradient_bounds(geom, p0, gsig, xw, rows, eps):
+    """(Gmid, Ghalf) [len(rows)][3]: every one-sided choice of the derivative at
+    support-edge boundaries within eps mm of +-a0 lies in Gmid +- Ghalf."""
+    g = make_geom(geom)
+    r, rp = _opt_ptr(rows, np.int64)
+    mid = np.zeros((len(r), 3))
+    half = np.zeros((len(r), 3))
+    lib().oracle_element_gradient_bounds(ctypes.byref(g), np.ascontiguousarray(p0, dtype=np.float32),
+                                         _f64(gsig), _f64(xw), rp, len(r), float(eps), mid, half)
+    return mid, half
 
 
 def loss(geom, sig, meas, mask=None):

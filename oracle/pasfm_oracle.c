@@ -225,6 +225,57 @@ void oracle_element_gradient_rows(const oracle_geom* g, const float* p0, const d
     element_gradient(g, p0, gsig + rows[k] * g->n_samples, xw + 3 * rows[k], G + 3 * k);
 }
 
+/* Element gradients with their one-sided ambiguity at the support edges.
+ * dW/dd jumps where a sample-interval boundary w_b = tau_b - h/2 - d crosses
+ * +-a0 (the strict rule counts a boundary as moving with d only if |w_b| < a0).
+ * For boundaries within eps (mm) of +-a0 both one-sided values are admissible:
+ * boundary b then adds c_b = (g_b - g_{b-1}) (-2 clamp(w_b)) / (4 d h) to
+ * sum_n g_n dW_n/dd, or nothing.  Gmid takes half of every such c_b and Ghalf
+ * their half-magnitudes (componentwise, times |x - r| / d), so every choice of
+ * sides lies in [Gmid - Ghalf, Gmid + Ghalf].  With eps = 0, Gmid equals the
+ * strict gradient and Ghalf is 0. */
+void oracle_element_gradient_bounds(const oracle_geom* g, const float* p0, const double* gsig,
+                                    const double* xw, const int64_t* rows, int64_t n_rows, double eps,
+                                    double* Gmid, double* Ghalf) {
+  const double h = g->c / g->fs;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t k = 0; k < n_rows; ++k) {
+    const double* x = xw + 3 * rows[k];
+    const double* gs = gsig + rows[k] * g->n_samples;
+    double mid[3] = {0, 0, 0}, half[3] = {0, 0, 0};
+    for (int iz = 0; iz < g->nz; ++iz)
+      for (int iy = 0; iy < g->ny; ++iy)
+        for (int ix = 0; ix < g->nx; ++ix) {
+          const double p = p0[((int64_t)iz * g->ny + iy) * g->nx + ix];
+          if (p == 0.0) continue;
+          double r[3];
+          voxel_centre(g, ix, iy, iz, r);
+          const double d = dist3(x, r);
+          int lo, hi;
+          if (!sample_range(g, d, &lo, &hi)) continue;
+          double s = 0.0, amb = 0.0;
+          for (int n = lo; n <= hi; ++n) s += gs[n] * oracle_pulse_dd(g, d, n);
+          for (int b = lo; b <= hi + 1; ++b) {
+            const double wb = g->c * (g->t0 + (double)b / g->fs) - 0.5 * h - d;
+            if (fabs(fabs(wb) - g->a0) >= eps) continue;
+            const double gb = b <= hi ? gs[b] : 0.0, gbm = b - 1 >= lo ? gs[b - 1] : 0.0;
+            const double cb = (gb - gbm) * (-2.0 * clampd(wb, g->a0)) / (4.0 * d * h);
+            const double strict = fabs(wb) < g->a0 ? cb : 0.0;
+            s += 0.5 * cb - strict;
+            amb += 0.5 * fabs(cb);
+          }
+          for (int a = 0; a < 3; ++a) {
+            mid[a] += p * s * (x[a] - r[a]) / d;
+            half[a] += fabs(p) * amb * fabs(x[a] - r[a]) / d;
+          }
+        }
+    for (int a = 0; a < 3; ++a) {
+      Gmid[3 * k + a] = mid[a];
+      Ghalf[3 * k + a] = half[a];
+    }
+  }
+}
+
 /* Element-position gradient G[f][j][3] and twist gradient grad6[f][6] = (w, v).
  * mask (may be NULL) zeroes whole (frame, element) traces of g. */
 void oracle_pose_grad(const oracle_geom* g, const float* p0, const double* gsig, const double* xw,

@@ -140,3 +140,23 @@ def test_adam_pose_first_step_moves_by_signed_lr():
     assert np.abs(out[0][:, :3] - E).max() < 1e-14
     assert np.abs(out[0][:, 3] - (E @ poses[0, :, 3] + expect[0, 3:])).max() < 1e-13
     assert math.isclose(np.linalg.det(out[1][:, :3]), 1.0, rel_tol=1e-14)
+
+
+def test_kink_band_reduces_to_strict_gradient_and_contains_it():
+    """The one-sided-ambiguity band of the element gradient: with eps = 0 it is the
+    strict gradient; with eps > 0 it contains the strict value and its width grows
+    with eps."""
+    import oracle
+    geom, elem, poses = oc.small_geom(shape=(6, 6, 6), spacing=0.2, m=3, n_frames=2, n_samples=320)
+    rng = np.random.default_rng(30)
+    p0 = rng.uniform(0.2, 1, size=(6, 6, 6)).astype(np.float32)
+    g = rng.standard_normal((2, 9, 320))
+    xw = oracle.element_positions(geom, elem, poses)
+    rows = np.arange(18)
+    strict = oracle.element_gradient_rows(geom, p0, g, xw, rows)
+    mid0, half0 = oracle.element_gradient_bounds(geom, p0, g, xw, rows, 0.0)
+    assert np.abs(mid0 - strict).max() <= 1e-13 * np.abs(strict).max() and half0.max() == 0.0
+    mid1, half1 = oracle.element_gradient_bounds(geom, p0, g, xw, rows, 1e-3)
+    mid2, half2 = oracle.element_gradient_bounds(geom, p0, g, xw, rows, 5e-3)
+    assert np.all(np.abs(strict - mid1) <= half1 * (1 + 1e-12) + 1e-15)
+    assert half2.sum() >= half1.sum() > 0.0

@@ -1,0 +1,313 @@
+"""CUDA path (through the C ABI) against the FP64 oracle on identical seeded inputs.
+
+Tolerances: relative L2 1e-5 on signals and volumes, 1e-4 on pose gradients
+(rotation and translation blocks of every frame separately).
+
+The pose gradient of the interval-averaged pulse is piecewise smooth in the
+element position: where a sample-interval boundary crosses the support edge
++-a0 its two one-sided values differ.  The FP32 path places boundaries with an
+error of ~3e-7 mm, so for a pair whose boundary sits that close to the edge it
+may take the other side than the FP64 oracle.  On the residuals the method
+produces (a pose mismatch) that changes nothing measurable and the strict 1e-4
+bound applies; on white-noise residuals each such flip moves a whole pair's
+contribution, so there the GPU value is checked against the oracle's band of
+admissible one-sided choices (boundaries within EPS_KINK of the edge).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2604_09643_b300 import binding, synth
+from tests.parity_cases import (REL_L2_POSE, REL_L2_SIG, coarse_case, pose_residual, ragged_case, rel_l2,
+                                residual, tma_case)
+
+pytestmark = pytest.mark.gpu
+
+EPS_KINK = 3e-6  # mm; about 10x the FP32 boundary-placement error
+
+
+def single_frame_case():
+    s = synth.single_frame()
+    return s.geom, s.p0, s.elem, s.poses
+
+
+CASES = {
+    "single_frame": single_frame_case,
+    "ragged": ragged_case,
+    "ragged_cut": lambda: ragged_case(cut=True),
+    "tma": tma_case,
+    "coarse": coarse_case,
+}
+
+
+@pytest.fixture(scope="module")
+def ctx(cuda_device):
+    c = binding.Context(0)
+    yield c
+    c.close()
+
+
+def dev(a, dtype=None):
+    t = torch.from_numpy(np.ascontiguousarray(a)).to("cuda")
+    return t if dtype is None else t.to(dtype)
+
+
+def assert_status_ok(ctx):
+    rc, bits = ctx.status()
+    assert rc == 0 and bits == 0, (rc, bits)
+
+
+@pytest.fixture(scope="module", params=sorted(CASES))
+def case(request):
+    geom, p0, elem, poses = CASES[request.param]()
+    xw = oracle.element_positions(geom, elem, poses)
+    return request.param, geom, p0, elem, poses, xw
+
+
+def test_element_positions(ctx, case):
+    _, geom, p0, elem, poses, xw = case
+    got = ctx.element_positions(geom, dev(elem), dev(poses)).cpu().numpy()
+    assert np.abs(got - xw).max() <= 1e-13 * np.abs(xw).max()
+
+
+def test_forward(ctx, case):
+    name, geom, p0, elem, poses, xw = case
+    ref = oracle.forward(geom, p0, xw)
+    got = ctx.forward(geom, dev(p0), dev(elem), dev(poses)).cpu().numpy()
+    assert_status_ok(ctx)
+    err = rel_l2(got, ref)
+    assert err < REL_L2_SIG, (name, err)
+
+
+def test_adjoint(ctx, case):
+    name, geom, p0, elem, poses, xw = case
+    g = residual(geom, seed=11)
+    ref = oracle.adjoint(geom, g, xw)
+    got = ctx.adjoint(geom, dev(elem), dev(poses), dev(g)).cpu().numpy()
+    assert_status_ok(ctx)
+    err = rel_l2(got, ref)
+    assert err < REL_L2_SIG, (name, err)
+
+
+@pytest.mark.parametrize("masked", [False, True])
+def test_pose_grad(ctx, case, masked):
+    """Strict 1e-4 on the residual of a pose mismatch."""
+    name, geom, p0, elem, poses, xw = case
+    g = pose_residual(geom, p0, elem, poses)
+    mask = None
+    if masked:
+        mask = (np.random.default_rng(13).uniform(size=(geom["n_frames"], geom["n_elem"])) > 0.3).astype(np.uint8)
+    ref6, refG = oracle.pose_grad(geom, p0, g, xw, mask)
+    got6, gotG = ctx.pose_grad(geom, dev(p0), dev(elem), dev(poses), dev(g),
+                               None if mask is None else dev(mask), want_elem=True)
+    got6, gotG = got6.cpu().numpy(), gotG.cpu().numpy()
+    assert_status_ok(ctx)
+    for f in range(geom["n_frames"]):
+        er = rel_l2(got6[f, :3], ref6[f, :3])
+        et = rel_l2(got6[f, 3:], ref6[f, 3:])
+        assert er < REL_L2_POSE and et < REL_L2_POSE, (name, f, er, et)
+    assert rel_l2(gotG, refG) < REL_L2_POSE
+
+
+def _band_check(gotG, got6, mid, half, xw_rows_by_frame, tol=REL_L2_POSE):
+    """Element gradients inside the oracle's one-sided band (plus tol), twist
+    gradients inside the band carried through x cross G."""
+    scale = np.linalg.norm(mid, axis=-1, keepdims=True)
+    assert np.all(np.abs(gotG - mid) <= half + tol * scale + 1e-300)
+    for f, (x, sl) in enumerate(xw_rows_by_frame):
+        m, hf = mid[sl], half[sl]
+        w_mid, v_mid = np.cross(x, m).sum(0), m.sum(0)
+        ax = np.abs(x)
+        w_half = np.stack([ax[:, 1] * hf[:, 2] + ax[:, 2] * hf[:, 1],
+                           ax[:, 2] * hf[:, 0] + ax[:, 0] * hf[:, 2],
+                           ax[:, 0] * hf[:, 1] + ax[:, 1] * hf[:, 0]], axis=1).sum(0)
+        v_half = hf.sum(0)
+        assert np.all(np.abs(got6[f, :3] - w_mid) <= w_half + tol * np.linalg.norm(w_mid))
+        assert np.all(np.abs(got6[f, 3:] - v_mid) <= v_half + tol * np.linalg.norm(v_mid))
+
+
+def test_pose_grad_white_noise_band(ctx, case):
+    name, geom, p0, elem, poses, xw = case
+    g = residual(geom, seed=12)
+    got6, gotG = ctx.pose_grad(geom, dev(p0), dev(elem), dev(poses), dev(g), want_elem=True)
+    got6, gotG = got6.cpu().numpy(), gotG.cpu().numpy()
+    assert_status_ok(ctx)
+    F, E = geom["n_frames"], geom["n_elem"]
+    mid, half = oracle.element_gradient_bounds(geom, p0, g, xw, np.arange(F * E), EPS_KINK)
+    # the band must be narrow for the check to mean anything
+    assert half.sum() < 0.05 * np.abs(mid).sum(), (name, half.sum() / np.abs(mid).sum())
+    _band_check(gotG.reshape(-1, 3), got6, mid, half,
+                [(xw[f], slice(f * E, (f + 1) * E)) for f in range(F)])
+
+
+def test_loss_head(ctx, case):
+    name, geom, p0, elem, poses, xw = case
+    rng = np.random.default_rng(14)
+    s = residual(geom, seed=15)
+    meas = residual(geom, seed=16)
+    mask = (rng.uniform(size=(geom["n_frames"], geom["n_elem"])) > 0.25).astype(np.uint8)
+    Lref, gref = oracle.loss(geom, s, meas, mask)
+    L, g = ctx.loss(geom, dev(s), dev(meas), dev(mask))
+    assert abs(float(L) - Lref) <= 1e-9 * Lref
+    assert np.array_equal(g.cpu().numpy(), (s - meas) * mask[:, :, None])
+
+
+def test_adjoint_identity_on_gpu(ctx, case):
+    """<A x, y> = <x, A^T y> with both operators on the GPU."""
+    name, geom, p0, elem, poses, xw = case
+    rng = np.random.default_rng(17)
+    x = rng.uniform(0, 1, size=p0.shape).astype(np.float32)
+    y = residual(geom, seed=18)
+    Ax = ctx.forward(geom, dev(x), dev(elem), dev(poses)).double()
+    Aty = ctx.adjoint(geom, dev(elem), dev(poses), dev(y)).double()
+    lhs = float((Ax * dev(y).double()).sum())
+    rhs = float((dev(x).double() * Aty).sum())
+    assert abs(lhs - rhs) <= 1e-5 * max(abs(lhs), abs(rhs)), (name, lhs, rhs)
+
+
+def test_repeat_calls_are_bitwise_identical(ctx):
+    geom, p0, elem, poses = tma_case()
+    g = residual(geom, seed=19)
+    a = [ctx.forward(geom, dev(p0), dev(elem), dev(poses)) for _ in range(2)]
+    b = [ctx.adjoint(geom, dev(elem), dev(poses), dev(g)) for _ in range(2)]
+    c = [ctx.pose_grad(geom, dev(p0), dev(elem), dev(poses), dev(g)) for _ in range(2)]
+    assert torch.equal(a[0], a[1]) and torch.equal(b[0], b[1]) and torch.equal(c[0], c[1])
+
+
+def test_frame_chunking_matches_single_pass(ctx):
+    """A tiny partial-result budget forces one frame per launch; the per-trace
+    arithmetic is unchanged, so results are bit-identical."""
+    geom, p0, elem, poses = ragged_case()
+    g = residual(geom, seed=20)
+    full_f = ctx.forward(geom, dev(p0), dev(elem), dev(poses))
+    full_p = ctx.pose_grad(geom, dev(p0), dev(elem), dev(poses), dev(g))
+    ctx.set_partial_budget(1)
+    try:
+        ch_f = ctx.forward(geom, dev(p0), dev(elem), dev(poses))
+        ch_p = ctx.pose_grad(geom, dev(p0), dev(elem), dev(poses), dev(g))
+    finally:
+        ctx.set_partial_budget(0)
+    assert torch.equal(full_f, ch_f)
+    assert torch.equal(full_p, ch_p)
+
+
+# ----------------------------------------------------------------------------- invariances on the GPU
+
+def test_grid_shift_invariance(ctx):
+    """Moving the array by k voxels along x equals moving the volume content by -k voxels."""
+    geom = synth.make_geom((24, 24, 32), 0.1, 64, 1, 1024)
+    rng = np.random.default_rng(21)
+    p0 = np.zeros((24, 24, 32), dtype=np.float32)
+    p0[4:20, 4:20, 8:24] = rng.uniform(0, 1, size=(16, 16, 16))
+    elem = synth.planar_array(8, 8, 0.5)
+    poses = np.zeros((1, 3, 4))
+    poses[0, :, :3] = synth.axis_angle_matrix([0.3, 1, 0.2], 0.05)
+    poses[0, :, 3] = [0.0, 0.0, synth.top_face_z(geom) + 4.0]
+    k = 3
+    moved = poses.copy()
+    moved[0, 0, 3] += k * geom["dx"]
+    p0s = np.zeros_like(p0)
+    p0s[:, :, :-k] = p0[:, :, k:]
+    a = ctx.forward(geom, dev(p0), dev(elem), dev(moved)).cpu().numpy()
+    b = ctx.forward(geom, dev(p0s), dev(elem), dev(poses)).cpu().numpy()
+    assert rel_l2(a, b) < REL_L2_SIG
+
+
+def test_rot90_invariance(ctx):
+    """Rotating the array by +90 deg about z equals rotating the volume by -90 deg."""
+    geom = synth.make_geom((16, 24, 24), 0.1, 64, 1, 1024)
+    rng = np.random.default_rng(22)
+    p0 = rng.uniform(0, 1, size=(16, 24, 24)).astype(np.float32)
+    elem = synth.planar_array(8, 8, 0.5)
+    poses = np.zeros((1, 3, 4))
+    poses[0, :, :3] = synth.axis_angle_matrix([0.2, 0.4, 1.0], 0.1)
+    poses[0, :, 3] = [0.3, -0.2, synth.top_face_z(geom) + 4.0]
+    Rz = np.array([[0.0, -1.0, 0.0], [1.0, 0.0, 0.0], [0.0, 0.0, 1.0]])
+    rot = poses.copy()
+    rot[0, :, :3] = Rz @ poses[0, :, :3]
+    rot[0, :, 3] = Rz @ poses[0, :, 3]
+    n = 24
+    p0r = np.empty_like(p0)
+    for iy in range(n):
+        for ix in range(n):
+            p0r[:, iy, ix] = p0[:, ix, n - 1 - iy]
+    xa = oracle.element_positions(geom, elem, rot)
+    xb = oracle.element_positions(geom, elem, poses)
+    assert rel_l2(oracle.forward(geom, p0, xa), oracle.forward(geom, p0r, xb)) < 1e-12
+    a = ctx.forward(geom, dev(p0), dev(elem), dev(rot)).cpu().numpy()
+    b = ctx.forward(geom, dev(p0r), dev(elem), dev(poses)).cpu().numpy()
+    assert rel_l2(a, b) < REL_L2_SIG
+
+
+# ----------------------------------------------------------------------------- edge cases
+
+def test_empty_volume_gives_zero_signals(ctx):
+    geom, p0, elem, poses = single_frame_case()
+    geom = dict(geom, nx=0)
+    out = torch.full((1, 64, 512), 7.0, device="cuda")
+    binding.pasfm_forward(ctx.handle, geom, torch.zeros(1, device="cuda"), dev(elem), dev(poses), out)
+    torch.cuda.synchronize()
+    assert float(out.abs().max()) == 0.0
+
+
+def test_zero_frames_and_elements_are_noops(ctx):
+    geom, p0, elem, poses = single_frame_case()
+    out = ctx.forward(dict(geom, n_frames=0), dev(p0), dev(elem), dev(poses))
+    assert out.numel() == 0
+    vol = ctx.adjoint(dict(geom, n_elem=0), dev(elem), dev(poses), torch.zeros(1, device="cuda"))
+    assert float(vol.abs().max()) == 0.0
+    assert_status_ok(ctx)
+
+
+def test_all_zero_volume(ctx):
+    geom, p0, elem, poses = tma_case()
+    out = ctx.forward(geom, dev(np.zeros_like(p0)), dev(elem), dev(poses))
+    assert float(out.abs().max()) == 0.0
+
+
+def test_element_inside_grid_sets_status(ctx):
+    geom, p0, elem, poses = single_frame_case()
+    bad = poses.copy()
+    bad[0, 2, 3] = 0.0  # array plane through the middle of the volume
+    ctx.forward(geom, dev(p0), dev(elem), dev(bad))
+    rc, bits = ctx.status()
+    assert rc == -5 and bits & binding.STATUS_ELEMENT_INSIDE
+    assert_status_ok(ctx)  # the status word was cleared
+
+
+def test_unsupported_sphere_radius_is_rejected(ctx):
+    geom, p0, elem, poses = single_frame_case()
+    with pytest.raises(binding.PasfmError) as e:
+        ctx.forward(dict(geom, a0_mm=0.5), dev(p0), dev(elem), dev(poses))
+    assert e.value.code == -6
+
+
+# ----------------------------------------------------------------------------- full-size workload, sampled
+
+def test_full_scan_sampled(ctx):
+    """128^3 voxels, 16x16 elements, 64 frames, 2048 samples: every output is
+    computed on the GPU; sampled traces, voxels and one frame's pose gradient are
+    recomputed by the oracle."""
+    s = synth.full_scan()
+    geom, p0 = s.geom, s.p0
+    xw = oracle.element_positions(geom, s.elem, s.poses)
+    g = residual(geom, seed=23)
+    dp0, delem, dpose, dg = dev(p0), dev(s.elem), dev(s.poses), dev(g)
+    sig = ctx.forward(geom, dp0, delem, dpose).cpu().numpy()
+    vol = ctx.adjoint(geom, delem, dpose, dg).cpu().numpy()
+    g6, gE = ctx.pose_grad(geom, dp0, delem, dpose, dg, want_elem=True)
+    g6, gE = g6.cpu().numpy(), gE.cpu().numpy()
+    assert_status_ok(ctx)
+    rng = np.random.default_rng(24)
+    E = geom["n_elem"]
+    rows = np.unique(rng.integers(0, geom["n_frames"] * E, size=12))
+    ref_rows = oracle.forward(geom, p0, xw, rows=rows)
+    assert rel_l2(sig.reshape(-1, geom["n_samples"])[rows], ref_rows) < REL_L2_SIG
+    vox = np.unique(rng.integers(0, p0.size, size=48))
+    assert rel_l2(vol.ravel()[vox], oracle.adjoint(geom, g, xw, voxels=vox)) < REL_L2_SIG
+    f = int(rng.integers(0, geom["n_frames"]))
+    frame_rows = np.arange(f * E, (f + 1) * E)
+    mid, half = oracle.element_gradient_bounds(geom, p0, g, xw, frame_rows, EPS_KINK)
+    assert half.sum() < 0.05 * np.abs(mid).sum()
+    _band_check(gE[f], g6[f:f + 1], mid, half, [(xw[f], slice(0, E))])
