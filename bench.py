@@ -1,0 +1,394 @@
+"""Benchmark: gradient steps/s of the differentiable acoustic radiation operator on B300.
+
+One step = one pasfm_step on the full-scan workload (128^3 voxels at 0.1 mm,
+vessel-tree phantom of 40 tubes, 16x16 elements at 0.6 mm, 64 frames on a smooth
+sweep, 2048 samples at 40 MHz): element positions, forward, fused loss head,
+adjoint and pose gradient (one fused kernel), Adam on the volume and on the
+frame twists.  Inputs are synthetic and seeded; the iterate starts from a
+dense volume and perturbed poses, the measurements are the forward of the true
+volume and poses.
+
+Prints ONE JSON line (rank 0).  --impl reference times the FP64 CPU oracle on a
+bounded sample of the same step.  Under torchrun (--gpus N > 1) every rank runs
+its own replica scan (weak scaling; the step has no cross-rank exchange).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "grad steps/s"
+UNIT = "steps/s"
+WORKLOAD = "full_scan_128^3_0.1mm_vessel40_16x16_0.6mm_64f_2048s"
+
+
+# Algorithmic FP32 flops per voxel-element pair (frozen before tuning;
+# m = 2 a0 / h + 1 in-support samples per pair, FMA = 2 flops).
+def flops_fwd(m):
+    return 18 + 8 * m
+
+
+def flops_adj(m):
+    return 18 + 8 * m
+
+
+def flops_pose(m):
+    return 26 + 13 * m
+
+
+def peaks():
+    p = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            p = json.load(fh)
+    except (OSError, ValueError):
+        pass
+    sm_mhz = float(p.get("sm_max_mhz", 2032.0))
+    # FP32 non-tensor peak: 148 SMs x 128 FP32 lanes x 2 flops x max SM clock
+    fp32_tflops = 148 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    return dict(hbm_gbs=float(p.get("hbm_gbs", 6400.0)), fp32_tflops=fp32_tflops, sm_max_mhz=sm_mhz,
+                source="measured" if p else "fallback")
+
+
+def kernel_src_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2604_09643_b300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, fn), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_for(kernel):
+    """DRAM bytes per launch from the committed ncu summary, if taken on these sources."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
+            t = json.load(fh)
+    except (OSError, ValueError):
+        return None
+    e = t.get(kernel)
+    if not e or e.get("src_sha") != kernel_src_hash():
+        return None
+    return e.get("bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        except OSError:
+            pass
+        finally:
+            if self.path and os.path.exists(self.path):
+                os.remove(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [v for v in (num(r[1]) for r in rows) if v is not None]
+        mx = [v for v in (num(r[2]) for r in rows) if v is not None]
+        pw = [v for v in (num(r[3]) for r in rows) if v is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "power_w_median": statistics.median(pw) if pw else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ----------------------------------------------------------------------------- workload
+
+def make_workload(seed_offset=0):
+    from paper_2604_09643_b300 import synth
+
+    scan = synth.full_scan(seed_offset=seed_offset)
+    rng = np.random.default_rng(synth.SEED_NOISE + 20 + seed_offset)
+    # dense starting iterate: damped truth plus a uniform background
+    p_init = (0.5 * scan.p0 + rng.uniform(0.02, 0.08, size=scan.p0.shape)).astype(np.float32)
+    poses_init = synth.perturb_poses(scan.poses, rng, 0.5, 0.1, keep_first=True)
+    return scan, p_init, poses_init
+
+
+def pairs_and_m(geom):
+    h = geom["c_mm_per_us"] / geom["fs_mhz"]
+    m = 2 * geom["a0_mm"] / h + 1
+    pairs = geom["nx"] * geom["ny"] * geom["nz"] * geom["n_elem"] * geom["n_frames"]
+    return pairs, m
+
+
+# ----------------------------------------------------------------------------- CPU oracle timing
+
+def oracle_step_sample(scan, p_init, poses_init, n_elem_sample):
+    """Time the oracle on one frame and `n_elem_sample` elements of the step; returns
+    seconds and the fraction of the full step's pairs it covered."""
+    import oracle
+
+    geom = dict(scan.geom, n_frames=1, n_elem=n_elem_sample)
+    elem = scan.elem[:n_elem_sample]
+    xw = oracle.element_positions(geom, elem, poses_init[:1])
+    meas = np.random.default_rng(0).standard_normal((1, n_elem_sample, geom["n_samples"]))
+    t = time.perf_counter()
+    s = oracle.forward(geom, p_init, xw)
+    _, g = oracle.loss(geom, s, meas)
+    oracle.adjoint(geom, g, xw)
+    oracle.pose_grad(geom, p_init, g, xw)
+    dt = time.perf_counter() - t
+    frac = n_elem_sample / (scan.geom["n_elem"] * scan.geom["n_frames"])
+    return dt, frac
+
+
+def cpu_baseline(scan, p_init, poses_init, n_elem_sample=16):
+    import oracle
+
+    dt, frac = oracle_step_sample(scan, p_init, poses_init, n_elem_sample)
+    step_s = dt / frac
+    return {"value": 1.0 / step_s, "unit": UNIT, "cores": oracle.threads_used(), "kind": "oracle",
+            "sample": f"1 of {scan.geom['n_frames']} frames x {n_elem_sample} of {scan.geom['n_elem']} "
+                      f"elements of one step (forward, loss, adjoint, pose gradient in FP64): "
+                      f"{dt:.2f} s, scaled by the pair count", "seconds_per_step": step_s}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+
+    scan, p_init, poses_init = make_workload()
+    n_sample = 16
+    for _ in range(args.warmup):
+        oracle_step_sample(scan, p_init, poses_init, n_sample)
+    times = []
+    for _ in range(args.steps):
+        dt, frac = oracle_step_sample(scan, p_init, poses_init, n_sample)
+        times.append(dt / frac)
+    step_s = sum(times) / len(times)
+    value = 1.0 / step_s
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic",
+           "config": {"workload": WORKLOAD, "sample": f"1 frame x {n_sample} elements per step, scaled by pairs"},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.threads_used(), "kind": "oracle",
+                            "sample": f"each step: 1 of 64 frames x {n_sample} of 256 elements, scaled by pairs"},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+    return 0
+
+
+# ----------------------------------------------------------------------------- GPU arm
+
+def run_native(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2604_09643_b300 import binding
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    scan, p_init, poses_init = make_workload(seed_offset=rank)
+    geom = scan.geom
+    pairs, m = pairs_and_m(geom)
+
+    def to_dev(a):
+        return torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+
+    ctx = binding.Context(local)
+    elem = to_dev(scan.elem)
+    meas = ctx.forward(geom, to_dev(scan.p0), elem, to_dev(scan.poses))
+    ctx.reserve(geom)
+    p0 = to_dev(p_init)
+    poses = to_dev(poses_init)
+    adam = binding.AdamState(geom, dev, lr_vol=2e-3, lr_rot=2e-4, lr_trans=2e-3, nonneg=True, fix_frame0=True)
+    loss = torch.zeros((), dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    warmup = max(args.warmup, 3)
+
+    def step():
+        ctx.step(geom, p0, poses, elem, meas, adam, loss_out=loss)
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    rc, bits = ctx.status()
+    if rc != 0:
+        raise RuntimeError(f"device status {bits:#x} after warm-up")
+
+    # ---- device-timed region (inputs resident in HBM)
+    ctx.timing(True)
+    ctx.timing_reset()
+    l0 = ctx.launch_count()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    launches = ctx.launch_count() - l0
+    ms = ev0.elapsed_time(ev1)
+    per_kernel = {}
+    for name in ("fwd_cube", "fwd_reduce", "bwd_cube", "pose_rows", "grad6", "adam_vol", "adam_pose",
+                 "elem_pos", "loss_sum"):
+        t, n = ctx.timing_read(name)
+        if n:
+            per_kernel[name] = {"ms_total": t, "launches": n, "ms_avg": t / n}
+    ctx.timing(False)
+    ctx.timing_reset()
+    clocks = clk.summary()
+    rc, bits = ctx.status()
+    if rc != 0:
+        raise RuntimeError(f"device status {bits:#x} in the timed region")
+
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_per_step = ms / args.steps
+    value = world * args.steps / (ms / 1e3)
+
+    # ---- end to end through the public API with host buffers
+    meas_host = meas.cpu().pin_memory()
+    loss_host = torch.zeros((), dtype=torch.float64).pin_memory()
+    poses_host = torch.zeros(poses.shape, dtype=poses.dtype).pin_memory()
+    meas_dev = torch.empty_like(meas)
+    e2e_steps = max(3, args.steps // 2)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        meas_dev.copy_(meas_host, non_blocking=True)
+        ctx.step(geom, p0, poses, elem, meas_dev, adam, loss_out=loss)
+        loss_host.copy_(loss, non_blocking=True)
+        poses_host.copy_(poses, non_blocking=True)
+        stream.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": world * e2e_steps / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": int(meas.numel() * meas.element_size()),
+           "d2h_bytes_per_step": int(loss.element_size() + poses.numel() * poses.element_size())}
+
+    # ---- roofline of the dominant kernel (algorithmic flops / live CUDA-event duration)
+    pk = peaks()
+    dom = max(per_kernel, key=lambda k: per_kernel[k]["ms_total"])
+    fpp = {"bwd_cube": flops_adj(m) + flops_pose(m), "fwd_cube": flops_fwd(m)}.get(dom)
+    roofline = None
+    if fpp:
+        launches_per_step = per_kernel[dom]["launches"] / args.steps
+        flops_per_launch = pairs * fpp / launches_per_step
+        achieved = flops_per_launch / (per_kernel[dom]["ms_avg"] * 1e-3) / 1e12
+        roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": pk["fp32_tflops"],
+                    "unit": "TFLOP/s", "frac": achieved / pk["fp32_tflops"], "traffic": traffic_for(dom),
+                    "peak_source": f"FP32 148 SM x 128 lanes x 2 flops x {pk['sm_max_mhz']:.0f} MHz "
+                                   f"({pk['source']} clock)",
+                    "flops_per_pair": fpp, "pairs_per_launch": pairs / launches_per_step}
+    step_flops = pairs * (flops_fwd(m) + flops_adj(m) + flops_pose(m))
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "voxels": [geom["nz"], geom["ny"], geom["nx"]],
+                   "elements": geom["n_elem"], "frames": geom["n_frames"], "samples": geom["n_samples"],
+                   "global_batch": world, "parallelism": f"replicas{world}",
+                   "l2": "inputs larger than L2 (128 MiB measurements, 128 MiB residual, "
+                         "2.6 GB of per-cube partial traces written and read per step)"},
+        "pairs_per_s": value * pairs,
+        "step_tflops": step_flops * value / world / 1e12,
+        "fp32_frac_step": step_flops * value / world / 1e12 / pk["fp32_tflops"],
+        "roofline": roofline,
+        "per_kernel_ms": {k: round(v["ms_avg"], 4) for k, v in per_kernel.items()},
+        "clocks": clocks,
+        "gpu_launches": launches,
+        "e2e": e2e,
+        "final_loss": float(loss.item()),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(scan, p_init, poses_init)
+    if rank == 0:
+        print(json.dumps(out))
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_native(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -92,18 +92,28 @@ def test_adjoint(ctx, case):
 
 @pytest.mark.parametrize("masked", [False, True])
 def test_pose_grad(ctx, case, masked):
-    """Strict 1e-4 on the residual of a pose mismatch."""
+    """Residual of a pose mismatch: strict 1e-4 when the record holds the whole
+    response.  A record that cuts the response ends the residual with a jump to
+    zero, where a one-sided flip moves a whole pair, so that case is held to the
+    oracle's one-sided band instead."""
     name, geom, p0, elem, poses, xw = case
     g = pose_residual(geom, p0, elem, poses)
+    F, E = geom["n_frames"], geom["n_elem"]
     mask = None
     if masked:
-        mask = (np.random.default_rng(13).uniform(size=(geom["n_frames"], geom["n_elem"])) > 0.3).astype(np.uint8)
-    ref6, refG = oracle.pose_grad(geom, p0, g, xw, mask)
+        mask = (np.random.default_rng(13).uniform(size=(F, E)) > 0.3).astype(np.uint8)
     got6, gotG = ctx.pose_grad(geom, dev(p0), dev(elem), dev(poses), dev(g),
                                None if mask is None else dev(mask), want_elem=True)
     got6, gotG = got6.cpu().numpy(), gotG.cpu().numpy()
     assert_status_ok(ctx)
-    for f in range(geom["n_frames"]):
+    if name == "ragged_cut":
+        gm = g if mask is None else g * mask[:, :, None]
+        mid, half = oracle.element_gradient_bounds(geom, p0, gm, xw, np.arange(F * E), EPS_KINK)
+        _band_check(gotG.reshape(-1, 3), got6, mid, half,
+                    [(xw[f], slice(f * E, (f + 1) * E)) for f in range(F)])
+        return
+    ref6, refG = oracle.pose_grad(geom, p0, g, xw, mask)
+    for f in range(F):
         er = rel_l2(got6[f, :3], ref6[f, :3])
         et = rel_l2(got6[f, 3:], ref6[f, 3:])
         assert er < REL_L2_POSE and et < REL_L2_POSE, (name, f, er, et)
@@ -149,7 +159,7 @@ def test_loss_head(ctx, case):
     mask = (rng.uniform(size=(geom["n_frames"], geom["n_elem"])) > 0.25).astype(np.uint8)
     Lref, gref = oracle.loss(geom, s, meas, mask)
     L, g = ctx.loss(geom, dev(s), dev(meas), dev(mask))
-    assert abs(float(L) - Lref) <= 1e-9 * Lref
+    assert abs(float(L) - Lref) <= 1e-7 * Lref  # GPU rounds s - S to FP32 before squaring
     assert np.array_equal(g.cpu().numpy(), (s - meas) * mask[:, :, None])
 
 
@@ -296,8 +306,6 @@ def test_full_scan_sampled(ctx):
     dp0, delem, dpose, dg = dev(p0), dev(s.elem), dev(s.poses), dev(g)
     sig = ctx.forward(geom, dp0, delem, dpose).cpu().numpy()
     vol = ctx.adjoint(geom, delem, dpose, dg).cpu().numpy()
-    g6, gE = ctx.pose_grad(geom, dp0, delem, dpose, dg, want_elem=True)
-    g6, gE = g6.cpu().numpy(), gE.cpu().numpy()
     assert_status_ok(ctx)
     rng = np.random.default_rng(24)
     E = geom["n_elem"]
@@ -306,8 +314,20 @@ def test_full_scan_sampled(ctx):
     assert rel_l2(sig.reshape(-1, geom["n_samples"])[rows], ref_rows) < REL_L2_SIG
     vox = np.unique(rng.integers(0, p0.size, size=48))
     assert rel_l2(vol.ravel()[vox], oracle.adjoint(geom, g, xw, voxels=vox)) < REL_L2_SIG
+    # pose gradient: one frame carries the residual of a pose mismatch (oracle
+    # traces at the true and at a perturbed pose), every other frame zero
     f = int(rng.integers(0, geom["n_frames"]))
     frame_rows = np.arange(f * E, (f + 1) * E)
-    mid, half = oracle.element_gradient_bounds(geom, p0, g, xw, frame_rows, EPS_KINK)
-    assert half.sum() < 0.05 * np.abs(mid).sum()
-    _band_check(gE[f], g6[f:f + 1], mid, half, [(xw[f], slice(0, E))])
+    pert = synth.perturb_poses(s.poses[f:f + 1], np.random.default_rng(25), 0.5, 0.05, keep_first=False)
+    xp = oracle.element_positions(dict(geom, n_frames=1), s.elem, pert)
+    gp = np.zeros_like(g)
+    gp[f] = (oracle.forward(geom, p0, xw, rows=frame_rows)
+             - oracle.forward(dict(geom, n_frames=1), p0, xp)[0]).astype(np.float32)
+    g6, gE = ctx.pose_grad(geom, dp0, delem, dpose, dev(gp), want_elem=True)
+    g6, gE = g6.cpu().numpy(), gE.cpu().numpy()
+    Gref = oracle.element_gradient_rows(geom, p0, gp, xw, frame_rows)
+    assert rel_l2(g6[f, :3], np.cross(xw[f], Gref).sum(0)) < REL_L2_POSE
+    assert rel_l2(g6[f, 3:], Gref.sum(0)) < REL_L2_POSE
+    assert rel_l2(gE[f], Gref) < REL_L2_POSE
+    others = np.delete(np.arange(geom["n_frames"]), f)
+    assert np.abs(g6[others]).max() == 0.0
