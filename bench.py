@@ -187,7 +187,7 @@ def oracle_step_sample(scan, p_init, poses_init, n_elem_sample):
     return dt, frac
 
 
-def cpu_baseline(scan, p_init, poses_init, n_elem_sample=16):
+def cpu_baseline(scan, p_init, poses_init, n_elem_sample=256):
     import oracle
 
     dt, frac = oracle_step_sample(scan, p_init, poses_init, n_elem_sample)

@@ -328,6 +328,8 @@ def test_full_scan_sampled(ctx):
     Gref = oracle.element_gradient_rows(geom, p0, gp, xw, frame_rows)
     assert rel_l2(g6[f, :3], np.cross(xw[f], Gref).sum(0)) < REL_L2_POSE
     assert rel_l2(g6[f, 3:], Gref.sum(0)) < REL_L2_POSE
-    assert rel_l2(gE[f], Gref) < REL_L2_POSE
+    # per-element gradients of the sharp vessel phantom: one-sided band
+    mid, half = oracle.element_gradient_bounds(geom, p0, gp, xw, frame_rows, EPS_KINK)
+    _band_check(gE[f], g6[f:f + 1], mid, half, [(xw[f], slice(0, E))])
     others = np.delete(np.arange(geom["n_frames"]), f)
     assert np.abs(g6[others]).max() == 0.0
