@@ -148,10 +148,10 @@ class ClockSampler:
 
 # ----------------------------------------------------------------------------- workload
 
-def make_workload(seed_offset=0):
+def make_workload(seed_offset=0, n_frames=64):
     from paper_2604_09643_b300 import synth
 
-    scan = synth.full_scan(seed_offset=seed_offset)
+    scan = synth.full_scan(seed_offset=seed_offset, n_frames=n_frames)
     rng = np.random.default_rng(synth.SEED_NOISE + 20 + seed_offset)
     # dense starting iterate: damped truth plus a uniform background
     p_init = (0.5 * scan.p0 + rng.uniform(0.02, 0.08, size=scan.p0.shape)).astype(np.float32)
@@ -242,7 +242,7 @@ def run_native(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    scan, p_init, poses_init = make_workload(seed_offset=rank)
+    scan, p_init, poses_init = make_workload(seed_offset=rank, n_frames=args.frames)
     geom = scan.geom
     pairs, m = pairs_and_m(geom)
 
@@ -367,6 +367,8 @@ def run_native(args):
         "e2e": e2e,
         "final_loss": float(loss.item()),
     }
+    if args.frames != 64:
+        out["config"]["workload"] += f" (profiling case: {args.frames} frames, not a bench line)"
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(scan, p_init, poses_init)
     if rank == 0:
@@ -384,6 +386,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--frames", type=int, default=64,
+                    help="frames of the scan (64 = the benchmark workload; fewer only for ncu captures)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
