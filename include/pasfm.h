@@ -165,6 +165,32 @@ int pasfm_step(pasfm_ctx* ctx, const pasfm_geom* geom, void* p0, double* pose, c
                const void* meas, const uint8_t* mask, pasfm_adam* state, double* loss_out,
                void* stream);
 
+/* Allocation-free pose gradient.  No counterpart in the paper: this is a
+ * library service for callers that must not allocate device memory while they
+ * run -- code hosted inside an application that owns all device memory through
+ * its own pool, or a real-time loop that cannot afford the latency and implicit
+ * synchronisation of cudaMalloc/cudaFree.  It computes what pasfm_pose_grad
+ * computes (same arguments minus the context, same kernels and results) but
+ * keeps all of its scratch in one fixed array of PASFM_NOALLOC_SCRATCH_BYTES
+ * that the library declares at file scope in device memory; every GPU that
+ * loads the library holds that array until the process exits.  It calls no
+ * allocation routine.
+ *  - Needs F*E*(48 + 24*ncubes) + 256 bytes of scratch (24 fewer per trace when
+ *    gelem_out is given), ncubes = number of 16^3 (or 8^3 on coarse grids) voxel
+ *    cubes; larger problems return PASFM_EUNSUPPORTED with a message.
+ *  - The first call on each device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture.
+ *  - All calls share the one array, which keeps what the last call left in it;
+ *    calls whose work overlaps on the GPU (other streams, other host threads)
+ *    race on it.  Serialise them.
+ *  - The element-inside-grid check runs but is not reported (there is no
+ *    context status word); outputs are then unspecified, accesses stay in bounds. */
+#define PASFM_NOALLOC_SCRATCH_BYTES (64u * 1024u * 1024u)
+int pasfm_pose_grad_noalloc(const pasfm_geom* geom, const void* p0, const double* elem, const double* pose,
+                            const void* g, const uint8_t* mask, double* grad6_out, double* gelem_out,
+                            void* stream);
+
 /* Synchronise `stream` and read (then clear) the context's device status word.
  * *bits receives the PASFM_STATUS_* bits seen (may be NULL).  Returns
  * PASFM_OK, PASFM_ETIMEOUT or PASFM_EDEVICE. */

@@ -66,6 +66,7 @@ _SIGS = {
     "pasfm_pose_grad": ([_VP, _G, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP], _I),
     "pasfm_loss": ([_VP, _G, _VP, _VP, _VP, _VP, _VP, _VP], _I),
     "pasfm_step": ([_VP, _G, _VP, _VP, _VP, _VP, _VP, ctypes.POINTER(PasfmAdam), _VP, _VP], _I),
+    "pasfm_pose_grad_noalloc": ([_G, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP], _I),
     "pasfm_status": ([_VP, _VP, ctypes.POINTER(ctypes.c_uint32)], _I),
     "pasfm_timing_enable": ([_VP, _I], _I),
     "pasfm_timing_reset": ([_VP], _I),
@@ -184,6 +185,17 @@ def pasfm_step(ctx, geom, p0, pose, elem, meas, mask, adam: PasfmAdam, loss_out=
                             _ptr(mask, torch.uint8, "mask", allow_none=True), ctypes.byref(adam),
                             _ptr(loss_out, torch.float64, "loss_out", allow_none=True),
                             _stream(stream, p0.device)))
+
+
+def pasfm_pose_grad_noalloc(geom, p0, elem, pose, g_sig, mask, grad6_out, gelem_out=None, stream=None):
+    """Pose gradient without any device allocation (fixed in-library scratch)."""
+    g = make_geom(geom, dtype_vol=p0.dtype, dtype_sig=g_sig.dtype)
+    _check(lib().pasfm_pose_grad_noalloc(ctypes.byref(g), _ptr(p0, _VOL, "p0"), _ptr(elem, torch.float64, "elem"),
+                                         _ptr(pose, torch.float64, "pose"), _ptr(g_sig, _VOL, "g"),
+                                         _ptr(mask, torch.uint8, "mask", allow_none=True),
+                                         _ptr(grad6_out, torch.float64, "grad6_out"),
+                                         _ptr(gelem_out, torch.float64, "gelem_out", allow_none=True),
+                                         _stream(stream, grad6_out.device)))
 
 
 def pasfm_status(ctx, stream=None, device=None):

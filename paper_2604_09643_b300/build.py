@@ -66,7 +66,8 @@ def build(force: bool = False, jobs: int | None = None, verbose: bool = False) -
     work = [(os.path.join(CSRC, "kernels_s.cu"), os.path.join(OBJ, f"kernels_s{s}.o"), [f"-DPASFM_S={s}"])
             for s in S_VALUES]
     work += [(os.path.join(CSRC, "aux.cu"), os.path.join(OBJ, "aux.o"), []),
-             (os.path.join(CSRC, "pasfm.cu"), os.path.join(OBJ, "pasfm.o"), [])]
+             (os.path.join(CSRC, "pasfm.cu"), os.path.join(OBJ, "pasfm.o"), []),
+             (os.path.join(CSRC, "noalloc.cu"), os.path.join(OBJ, "noalloc.o"), [])]
     jobs = jobs or max(1, min(len(work), os.cpu_count() or 1))
     with cf.ThreadPoolExecutor(jobs) as ex:
         objs = list(ex.map(_compile, work))

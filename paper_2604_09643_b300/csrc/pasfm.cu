@@ -772,3 +772,20 @@ int pasfm_timing_read(pasfm_ctx* ctx, const char* kernel, double* ms_total, int6
 int64_t pasfm_launch_count(pasfm_ctx* ctx) { return ctx ? ctx->launches : -1; }
 
 }  // extern "C"
+
+namespace pasfm {
+
+// Geometry validation and planning for entry points defined in other
+// translation units (the allocation-free pose gradient in noalloc.cu).
+int plan_geometry(const pasfm_geom* geom, Plan* pl, double* a0) {
+  Geo G;
+  TRY(check_geom(geom, &G));
+  TRY(make_plan(G, pl));
+  *a0 = G.a0;
+  return PASFM_OK;
+}
+
+// Record an error message for pasfm_last_error() from another translation unit.
+int report_error(int code, const char* msg) { return fail(code, "%s", msg); }
+
+}  // namespace pasfm
