@@ -62,11 +62,14 @@ def peaks():
                 source="measured" if p else "fallback")
 
 
+HOT_SOURCES = ("kernels.cuh", "pasfm_dev.cuh", "kernels_s.cu")
+
+
 def kernel_src_hash():
+    """Hash of the sources that define the hot kernels (bwd_cube, fwd_cube)."""
     h = hashlib.sha256()
-    csrc = os.path.join(ROOT, "paper_2604_09643_b300", "csrc")
-    for fn in sorted(os.listdir(csrc)):
-        with open(os.path.join(csrc, fn), "rb") as fh:
+    for fn in HOT_SOURCES:
+        with open(os.path.join(ROOT, "paper_2604_09643_b300", "csrc", fn), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 

@@ -165,6 +165,18 @@ int pasfm_step(pasfm_ctx* ctx, const pasfm_geom* geom, void* p0, double* pose, c
                const void* meas, const uint8_t* mask, pasfm_adam* state, double* loss_out,
                void* stream);
 
+/* A7 support -- twist coordinates for autograd (Stage 4 rigid parameters read
+ * as an se(3) left twist xi = (w, v) on top of a base pose).
+ * pasfm_apply_twists: pose_out[f] = (Exp(w_f) R_f, Exp(w_f) t_f + v_f).
+ * pasfm_twist_grad: chain rule from grad6 (pasfm_pose_grad at the twisted pose)
+ * to xi: dL/dv = g_v, dL/dw = J_l(w)^T (g_w - v x g_v), J_l the left Jacobian
+ * of SO(3).  pose, pose_out: double [F][3][4]; xi, grad6, grad_xi_out: double
+ * [F][6]; all device memory. */
+int pasfm_apply_twists(pasfm_ctx* ctx, int n_frames, const double* pose, const double* xi, double* pose_out,
+                       void* stream);
+int pasfm_twist_grad(pasfm_ctx* ctx, int n_frames, const double* xi, const double* grad6, double* grad_xi_out,
+                     void* stream);
+
 /* Allocation-free pose gradient.  No counterpart in the paper: this is a
  * library service for callers that must not allocate device memory while they
  * run -- code hosted inside an application that owns all device memory through

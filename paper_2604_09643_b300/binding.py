@@ -66,6 +66,8 @@ _SIGS = {
     "pasfm_pose_grad": ([_VP, _G, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP], _I),
     "pasfm_loss": ([_VP, _G, _VP, _VP, _VP, _VP, _VP, _VP], _I),
     "pasfm_step": ([_VP, _G, _VP, _VP, _VP, _VP, _VP, ctypes.POINTER(PasfmAdam), _VP, _VP], _I),
+    "pasfm_apply_twists": ([_VP, _I, _VP, _VP, _VP, _VP], _I),
+    "pasfm_twist_grad": ([_VP, _I, _VP, _VP, _VP, _VP], _I),
     "pasfm_pose_grad_noalloc": ([_G, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP], _I),
     "pasfm_status": ([_VP, _VP, ctypes.POINTER(ctypes.c_uint32)], _I),
     "pasfm_timing_enable": ([_VP, _I], _I),
@@ -277,6 +279,22 @@ class Context:
 
     def step(self, geom, p0, pose, elem, meas, adam: "AdamState", mask=None, loss_out=None, stream=None):
         pasfm_step(self.handle, geom, p0, pose, elem, meas, mask, adam.c, loss_out, stream)
+
+    def apply_twists(self, pose, xi, out=None, stream=None):
+        """pose (F,3,4) with left twists xi (F,6) applied: (Exp(w) R, Exp(w) t + v)."""
+        out = torch.empty_like(pose) if out is None else out
+        _check(lib().pasfm_apply_twists(self.handle, int(pose.shape[0]), _ptr(pose, torch.float64, "pose"),
+                                        _ptr(xi, torch.float64, "xi"), _ptr(out, torch.float64, "out"),
+                                        _stream(stream, self.device)))
+        return out
+
+    def twist_grad(self, xi, grad6, out=None, stream=None):
+        """Gradient in twist coordinates from the gradient at the twisted pose."""
+        out = torch.empty_like(grad6) if out is None else out
+        _check(lib().pasfm_twist_grad(self.handle, int(xi.shape[0]), _ptr(xi, torch.float64, "xi"),
+                                      _ptr(grad6, torch.float64, "grad6"), _ptr(out, torch.float64, "out"),
+                                      _stream(stream, self.device)))
+        return out
 
     def status(self, stream=None):
         return pasfm_status(self.handle, stream, self.device)

@@ -290,3 +290,77 @@ __global__ void adam_pose_kernel(double* __restrict__ pose, const double* __rest
 }
 
 }  // namespace pasfm
+
+namespace pasfm {
+
+// Rodrigues pieces of the SO(3) exponential and its left Jacobian:
+// Exp(w) = I + A K + B K^2, J_l(w) = I + B K + C K^2, K = skew(w),
+// A = sin t / t, B = (1 - cos t) / t^2, C = (t - sin t) / t^3.
+__device__ void so3_coeffs(double w0, double w1, double w2, double* A, double* B, double* C) {
+  const double t2 = w0 * w0 + w1 * w1 + w2 * w2;
+  if (t2 < 1e-12) {  // series to O(t^4)
+    *A = 1.0 - t2 / 6.0;
+    *B = 0.5 - t2 / 24.0;
+    *C = 1.0 / 6.0 - t2 / 120.0;
+    return;
+  }
+  const double t = sqrt(t2);
+  *A = sin(t) / t;
+  *B = (1.0 - cos(t)) / t2;
+  *C = (t - sin(t)) / (t2 * t);
+}
+
+__device__ void so3_matrix(double w0, double w1, double w2, double a, double b, double M[3][3]) {
+  const double K[3][3] = {{0, -w2, w1}, {w2, 0, -w0}, {-w1, w0, 0}};
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c) {
+      double k2 = 0.0;
+      for (int q = 0; q < 3; ++q) k2 += K[r][q] * K[q][c];
+      M[r][c] = (r == c ? 1.0 : 0.0) + a * K[r][c] + b * k2;
+    }
+}
+
+// pose_out[f] = left twist xi_f applied to pose[f]: R' = Exp(w) R, t' = Exp(w) t + v.
+__global__ void apply_twist_kernel(const double* __restrict__ pose, const double* __restrict__ xi,
+                                   double* __restrict__ out, int F) {
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= F) return;
+  const double* x = xi + 6 * static_cast<int64_t>(f);
+  double A, B, C;
+  so3_coeffs(x[0], x[1], x[2], &A, &B, &C);
+  double E[3][3];
+  so3_matrix(x[0], x[1], x[2], A, B, E);
+  const double* P = pose + 12 * static_cast<int64_t>(f);
+  double o[12];
+  for (int r = 0; r < 3; ++r) {
+    for (int c = 0; c < 4; ++c) {
+      double s = 0.0;
+      for (int q = 0; q < 3; ++q) s += E[r][q] * P[4 * q + c];
+      o[4 * r + c] = s;
+    }
+    o[4 * r + 3] += x[3 + r];
+  }
+  double* Q = out + 12 * static_cast<int64_t>(f);
+  for (int k = 0; k < 12; ++k) Q[k] = o[k];
+}
+
+// Gradient in the twist coordinates from the gradient at the twisted pose:
+// dL/dv = g_v, dL/dw = J_l(w)^T (g_w - v x g_v).
+__global__ void twist_grad_kernel(const double* __restrict__ xi, const double* __restrict__ g6,
+                                  double* __restrict__ out, int F) {
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= F) return;
+  const double* x = xi + 6 * static_cast<int64_t>(f);
+  const double* g = g6 + 6 * static_cast<int64_t>(f);
+  double A, B, C;
+  so3_coeffs(x[0], x[1], x[2], &A, &B, &C);
+  double J[3][3];
+  so3_matrix(x[0], x[1], x[2], B, C, J);
+  const double r[3] = {g[0] - (x[4] * g[5] - x[5] * g[4]), g[1] - (x[5] * g[3] - x[3] * g[5]),
+                       g[2] - (x[3] * g[4] - x[4] * g[3])};
+  double* o = out + 6 * static_cast<int64_t>(f);
+  for (int c = 0; c < 3; ++c) o[c] = J[0][c] * r[0] + J[1][c] * r[1] + J[2][c] * r[2];
+  for (int c = 0; c < 3; ++c) o[3 + c] = g[3 + c];
+}
+
+}  // namespace pasfm

@@ -26,6 +26,9 @@ __global__ void adam_pose_kernel(double* pose, const double* grad6, double* m, d
                                  double b2, double bc1, double bc2, double lr_rot, double lr_trans, double eps,
                                  int fix0, int freeze);
 
+__global__ void apply_twist_kernel(const double* pose, const double* xi, double* out, int F);
+__global__ void twist_grad_kernel(const double* xi, const double* g6, double* out, int F);
+
 using FwdLaunch = cudaError_t (*)(int C, const CUtensorMap& map, const FwdParams& P, dim3 grid, int threads,
                                   size_t smem, cudaStream_t st);
 using BwdLaunch = cudaError_t (*)(int C, int mode, const CUtensorMap& map, const BwdParams& P, dim3 grid,

@@ -216,7 +216,7 @@ struct BwdLayout {
   __host__ __device__ static int refb_off(int WP) { return refa_off(WP) + 2 * kBatch * 16; }
   __host__ __device__ static int refu_off(int WP) { return refb_off(WP) + 2 * kBatch * 16; }
   __host__ __device__ static int red_off(int WP) { return refu_off(WP) + 2 * kBatch * 24; }
-  __host__ __device__ static int bar_off(int WP) { return red_off(WP) + NW * kBatch * 16; }
+  __host__ __device__ static int bar_off(int WP) { return red_off(WP) + 2 * NW * kBatch * 16; }
   __host__ __device__ static int total(int WP) { return bar_off(WP) + 16; }
 };
 
@@ -270,10 +270,11 @@ __global__ void __launch_bounds__(C* C, (C == 16 ? 2 : 8))
                    : 0.f;
     }
   }
-  float acc[ADJ ? C : 1], comp[ADJ ? C : 1], bacc[ADJ ? C : 1];
+  // adjoint: per-batch partial sums (<= 32 traces x S terms) folded once per batch
+  float acc[ADJ ? C : 1], bacc[ADJ ? C : 1];
   if (ADJ) {
 #pragma unroll
-    for (int k = 0; k < C; ++k) acc[k] = comp[k] = bacc[k] = 0.f;
+    for (int k = 0; k < C; ++k) acc[k] = bacc[k] = 0.f;
   }
 
   const double hc = 0.5 * (C - 1);
@@ -288,7 +289,7 @@ __global__ void __launch_bounds__(C* C, (C == 16 ? 2 : 8))
   }
   __syncthreads();
 
-  // producer: warp 0 stages batch b into buffer buf
+  // producer: one warp stages batch b into buffer buf (lane l handles trace l)
   auto issue = [&](int b, int buf) {
     const int it = b * kBatch + lane;
     const int cnt = min(kBatch, P.n_items - b * kBatch);
@@ -334,21 +335,21 @@ __global__ void __launch_bounds__(C* C, (C == 16 ? 2 : 8))
     if (nb > 1) issue(1, 1);
   }
 
+  // One block barrier per batch.  After the barrier of batch b, warp b % NW
+  // (rotating, so the extra work is spread over the warps) reduces batch b's
+  // pose partials and restages buffer b & 1 with batch b + 2, while the other
+  // warps already compute batch b + 1.  The warp-reduction slots are
+  // double-buffered; the reducing warp's program order keeps its reads of
+  // refs[buf] ahead of its producer writes.  A timed-out wait makes every
+  // thread skip the compute, and the barrier (an OR vote) ends the CTA.
   const unsigned max_idx = static_cast<unsigned>(WP - S);
   bool clamped = false;
   for (int b = 0; b < nb; ++b) {
     const int buf = b & 1;
     const bool ok = mbar_wait_bounded(&bar[buf], (b >> 1) & 1, P.status);
-    if (__syncthreads_or(!ok)) {
-      if (tid == 0) {  // let copies in flight land before the CTA exits
-        mbar_wait_bounded(&bar[buf], (b >> 1) & 1, P.status);
-        if (b + 1 < nb) mbar_wait_bounded(&bar[buf ^ 1], ((b + 1) >> 1) & 1, P.status);
-      }
-      return;
-    }
     const int cnt = min(kBatch, P.n_items - b * kBatch);
     const float* wb = win + buf * kBatch * WP;
-    for (int e = 0; e < cnt; ++e) {
+    for (int e = 0; ok && e < cnt; ++e) {
       const float4 ra = refa[buf * kBatch + e];
       const float4 rb = refb[buf * kBatch + e];
       const int offs = __float_as_int(rb.z);
@@ -396,38 +397,43 @@ __global__ void __launch_bounds__(C* C, (C == 16 ? 2 : 8))
           R2 += __shfl_xor_sync(0xffffffffu, R2, o);
           R3 += __shfl_xor_sync(0xffffffffu, R3, o);
         }
-        if (lane == 0) red[warp * kBatch + e] = make_float4(R0, R1, R2, R3);
+        if (lane == 0) red[(buf * L::NW + warp) * kBatch + e] = make_float4(R0, R1, R2, R3);
       }
     }
-    if (ADJ) {  // fold the batch into a compensated per-voxel sum
+    if (ADJ) {  // fold the batch partial (<= 32 traces x S terms) into the voxel sum
 #pragma unroll
       for (int k = 0; k < C; ++k) {
-        const float y = bacc[k] - comp[k];
-        const float t = acc[k] + y;
-        comp[k] = (t - acc[k]) - y;
-        acc[k] = t;
+        acc[k] += bacc[k];
         bacc[k] = 0.f;
       }
     }
-    __syncthreads();
-    if (POSE && tid < cnt) {
-      double r0 = 0.0, r1 = 0.0, r2 = 0.0, r3 = 0.0;
-      for (int w = 0; w < L::NW; ++w) {
-        const float4 v = red[w * kBatch + tid];
-        r0 += v.x;
-        r1 += v.y;
-        r2 += v.z;
-        r3 += v.w;
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) {  // let copies in flight land before the CTA exits
+        mbar_wait_bounded(&bar[buf], (b >> 1) & 1, P.status);
+        if (b + 1 < nb) mbar_wait_bounded(&bar[buf ^ 1], ((b + 1) >> 1) & 1, P.status);
       }
-      const float mk = refb[buf * kBatch + tid].w;
-      const double* u = refu + (buf * kBatch + tid) * 3;
-      double* gp = P.gpart + (static_cast<int64_t>(b * kBatch + tid) * ncubes + c) * 3;
-      gp[0] = mk * (u[0] * r0 - r1);
-      gp[1] = mk * (u[1] * r0 - r2);
-      gp[2] = mk * (u[2] * r0 - r3);
+      return;
     }
-    __syncthreads();
-    if (warp == 0 && b + 2 < nb) issue(b + 2, buf);
+    if (warp == b % L::NW) {
+      if (POSE && lane < cnt) {
+        double r0 = 0.0, r1 = 0.0, r2 = 0.0, r3 = 0.0;
+        for (int w = 0; w < L::NW; ++w) {
+          const float4 v = red[(buf * L::NW + w) * kBatch + lane];
+          r0 += v.x;
+          r1 += v.y;
+          r2 += v.z;
+          r3 += v.w;
+        }
+        const float mk = refb[buf * kBatch + lane].w;
+        const double* u = refu + (buf * kBatch + lane) * 3;
+        double* gp = P.gpart + (static_cast<int64_t>(b * kBatch + lane) * ncubes + c) * 3;
+        gp[0] = mk * (u[0] * r0 - r1);
+        gp[1] = mk * (u[1] * r0 - r2);
+        gp[2] = mk * (u[2] * r0 - r3);
+      }
+      __syncwarp();
+      if (b + 2 < nb) issue(b + 2, buf);
+    }
   }
   if (clamped) atomicOr(P.status, PASFM_STATUS_INDEX_CLAMPED);
 
@@ -437,7 +443,7 @@ __global__ void __launch_bounds__(C* C, (C == 16 ? 2 : 8))
     for (int k = 0; k < C; ++k) {
       const int ix = cx * C + k;
       if (ix < P.nx) {
-        const float v = (acc[k] - comp[k]) * P.scale;
+        const float v = acc[k] * P.scale;
         out[ix] = P.accumulate ? out[ix] + v : v;
       }
     }

@@ -722,6 +722,34 @@ int pasfm_step(pasfm_ctx* ctx, const pasfm_geom* geom, void* p0, double* pose, c
   return PASFM_OK;
 }
 
+int pasfm_apply_twists(pasfm_ctx* ctx, int n_frames, const double* pose, const double* xi, double* pose_out,
+                       void* stream) {
+  if (!ctx) return fail(PASFM_EINVAL, "ctx is NULL");
+  if (n_frames < 0) return fail(PASFM_EINVAL, "negative frame count");
+  if (n_frames == 0) return PASFM_OK;
+  if (!pose || !xi || !pose_out) return fail(PASFM_EINVAL, "NULL array argument");
+  TRY(set_device(ctx));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaEvent_t t = ctx->begin(st);
+  apply_twist_kernel<<<(n_frames + 127) / 128, 128, 0, st>>>(pose, xi, pose_out, n_frames);
+  ctx->end("apply_twist", t, st);
+  return check_launch("apply_twist");
+}
+
+int pasfm_twist_grad(pasfm_ctx* ctx, int n_frames, const double* xi, const double* grad6, double* grad_xi_out,
+                     void* stream) {
+  if (!ctx) return fail(PASFM_EINVAL, "ctx is NULL");
+  if (n_frames < 0) return fail(PASFM_EINVAL, "negative frame count");
+  if (n_frames == 0) return PASFM_OK;
+  if (!xi || !grad6 || !grad_xi_out) return fail(PASFM_EINVAL, "NULL array argument");
+  TRY(set_device(ctx));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaEvent_t t = ctx->begin(st);
+  twist_grad_kernel<<<(n_frames + 127) / 128, 128, 0, st>>>(xi, grad6, grad_xi_out, n_frames);
+  ctx->end("twist_grad", t, st);
+  return check_launch("twist_grad");
+}
+
 int pasfm_status(pasfm_ctx* ctx, void* stream, uint32_t* bits) {
   if (!ctx) return fail(PASFM_EINVAL, "ctx is NULL");
   TRY(set_device(ctx));
