@@ -177,6 +177,14 @@ int pasfm_apply_twists(pasfm_ctx* ctx, int n_frames, const double* pose, const d
 int pasfm_twist_grad(pasfm_ctx* ctx, int n_frames, const double* xi, const double* grad6, double* grad_xi_out,
                      void* stream);
 
+/* A8 support -- trilinear resampling of a float volume between two voxel
+ * grids (coarse-to-fine level change of the volume estimate).  Only the grid
+ * fields of the two geometries are used; destination voxel centres outside the
+ * source's outermost centres take the clamped (edge) value.  src: float
+ * [sz][sy][sx], dst: float [nz][ny][nx], device memory, must not overlap. */
+int pasfm_resample(pasfm_ctx* ctx, const pasfm_geom* src_geom, const float* src, const pasfm_geom* dst_geom,
+                   float* dst, void* stream);
+
 /* Allocation-free pose gradient.  No counterpart in the paper: this is a
  * library service for callers that must not allocate device memory while they
  * run -- code hosted inside an application that owns all device memory through

@@ -68,6 +68,7 @@ _SIGS = {
     "pasfm_step": ([_VP, _G, _VP, _VP, _VP, _VP, _VP, ctypes.POINTER(PasfmAdam), _VP, _VP], _I),
     "pasfm_apply_twists": ([_VP, _I, _VP, _VP, _VP, _VP], _I),
     "pasfm_twist_grad": ([_VP, _I, _VP, _VP, _VP, _VP], _I),
+    "pasfm_resample": ([_VP, _G, _VP, _G, _VP, _VP], _I),
     "pasfm_pose_grad_noalloc": ([_G, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP], _I),
     "pasfm_status": ([_VP, _VP, ctypes.POINTER(ctypes.c_uint32)], _I),
     "pasfm_timing_enable": ([_VP, _I], _I),
@@ -294,6 +295,15 @@ class Context:
         _check(lib().pasfm_twist_grad(self.handle, int(xi.shape[0]), _ptr(xi, torch.float64, "xi"),
                                       _ptr(grad6, torch.float64, "grad6"), _ptr(out, torch.float64, "out"),
                                       _stream(stream, self.device)))
+        return out
+
+    def resample(self, src_geom, src, dst_geom, out=None, stream=None):
+        """Trilinear resampling of a float volume onto another voxel grid."""
+        shape = (dst_geom["nz"], dst_geom["ny"], dst_geom["nx"])
+        out = torch.empty(shape, dtype=torch.float32, device=self.device) if out is None else out
+        gs, gd = make_geom(src_geom), make_geom(dst_geom)
+        _check(lib().pasfm_resample(self.handle, ctypes.byref(gs), _ptr(src, torch.float32, "src"),
+                                    ctypes.byref(gd), _ptr(out, torch.float32, "out"), _stream(stream, self.device)))
         return out
 
     def status(self, stream=None):

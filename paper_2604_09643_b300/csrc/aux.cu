@@ -364,3 +364,39 @@ __global__ void twist_grad_kernel(const double* __restrict__ xi, const double* _
 }
 
 }  // namespace pasfm
+
+namespace pasfm {
+
+// Trilinear resampling between voxel-centred grids covering the same world
+// region (coarse-to-fine level change): dst(r) = src interpolated at r, with
+// coordinates clamped to the source's outermost voxel centres.
+__global__ void resample_kernel(const float* __restrict__ src, int sx, int sy, int sz, double sox, double soy,
+                                double soz, double sdx, double sdy, double sdz, float* __restrict__ dst, int nx,
+                                int ny, int nz, double ox, double oy, double oz, double dx, double dy, double dz) {
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int64_t n = static_cast<int64_t>(nx) * ny * nz;
+  if (i >= n) return;
+  const int ix = static_cast<int>(i % nx), iy = static_cast<int>((i / nx) % ny), iz = static_cast<int>(i / (int64_t(nx) * ny));
+  const double u[3] = {(ox + dx * ix - sox) / sdx, (oy + dy * iy - soy) / sdy, (oz + dz * iz - soz) / sdz};
+  const int lim[3] = {sx, sy, sz};
+  int i0[3];
+  double w[3];
+  for (int a = 0; a < 3; ++a) {
+    const double c = fmin(fmax(u[a], 0.0), static_cast<double>(lim[a] - 1));
+    int k = static_cast<int>(floor(c));
+    if (k > lim[a] - 2) k = max(lim[a] - 2, 0);
+    i0[a] = k;
+    w[a] = lim[a] > 1 ? c - k : 0.0;
+  }
+  double acc = 0.0;
+  for (int cz = 0; cz < 2; ++cz)
+    for (int cy = 0; cy < 2; ++cy)
+      for (int cx = 0; cx < 2; ++cx) {
+        const int jx = min(i0[0] + cx, sx - 1), jy = min(i0[1] + cy, sy - 1), jz = min(i0[2] + cz, sz - 1);
+        const double wt = (cx ? w[0] : 1.0 - w[0]) * (cy ? w[1] : 1.0 - w[1]) * (cz ? w[2] : 1.0 - w[2]);
+        acc += wt * src[(static_cast<int64_t>(jz) * sy + jy) * sx + jx];
+      }
+  dst[i] = static_cast<float>(acc);
+}
+
+}  // namespace pasfm

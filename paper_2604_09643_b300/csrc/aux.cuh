@@ -29,6 +29,10 @@ __global__ void adam_pose_kernel(double* pose, const double* grad6, double* m, d
 __global__ void apply_twist_kernel(const double* pose, const double* xi, double* out, int F);
 __global__ void twist_grad_kernel(const double* xi, const double* g6, double* out, int F);
 
+__global__ void resample_kernel(const float* src, int sx, int sy, int sz, double sox, double soy, double soz,
+                                double sdx, double sdy, double sdz, float* dst, int nx, int ny, int nz, double ox,
+                                double oy, double oz, double dx, double dy, double dz);
+
 using FwdLaunch = cudaError_t (*)(int C, const CUtensorMap& map, const FwdParams& P, dim3 grid, int threads,
                                   size_t smem, cudaStream_t st);
 using BwdLaunch = cudaError_t (*)(int C, int mode, const CUtensorMap& map, const BwdParams& P, dim3 grid,

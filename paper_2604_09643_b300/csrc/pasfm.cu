@@ -750,6 +750,27 @@ int pasfm_twist_grad(pasfm_ctx* ctx, int n_frames, const double* xi, const doubl
   return check_launch("twist_grad");
 }
 
+int pasfm_resample(pasfm_ctx* ctx, const pasfm_geom* src_geom, const float* src, const pasfm_geom* dst_geom,
+                   float* dst, void* stream) {
+  if (!ctx || !src_geom || !dst_geom) return fail(PASFM_EINVAL, "NULL argument");
+  Geo S, D;
+  TRY(check_geom(src_geom, &S));
+  TRY(check_geom(dst_geom, &D));
+  if (D.nvox == 0) return PASFM_OK;
+  if (S.nvox == 0) return fail(PASFM_EINVAL, "empty source grid");
+  if (!src || !dst) return fail(PASFM_EINVAL, "NULL array argument");
+  TRY(set_device(ctx));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const pasfm_geom& a = *src_geom;
+  const pasfm_geom& b = *dst_geom;
+  cudaEvent_t t = ctx->begin(st);
+  resample_kernel<<<static_cast<unsigned>((D.nvox + 255) / 256), 256, 0, st>>>(
+      src, a.nx, a.ny, a.nz, a.ox, a.oy, a.oz, a.dx, a.dy, a.dz, dst, b.nx, b.ny, b.nz, b.ox, b.oy, b.oz, b.dx,
+      b.dy, b.dz);
+  ctx->end("resample", t, st);
+  return check_launch("resample");
+}
+
 int pasfm_status(pasfm_ctx* ctx, void* stream, uint32_t* bits) {
   if (!ctx) return fail(PASFM_EINVAL, "ctx is NULL");
   TRY(set_device(ctx));

@@ -1,0 +1,204 @@
+"""Coarse-to-fine joint reconstruction of the source volume and the frame poses.
+
+The paper's pipeline (Algorithm 1) reconstructs P_c with Adam on the Eq. 2
+data term, localises sensors from gradients of the radiation engine (Stage 2),
+snaps noisy sensor estimates onto the rigid array template with a RANSAC whose
+subsets are pre-checked on pairwise edge lengths before a Kabsch fit (Stage 3),
+and refines the rigid parameters with an inlier-masked loss (Stage 4, Eq. 4).
+Here those pieces drive a joint optimisation over every frame:
+
+* Levels: the volume estimate lives on a pyramid of grids over the same world
+  box (for example 64^3 -> 128^3 -> 256^3), each with sphere radius a0 = spacing / 2.
+  A coarse level has wider pulses, which smooths the loss like the paper's
+  decaying kernel width.  Since (4/3) pi a0^3 / spacing^3 = pi / 6 on every level,
+  the estimate carries over by trilinear resampling without rescaling.
+* Steps: each is one ``pasfm_step``: forward, inlier-masked loss head, fused
+  adjoint + pose gradient, Adam on the volume (projected to p0 >= 0) and on the
+  frame twists.  Frame 0 is the gauge, held at its known pose like the paper's
+  Pose A.
+* Rigid consensus, every ``refine_every`` steps:
+  1. Each element proposes a position one fixed-length step down its own
+     gradient (the per-sensor gradient step of Stage 2).
+  2. Per frame, RANSAC over 3-element subsets runs the edge-length pre-check,
+     then a Kabsch fit, to pick the rigid pose most elements agree with.
+  3. Its inliers become the loss mask of Eq. 4.
+  4. A frame whose consensus pose moves its elements by more than
+     ``reset_mm`` from the current pose is reset to the consensus pose (rigid
+     outlier rejection).
+
+The paper leaves the thresholds, step sizes, iteration counts and the subset
+sampler unstated; they are fields of :class:`C2FConfig`.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+import time
+
+import numpy as np
+import torch
+
+from . import binding
+
+
+# ----------------------------------------------------------------------------- rigid-body pieces
+
+def kabsch(src, dst, weights=None):
+    """Rotation R and translation t minimising sum w |R src_i + t - dst_i|^2 (det R = +1)."""
+    src = np.asarray(src, dtype=np.float64)
+    dst = np.asarray(dst, dtype=np.float64)
+    w = np.ones(len(src)) if weights is None else np.asarray(weights, dtype=np.float64)
+    w = w / w.sum()
+    cs = w @ src
+    cd = w @ dst
+    cov = (src - cs).T @ ((dst - cd) * w[:, None])
+    u, _, vt = np.linalg.svd(cov)
+    d = 1.0 if np.linalg.det(vt.T @ u.T) >= 0 else -1.0
+    rot = vt.T @ np.diag([1.0, 1.0, d]) @ u.T
+    return rot, cd - rot @ cs
+
+
+def edge_precheck(template, observed, subset, tol_mm):
+    """True when every pairwise distance in the subset matches the template within tol."""
+    s = list(subset)
+    for a in range(len(s)):
+        for b in range(a + 1, len(s)):
+            lt = math.dist(template[s[a]], template[s[b]])
+            lo = math.dist(observed[s[a]], observed[s[b]])
+            if abs(lt - lo) > tol_mm:
+                return False
+    return True
+
+
+def ransac(template, observed, subsets, edge_tol_mm, inlier_tol_mm):
+    """Stage 3 consensus over the given subsets.  Returns (R, t, inlier mask, winning
+    subset index or -1); the winner is the first subset with the most inliers, and
+    the returned fit is refitted on its inliers."""
+    template = np.asarray(template, dtype=np.float64)
+    observed = np.asarray(observed, dtype=np.float64)
+    best_n, best_i, best_mask = -1, -1, None
+    for i, sub in enumerate(subsets):
+        if not edge_precheck(template, observed, sub, edge_tol_mm):
+            continue
+        rot, tr = kabsch(template[list(sub)], observed[list(sub)])
+        err = np.linalg.norm(template @ rot.T + tr - observed, axis=1)
+        inl = err < inlier_tol_mm
+        if int(inl.sum()) > best_n:
+            best_n, best_i, best_mask = int(inl.sum()), i, inl
+    if best_i < 0 or best_n < 3:
+        return np.eye(3), np.zeros(3), np.zeros(len(template), dtype=bool), -1
+    rot, tr = kabsch(template[best_mask], observed[best_mask])
+    return rot, tr, best_mask, best_i
+
+
+# ----------------------------------------------------------------------------- levels
+
+def level_geometry(geom, shape):
+    """Grid of `shape` = (nz, ny, nx) covering the same world box as `geom`'s voxels,
+    with a0 = half the smallest spacing (the inscribed sphere)."""
+    nz, ny, nx = (int(s) for s in shape)
+    out = dict(geom)
+    for ax, n in (("x", nx), ("y", ny), ("z", nz)):
+        lo = geom["o" + ax] - 0.5 * geom["d" + ax]
+        ext = geom["n" + ax] * geom["d" + ax]
+        d = ext / n
+        out["n" + ax] = n
+        out["d" + ax] = d
+        out["o" + ax] = lo + 0.5 * d
+    out["a0_mm"] = 0.5 * min(out["dx"], out["dy"], out["dz"])
+    return out
+
+
+@dataclasses.dataclass
+class C2FConfig:
+    levels: tuple = ((64, 64, 64), (128, 128, 128), (256, 256, 256))
+    steps: tuple = (100, 100, 100)
+    lr_vol: float = 0.02
+    lr_rot: float = 2e-3
+    lr_trans: float = 2e-2
+    lr_decay: float = 0.5          # learning-rate factor applied per level
+    init_value: float = 0.0
+    nonneg: bool = True
+    fix_frame0: bool = True
+    refine_every: int = 0          # 0 disables the rigid-consensus pass
+    elem_step_mm: float = 0.05
+    edge_tol_mm: float = 0.05
+    inlier_tol_mm: float = 0.1
+    reset_mm: float = 0.3
+    n_subsets: int = 64
+    seed: int = 0
+
+
+def element_errors(elem, poses_a, poses_b):
+    """Mean distance (mm) between element positions under two pose sets."""
+    pa = np.einsum("fab,jb->fja", poses_a[:, :, :3], elem) + poses_a[:, None, :, 3]
+    pb = np.einsum("fab,jb->fja", poses_b[:, :, :3], elem) + poses_b[:, None, :, 3]
+    return float(np.linalg.norm(pa - pb, axis=-1).mean())
+
+
+def rigid_consensus(ctx, geom, p0, poses, elem, meas, mask, cfg: C2FConfig, rng):
+    """One Stage 2/3 pass; returns (new inlier mask, poses) on the device."""
+    F, E = geom["n_frames"], geom["n_elem"]
+    sig = ctx.forward(geom, p0, elem, poses)
+    _, g = ctx.loss(geom, sig, meas, mask)
+    _, G = ctx.pose_grad(geom, p0, elem, poses, g, mask, want_elem=True)
+    G = G.cpu().numpy()
+    P = poses.cpu().numpy()
+    tmpl = elem.cpu().numpy()
+    x = np.einsum("fab,jb->fja", P[:, :, :3], tmpl) + P[:, None, :, 3]
+    new_mask = np.ones((F, E), dtype=np.uint8)
+    first = 1 if cfg.fix_frame0 else 0
+    for f in range(first, F):
+        gn = np.linalg.norm(G[f], axis=1)
+        if gn.max() <= 0:
+            continue
+        prop = x[f] - cfg.elem_step_mm * G[f] / gn.max()
+        subsets = [rng.choice(E, size=3, replace=False) for _ in range(cfg.n_subsets)]
+        rot, tr, inl, k = ransac(tmpl, prop, subsets, cfg.edge_tol_mm, cfg.inlier_tol_mm)
+        if k < 0:
+            continue
+        new_mask[f] = inl.astype(np.uint8)
+        cons = tmpl @ rot.T + tr
+        if np.linalg.norm(cons - x[f], axis=1).max() > cfg.reset_mm:
+            P[f, :, :3] = rot
+            P[f, :, 3] = tr
+    poses.copy_(torch.from_numpy(P))
+    return torch.from_numpy(new_mask).to(poses.device), poses
+
+
+def reconstruct(ctx: binding.Context, geom_fine, elem, meas, poses_init, cfg: C2FConfig = C2FConfig(),
+                truth_poses=None, log=None):
+    """Joint coarse-to-fine reconstruction.  meas: float [F][E][Nt] on the device.
+    Returns (p0 on the finest level, poses [F][3][4] float64, history list)."""
+    dev = ctx.device
+    poses = torch.as_tensor(np.asarray(poses_init, dtype=np.float64)).to(dev).contiguous()
+    elem_d = torch.as_tensor(np.asarray(elem, dtype=np.float64)).to(dev).contiguous()
+    elem_np = np.asarray(elem, dtype=np.float64)
+    rng = np.random.default_rng(cfg.seed)
+    history = []
+    p0, prev_geom, mask = None, None, None
+    loss = torch.zeros((), dtype=torch.float64, device=dev)
+    for li, (shape, n_steps) in enumerate(zip(cfg.levels, cfg.steps)):
+        geom = level_geometry(geom_fine, shape)
+        if p0 is None:
+            p0 = torch.full(tuple(shape), cfg.init_value, dtype=torch.float32, device=dev)
+        else:
+            p0 = ctx.resample(prev_geom, p0, geom)
+        decay = cfg.lr_decay ** li
+        adam = binding.AdamState(geom, dev, lr_vol=cfg.lr_vol * decay, lr_rot=cfg.lr_rot * decay,
+                                 lr_trans=cfg.lr_trans * decay, nonneg=cfg.nonneg, fix_frame0=cfg.fix_frame0)
+        t0 = time.perf_counter()
+        for k in range(n_steps):
+            ctx.step(geom, p0, poses, elem_d, meas, adam, mask=mask, loss_out=loss)
+            if cfg.refine_every and (k + 1) % cfg.refine_every == 0:
+                mask, poses = rigid_consensus(ctx, geom, p0, poses, elem_d, meas, mask, cfg, rng)
+        torch.cuda.synchronize(dev)
+        rec = {"level": li, "shape": list(shape), "steps": n_steps, "loss": float(loss),
+               "seconds": time.perf_counter() - t0}
+        if truth_poses is not None:
+            rec["mean_element_error_mm"] = element_errors(elem_np, poses.cpu().numpy(), np.asarray(truth_poses))
+        history.append(rec)
+        if log:
+            log(rec)
+        prev_geom = geom
+    return p0, poses, history

@@ -1,0 +1,228 @@
+"""Continuous-batching reconstruction server over the radiation operator.
+
+Freehand scans arrive as requests, each asking for a number of gradient steps of
+the joint volume + pose reconstruction.  The server:
+
+* admits a waiting request when its device footprint fits the free HBM (minus a
+  reserve), refuses with a status one that could never fit, and otherwise keeps
+  it queued until running scans finish and release memory;
+* keeps every admitted scan resident: its volume, poses, measurements, Adam
+  state and a private library context (workspace) on its own CUDA stream;
+* each iteration keeps up to ``inflight`` steps enqueued per scan, so kernels
+  of different scans overlap on the device, and admits new arrivals between
+  iterations (continuous batching rather than a queue drained one by one);
+* times every step with CUDA events on the scan's stream, records queue wait,
+  and reports p50/p99 step latency and aggregate steps/s;
+* isolates failures: a scan whose loss turns non-finite or whose device status
+  word is set is stopped and released while the others continue.
+
+All scans use deterministic kernels with private workspaces, so a scan's result
+does not depend on what else is running.
+"""
+from __future__ import annotations
+
+import dataclasses
+import time
+from collections import deque
+
+import numpy as np
+import torch
+
+from . import binding
+
+ADMIT, WAIT, REJECT = "admit", "wait", "reject"
+
+
+def admission(footprint, free, total, reserve):
+    """Decision for one request given device memory figures (bytes)."""
+    if footprint + reserve > total:
+        return REJECT
+    if footprint + reserve > free:
+        return WAIT
+    return ADMIT
+
+
+def footprint_bytes(geom):
+    """Device bytes a resident scan needs: library workspace plus its arrays."""
+    import ctypes
+    g = binding.make_geom(geom)
+    ws = ctypes.c_size_t(0)
+    binding._check(binding.lib().pasfm_workspace_size(ctypes.byref(g), ctypes.byref(ws)))
+    nvox = geom["nx"] * geom["ny"] * geom["nz"]
+    F, E, T = geom["n_frames"], geom["n_elem"], geom["n_samples"]
+    arrays = nvox * 4 * 3 + F * E * T * 4 + F * 96 * 3 + E * 24 + 1024
+    return int(ws.value + arrays)
+
+
+@dataclasses.dataclass
+class Request:
+    """One reconstruction request: measurements, array template, starting point."""
+    id: int
+    arrival_s: float
+    geom: dict
+    elem: np.ndarray
+    meas: np.ndarray | torch.Tensor   # float32 [F][E][Nt] (host or device)
+    poses_init: np.ndarray
+    steps: int = 20
+    p0_init: np.ndarray | None = None
+    lr_vol: float = 0.02
+    lr_rot: float = 1e-3
+    lr_trans: float = 1e-2
+
+
+@dataclasses.dataclass
+class Result:
+    id: int
+    status: str
+    steps: int
+    p0: np.ndarray | None
+    poses: np.ndarray | None
+    final_loss: float
+    queue_wait_s: float
+    step_ms: list
+    admitted_s: float = 0.0
+    finished_s: float = 0.0
+
+
+class _Scan:
+    def __init__(self, req: Request, device, now):
+        self.req = req
+        self.ctx = binding.Context(device)
+        self.stream = torch.cuda.Stream(device)
+        self.admitted_s = now
+        d = self.ctx.device
+        with torch.cuda.stream(self.stream):
+            g = req.geom
+            shape = (g["nz"], g["ny"], g["nx"])
+            self.p0 = (torch.zeros(shape, dtype=torch.float32, device=d) if req.p0_init is None
+                       else torch.as_tensor(np.ascontiguousarray(req.p0_init, dtype=np.float32)).to(d))
+            self.poses = torch.as_tensor(np.ascontiguousarray(req.poses_init, dtype=np.float64)).to(d)
+            self.elem = torch.as_tensor(np.ascontiguousarray(req.elem, dtype=np.float64)).to(d)
+            self.meas = torch.as_tensor(req.meas).to(d, torch.float32).contiguous()
+            self.adam = binding.AdamState(g, d, lr_vol=req.lr_vol, lr_rot=req.lr_rot, lr_trans=req.lr_trans,
+                                          nonneg=True, fix_frame0=True)
+            self.loss = torch.zeros((), dtype=torch.float64, device=d)
+        self.ctx.reserve(req.geom)
+        self.issued = 0
+        self.events = deque()   # (start, end) per issued step, oldest first
+        self.step_ms = []
+        self.failed = None
+
+    def issue(self):
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record(self.stream)
+        self.ctx.step(self.req.geom, self.p0, self.poses, self.elem, self.meas, self.adam, loss_out=self.loss,
+                      stream=self.stream)
+        e.record(self.stream)
+        self.events.append((s, e))
+        self.issued += 1
+
+    def poll(self):
+        while self.events and self.events[0][1].query():
+            s, e = self.events.popleft()
+            self.step_ms.append(s.elapsed_time(e))
+
+    def done(self):
+        return self.issued >= self.req.steps and not self.events
+
+    def finish(self, now, wait_s):
+        self.stream.synchronize()
+        rc, bits = self.ctx.status(self.stream)
+        loss = float(self.loss.item())
+        status = "ok"
+        if rc != 0:
+            status = f"failed: device status {bits:#x}"
+        elif not np.isfinite(loss):
+            status = "failed: non-finite loss"
+        ok = status == "ok"
+        res = Result(self.req.id, status, self.issued, self.p0.cpu().numpy() if ok else None,
+                     self.poses.cpu().numpy() if ok else None, loss, wait_s, list(self.step_ms),
+                     self.admitted_s, now)
+        self.release()
+        return res
+
+    def release(self):
+        self.ctx.close()
+        self.p0 = self.poses = self.elem = self.meas = self.adam = self.loss = None
+
+
+class Server:
+    """Admit, run and retire reconstruction requests on one GPU."""
+
+    def __init__(self, device=0, reserve_bytes=2 << 30, max_active=16, inflight=2, mem_info=None,
+                 clock=time.perf_counter):
+        self.device = torch.device("cuda", device) if isinstance(device, int) else device
+        self.reserve = reserve_bytes
+        self.max_active = max_active
+        self.inflight = inflight
+        self.mem_info = mem_info or (lambda: torch.cuda.mem_get_info(self.device))
+        self.clock = clock
+        self.queue = deque()
+        self.active = []
+        self.results = []
+        self.t0 = None
+
+    def submit(self, req: Request):
+        self.queue.append(req)
+
+    def _now(self):
+        return self.clock() - self.t0
+
+    def _admit(self):
+        while self.queue and len(self.active) < self.max_active:
+            req = self.queue[0]
+            if req.arrival_s > self._now():
+                return
+            free, total = self.mem_info()
+            need = footprint_bytes(req.geom)
+            dec = admission(need, free, total, self.reserve)
+            if dec == REJECT:
+                self.queue.popleft()
+                self.results.append(Result(req.id, f"rejected: needs {need} bytes, device has {total}", 0,
+                                           None, None, float("nan"), self._now() - req.arrival_s, []))
+                continue
+            if dec == WAIT:
+                return
+            self.queue.popleft()
+            self.active.append((_Scan(req, self.device, self._now()), self._now() - req.arrival_s))
+
+    def run(self, max_seconds=None):
+        """Serve until the queue and the active set are empty (or max_seconds)."""
+        self.t0 = self.clock()
+        while self.queue or self.active:
+            self._admit()
+            for scan, _ in self.active:
+                scan.poll()
+                while scan.issued < scan.req.steps and len(scan.events) < self.inflight:
+                    scan.issue()
+            keep = []
+            for scan, wait in self.active:
+                scan.poll()
+                if scan.done():
+                    self.results.append(scan.finish(self._now(), wait))
+                else:
+                    keep.append((scan, wait))
+            self.active = keep
+            if not self.active and self.queue:
+                delay = self.queue[0].arrival_s - self._now()
+                if delay > 0:
+                    time.sleep(min(delay, 0.05))
+            elif self.active:
+                time.sleep(0.0005)
+            if max_seconds is not None and self._now() > max_seconds:
+                break
+        return self.results
+
+    def report(self):
+        ok = [r for r in self.results if r.status == "ok"]
+        lat = [m for r in ok for m in r.step_ms]
+        waits = [r.queue_wait_s for r in ok]
+        wall = max((r.finished_s for r in ok), default=0.0)
+        steps = sum(r.steps for r in ok)
+        pct = lambda v, q: float(np.percentile(v, q)) if v else None
+        return {"requests": len(self.results), "completed": len(ok),
+                "rejected": sum(r.status.startswith("rejected") for r in self.results),
+                "failed": sum(r.status.startswith("failed") for r in self.results),
+                "steps": steps, "wall_s": wall, "steps_per_s": steps / wall if wall > 0 else None,
+                "step_ms_p50": pct(lat, 50), "step_ms_p99": pct(lat, 99),
+                "queue_wait_s_p50": pct(waits, 50), "queue_wait_s_p99": pct(waits, 99)}

@@ -62,10 +62,13 @@ def test_autograd_gradients_match_oracle(cuda_device):
         gxi = txi.grad.cpu().numpy()
         assert ctx.status()[0] == 0
     L0, r, posed = _oracle_loss(geom, p0, elem, base, xi, meas)
-    assert abs(float(loss) - L0) <= 1e-5 * L0
+    assert abs(float(loss.detach()) - L0) <= 1e-5 * L0
     ref_p0 = oracle.adjoint(geom, r, oracle.element_positions(geom, elem, posed))
     assert rel_l2(gp0, ref_p0) < 2e-5  # residual of two FP32 traces, then the adjoint
-    eps = 1e-6
+    # small step: the loss is only piecewise smooth (support-edge kinks), and a
+    # 1e-8 rad / mm step lets few pairs straddle a kink while FP64 round-off
+    # stays near 1e-6 relative
+    eps = 1e-8
     for f in range(2):
         fd = np.zeros(6)
         for k in range(6):

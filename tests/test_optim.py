@@ -1,0 +1,54 @@
+"""Host-side pieces of the coarse-to-fine optimiser (CPU): pyramid geometry and the
+Stage 3 rigid consensus against the oracle's independent Kabsch / RANSAC."""
+import numpy as np
+
+from oracle import rigid
+from paper_2604_09643_b300 import optim, synth
+
+
+def test_level_geometry_keeps_the_world_box():
+    g = synth.make_geom((256, 256, 256), 0.1, 256, 4, 2048)
+    for n in (64, 128, 256):
+        lg = optim.level_geometry(g, (n, n, n))
+        for ax in "xyz":
+            lo = lg["o" + ax] - 0.5 * lg["d" + ax]
+            hi = lo + lg["n" + ax] * lg["d" + ax]
+            assert abs(lo - (g["o" + ax] - 0.05)) < 1e-12 and abs(hi - (-lo)) < 1e-12
+        assert abs(lg["a0_mm"] - 0.5 * 25.6 / n) < 1e-12
+        # pi/6 fill factor of the inscribed sphere is level-invariant
+        assert abs(4 / 3 * np.pi * lg["a0_mm"] ** 3 / lg["dx"] ** 3 - np.pi / 6) < 1e-12
+
+
+def test_kabsch_matches_oracle():
+    rng = np.random.default_rng(0)
+    P = rng.normal(size=(20, 3))
+    R = rigid.so3_exp(rng.normal(size=3))
+    Q = P @ R.T + rng.normal(size=3) + 0.01 * rng.normal(size=(20, 3))
+    w = rng.uniform(0.5, 2, size=20)
+    r1, t1 = optim.kabsch(P, Q, w)
+    r2, t2 = rigid.kabsch(P, Q, w)
+    assert np.abs(r1 - r2).max() < 1e-12 and np.abs(t1 - t2).max() < 1e-12
+
+
+def test_ransac_matches_oracle_on_the_same_subsets():
+    rng = np.random.default_rng(1)
+    tmpl = synth.planar_array(8, 8, 0.6)
+    R = rigid.so3_exp([0.05, -0.1, 0.2])
+    obs = tmpl @ R.T + np.array([0.3, -0.2, 9.0]) + 0.005 * rng.normal(size=(64, 3))
+    bad = rng.choice(64, size=12, replace=False)
+    obs[bad] += rng.normal(scale=0.5, size=(12, 3))
+    subsets = [rng.choice(64, size=3, replace=False) for _ in range(100)]
+    r1, t1, m1, k1 = optim.ransac(tmpl, obs, subsets, 0.05, 0.05)
+    r2, t2, m2, k2 = rigid.ransac_consensus(tmpl, obs, subsets, 0.05, 0.05)
+    assert k1 == k2 >= 0 and np.array_equal(m1, m2)
+    assert np.abs(r1 - r2).max() < 1e-12 and np.abs(t1 - t2).max() < 1e-12
+    assert not m1[bad].any()
+
+
+def test_element_errors():
+    poses = synth.sweep_poses(3, 0.3, 8.0, np.random.default_rng(2))
+    elem = synth.planar_array(4, 4, 0.5)
+    assert optim.element_errors(elem, poses, poses) == 0.0
+    moved = poses.copy()
+    moved[:, 0, 3] += 0.1
+    assert abs(optim.element_errors(elem, poses, moved) - 0.1) < 1e-12

@@ -1,0 +1,39 @@
+"""Serving scheduler host logic (CPU): admission policy and refusal without any GPU work."""
+import numpy as np
+
+from paper_2604_09643_b300 import serve, synth
+
+
+def test_admission_policy():
+    GB = 1 << 30
+    assert serve.admission(10 * GB, 100 * GB, 200 * GB, 2 * GB) == serve.ADMIT
+    assert serve.admission(10 * GB, 11 * GB, 200 * GB, 2 * GB) == serve.WAIT
+    assert serve.admission(199 * GB, 200 * GB, 200 * GB, 2 * GB) == serve.REJECT
+
+
+def test_footprint_grows_with_the_scan():
+    small = synth.make_geom((64, 64, 64), 0.1, 64, 16, 1024)
+    big = synth.make_geom((256, 256, 256), 0.1, 1024, 256, 3072)
+    assert 0 < serve.footprint_bytes(small) < serve.footprint_bytes(big)
+
+
+def _req(i, n=32, F=4):
+    geom = synth.make_geom((n, n, n), 0.2, 16, F, 256)
+    return serve.Request(i, 0.0, geom, synth.planar_array(4, 4, 0.5),
+                         np.zeros((F, 16, 256), np.float32), np.tile(np.eye(3, 4), (F, 1, 1)), steps=2)
+
+
+def test_oversize_request_is_refused_with_a_status():
+    GB = 1 << 30
+    srv = serve.Server(device=0, reserve_bytes=0, mem_info=lambda: (GB // 1024, GB // 1024))
+    srv.submit(_req(0))
+    res = srv.run(max_seconds=1.0)
+    assert len(res) == 1 and res[0].status.startswith("rejected")
+
+
+def test_request_that_does_not_fit_now_waits():
+    GB = 1 << 30
+    srv = serve.Server(device=0, reserve_bytes=0, mem_info=lambda: (0, 100 * GB))
+    srv.submit(_req(0))
+    res = srv.run(max_seconds=0.2)
+    assert res == [] and len(srv.queue) == 1

@@ -1,0 +1,62 @@
+"""Serving scheduler on the GPU: continuous batching of scans of different sizes.
+A scan's result is bit-identical alone and in the mix; a failing scan is isolated."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2604_09643_b300 import binding, serve, synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _request(i, n, m, F, T, arrival, steps=6, poison=False):
+    geom = synth.make_geom((n, n, n), 0.1, m * m, F, T)
+    rng = np.random.default_rng(200 + i)
+    p0 = synth.vessel_tree_phantom(geom, 6, rng)
+    elem = synth.planar_array(m, m, 0.5)
+    poses = synth.sweep_poses(F, 0.3, synth.top_face_z(geom) + 4.0, np.random.default_rng(300 + i))
+    with binding.Context(0) as ctx:
+        meas = ctx.forward(geom, torch.tensor(p0, device="cuda"), torch.tensor(elem, device="cuda"),
+                           torch.tensor(poses, device="cuda")).cpu().numpy()
+    if poison:
+        meas[0, 0, :] = np.nan
+    init = synth.perturb_poses(poses, np.random.default_rng(400 + i), 0.5, 0.05, keep_first=True)
+    return serve.Request(i, arrival, geom, elem, meas, init, steps=steps,
+                         p0_init=np.full(p0.shape, 0.05, np.float32))
+
+
+def _requests():
+    return [_request(0, 48, 8, 6, 1024, 0.0), _request(1, 32, 16, 4, 768, 0.0),
+            _request(2, 40, 4, 8, 1024, 0.05), _request(3, 24, 8, 3, 512, 0.1)]
+
+
+def test_results_are_identical_alone_and_in_the_mix(cuda_device):
+    reqs = _requests()
+    alone = {}
+    for r in reqs:
+        srv = serve.Server(device=0)
+        srv.submit(r)
+        res = srv.run()
+        assert res[0].status == "ok"
+        alone[r.id] = res[0]
+    srv = serve.Server(device=0, inflight=2)
+    for r in reqs:
+        srv.submit(r)
+    mixed = {r.id: r for r in srv.run()}
+    for i, a in alone.items():
+        b = mixed[i]
+        assert b.status == "ok" and b.steps == a.steps
+        assert np.array_equal(a.p0, b.p0) and np.array_equal(a.poses, b.poses)
+        assert a.final_loss == b.final_loss
+    rep = srv.report()
+    assert rep["completed"] == 4 and rep["step_ms_p50"] > 0 and rep["step_ms_p99"] >= rep["step_ms_p50"]
+
+
+def test_failing_scan_is_isolated(cuda_device):
+    reqs = _requests()[:2] + [_request(9, 32, 8, 4, 512, 0.0, poison=True)]
+    srv = serve.Server(device=0)
+    for r in reqs:
+        srv.submit(r)
+    res = {r.id: r for r in srv.run()}
+    assert res[9].status.startswith("failed")
+    assert res[0].status == "ok" and res[1].status == "ok"
