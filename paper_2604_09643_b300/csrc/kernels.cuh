@@ -35,24 +35,23 @@ namespace pasfm {
 // per-pair slot math
 // ------------------------------------------------------------------------
 struct PairMath {
-  float rs;     // 1 / d
-  float ns;     // first slot relative to N_c (float)
-  int nsi;      // first slot relative to N_c
-  float beta0;  // lower boundary of the first slot (mm), <= -a0
+  float rs;       // 1 / d
+  unsigned idx;   // first slot's index in the window (before clamping)
+  float beta0;    // lower boundary of the first slot (mm), <= -a0
 };
 
+// idx_bias = kMagicBits + (window slot 0 relative to N_c), so that
+// idx = n_s - (slot 0) comes out of the rounding trick with one integer op.
 __device__ __forceinline__ PairMath pair_math(float A, float dc2, float dcf, float phim, float inv_h, float h,
-                                              float cb) {
+                                              float cb, int idx_bias) {
   PairMath m;
   const float D2 = dc2 + A;
   m.rs = rsqrtf(D2);
-  const float d = D2 * m.rs;
-  const float del = __fdividef(A, d + dcf);  // d - d_c without cancellation
-  const float psi = fmaf(del, inv_h, phim);  // psi_c - N_c - 1/2 + delta / h
-  const float t = psi + kMagic;              // round to nearest = floor(psi + 1/2)
-  m.ns = t - kMagic;
-  m.nsi = __float_as_int(t) - kMagicBits;
-  m.beta0 = fmaf(m.ns - psi, h, cb);         // (n_s - psi_full) h - a0
+  const float del = __fdividef(A, fmaf(D2, m.rs, dcf));  // d - d_c = A / (d + d_c), no cancellation
+  const float psi = fmaf(del, inv_h, phim);               // psi_c - N_c - 1/2 + delta / h
+  const float t = psi + kMagic;                           // round to nearest = floor(psi + 1/2)
+  m.idx = static_cast<unsigned>(__float_as_int(t) - idx_bias);
+  m.beta0 = fmaf((t - kMagic) - psi, h, cb);              // (n_s - psi_full) h - a0
   return m;
 }
 
@@ -142,7 +141,8 @@ __global__ void __launch_bounds__(256, 2)
 
   // 5. pair loop: every voxel of the cube against this lane's element
   const unsigned max_idx = static_cast<unsigned>(P.W - S);
-  bool clamped = false;
+  const int idx_bias = kMagicBits + nb_rel;
+  unsigned seen = 0;  // largest raw index (a negative one wraps to a huge value)
   for (int lz = 0; lz < C; ++lz) {
     const float qz = (lz - 0.5f * (C - 1)) * dzf;
     const float Cz = qz * (qz + R.m2uz);
@@ -157,11 +157,9 @@ __global__ void __launch_bounds__(256, 2)
         const float pv[4] = {pv4.x, pv4.y, pv4.z, pv4.w};
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-          const PairMath m = pair_math(Pix[i4 + u] + Crow, R.dc2, R.dcf, R.phim, P.inv_hf, P.h, P.cb);
-          unsigned idx = static_cast<unsigned>(m.nsi - nb_rel);
-          clamped |= idx > max_idx;
-          idx = min(idx, max_idx);
-          float* slot = col + idx * kWarp;
+          const PairMath m = pair_math(Pix[i4 + u] + Crow, R.dc2, R.dcf, R.phim, P.inv_hf, P.h, P.cb, idx_bias);
+          seen = max(seen, m.idx);
+          float* slot = col + min(m.idx, max_idx) * kWarp;
           const float s = pv[u] * m.rs;
           float beta = m.beta0;
           float bprev = P.a0sq;
@@ -182,7 +180,7 @@ __global__ void __launch_bounds__(256, 2)
       }
     }
   }
-  if (clamped) atomicOr(P.status, PASFM_STATUS_INDEX_CLAMPED);
+  if (seen > max_idx) atomicOr(P.status, PASFM_STATUS_INDEX_CLAMPED);
 
   // 6. flush the window as this cube's partial trace (scaled by 1 / (4 h))
   __syncwarp();
@@ -343,7 +341,7 @@ __global__ void __launch_bounds__(C* C, (C == 16 ? 2 : 8))
   // refs[buf] ahead of its producer writes.  A timed-out wait makes every
   // thread skip the compute, and the barrier (an OR vote) ends the CTA.
   const unsigned max_idx = static_cast<unsigned>(WP - S);
-  bool clamped = false;
+  unsigned seen = 0;  // largest raw window index (a negative one wraps to a huge value)
   for (int b = 0; b < nb; ++b) {
     const int buf = b & 1;
     const bool ok = mbar_wait_bounded(&bar[buf], (b >> 1) & 1, P.status);
@@ -352,20 +350,19 @@ __global__ void __launch_bounds__(C* C, (C == 16 ? 2 : 8))
     for (int e = 0; ok && e < cnt; ++e) {
       const float4 ra = refa[buf * kBatch + e];
       const float4 rb = refb[buf * kBatch + e];
-      const int offs = __float_as_int(rb.z);
+      const int idx_bias = kMagicBits - __float_as_int(rb.z);
       const float* wv = wb + e * WP;
       const float Crow = fmaf(qy, qy + ra.y, qz * (qz + ra.z));
       float R0 = 0.f, R1 = 0.f;
 #pragma unroll
       for (int k = 0; k < C; ++k) {
         const float A = fmaf(qx[k], qx[k] + ra.x, Crow);
-        const PairMath m = pair_math(A, ra.w, rb.x, rb.y, P.inv_hf, P.h, P.cb);
-        unsigned idx = static_cast<unsigned>(m.nsi + offs);
-        clamped |= idx > max_idx;
-        idx = min(idx, max_idx);
+        const PairMath m = pair_math(A, ra.w, rb.x, rb.y, P.inv_hf, P.h, P.cb, idx_bias);
+        seen = max(seen, m.idx);
+        const float* gw = wv + min(m.idx, max_idx);
         float g[S];
 #pragma unroll
-        for (int s = 0; s < S; ++s) g[s] = wv[idx + s];
+        for (int s = 0; s < S; ++s) g[s] = gw[s];
         float beta = m.beta0;
         float S1 = P.a0sq * (g[0] - g[S - 1]);
         float S2 = 0.f;
@@ -435,7 +432,7 @@ __global__ void __launch_bounds__(C* C, (C == 16 ? 2 : 8))
       if (b + 2 < nb) issue(b + 2, buf);
     }
   }
-  if (clamped) atomicOr(P.status, PASFM_STATUS_INDEX_CLAMPED);
+  if (seen > max_idx) atomicOr(P.status, PASFM_STATUS_INDEX_CLAMPED);
 
   if (ADJ && row_in) {
     float* out = P.vol + (static_cast<int64_t>(iz) * P.ny + iy) * P.nx;
