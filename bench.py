@@ -151,10 +151,16 @@ class ClockSampler:
 
 # ----------------------------------------------------------------------------- workload
 
-def make_workload(seed_offset=0, n_frames=64):
+WORKLOAD_MIXED = "mixed_precision_256x256x128_0.1mm_vessel150_32x32_0.3mm_400f_3072s"
+
+
+def make_workload(seed_offset=0, n_frames=64, workload="full_scan"):
     from paper_2604_09643_b300 import synth
 
-    scan = synth.full_scan(seed_offset=seed_offset, n_frames=n_frames)
+    if workload == "mixed_precision":
+        scan = synth.mixed_precision_scan(n_frames=n_frames, seed_offset=seed_offset)
+    else:
+        scan = synth.full_scan(seed_offset=seed_offset, n_frames=n_frames)
     rng = np.random.default_rng(synth.SEED_NOISE + 20 + seed_offset)
     # dense starting iterate: damped truth plus a uniform background
     p_init = (0.5 * scan.p0 + rng.uniform(0.02, 0.08, size=scan.p0.shape)).astype(np.float32)
@@ -245,7 +251,9 @@ def run_native(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    scan, p_init, poses_init = make_workload(seed_offset=rank, n_frames=args.frames)
+    frames = args.frames if args.frames else (400 if args.workload == "mixed_precision" else 64)
+    scan, p_init, poses_init = make_workload(seed_offset=rank, n_frames=frames, workload=args.workload)
+    store = {"f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16}[args.storage]
     geom = scan.geom
     pairs, m = pairs_and_m(geom)
 
@@ -254,9 +262,9 @@ def run_native(args):
 
     ctx = binding.Context(local)
     elem = to_dev(scan.elem)
-    meas = ctx.forward(geom, to_dev(scan.p0), elem, to_dev(scan.poses))
+    meas = ctx.forward(geom, to_dev(scan.p0), elem, to_dev(scan.poses)).to(store)
     ctx.reserve(geom)
-    p0 = to_dev(p_init)
+    p0 = to_dev(p_init).to(store)
     poses = to_dev(poses_init)
     adam = binding.AdamState(geom, dev, lr_vol=2e-3, lr_rot=2e-4, lr_trans=2e-3, nonneg=True, fix_frame0=True)
     loss = torch.zeros((), dtype=torch.float64, device=dev)
@@ -354,8 +362,11 @@ def run_native(args):
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "voxels": [geom["nz"], geom["ny"], geom["nx"]],
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if args.storage == "f32" else f"f32 (volume and measurements stored {args.storage})",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD if args.workload == "full_scan" else WORKLOAD_MIXED,
+                   "voxels": [geom["nz"], geom["ny"], geom["nx"]],
                    "elements": geom["n_elem"], "frames": geom["n_frames"], "samples": geom["n_samples"],
                    "global_batch": world, "parallelism": f"replicas{world}",
                    "l2": "inputs larger than L2 (128 MiB measurements, 128 MiB residual, "
@@ -370,9 +381,9 @@ def run_native(args):
         "e2e": e2e,
         "final_loss": float(loss.item()),
     }
-    if args.frames != 64:
+    if args.frames:
         out["config"]["workload"] += f" (profiling case: {args.frames} frames, not a bench line)"
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "full_scan":
         out["cpu_baseline"] = cpu_baseline(scan, p_init, poses_init)
     if rank == 0:
         print(json.dumps(out))
@@ -389,8 +400,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--frames", type=int, default=64,
-                    help="frames of the scan (64 = the benchmark workload; fewer only for ncu captures)")
+    ap.add_argument("--frames", type=int, default=0,
+                    help="override the frame count (only for small ncu captures; not a bench line)")
+    ap.add_argument("--workload", choices=["full_scan", "mixed_precision"], default="full_scan",
+                    help="full_scan: the benchmark; mixed_precision: 256x256x128, 32x32 elements, 400 frames")
+    ap.add_argument("--storage", choices=["f32", "bf16", "f16"], default="f32",
+                    help="storage type of the volume and the measurements (arithmetic stays FP32)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

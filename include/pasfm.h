@@ -185,6 +185,16 @@ int pasfm_twist_grad(pasfm_ctx* ctx, int n_frames, const double* xi, const doubl
 int pasfm_resample(pasfm_ctx* ctx, const pasfm_geom* src_geom, const float* src, const pasfm_geom* dst_geom,
                    float* dst, void* stream);
 
+/* A8 support -- Gaussian low-pass of every trace along time: the coarse levels
+ * of the coarse-to-fine optimiser fit their wider pulses to band-limited data
+ * (the data-side counterpart of the paper's decaying kernel width, Stage 2).
+ * dst[r][n] = sum_k w_k src[r][n + k], |k| <= int(4 sigma + 0.5), w_k ~
+ * exp(-k^2 / (2 sigma^2)) normalised to sum 1, zero outside the record
+ * (sigma in samples; sigma <= 0 copies).  src, dst: float [n_rows][n_samples]
+ * device memory; dst may alias src.  Synchronises `stream` before returning. */
+int pasfm_lowpass(pasfm_ctx* ctx, int64_t n_rows, int n_samples, double sigma, const float* src, float* dst,
+                  void* stream);
+
 /* Allocation-free pose gradient.  No counterpart in the paper: this is a
  * library service for callers that must not allocate device memory while they
  * run -- code hosted inside an application that owns all device memory through

@@ -69,6 +69,7 @@ _SIGS = {
     "pasfm_apply_twists": ([_VP, _I, _VP, _VP, _VP, _VP], _I),
     "pasfm_twist_grad": ([_VP, _I, _VP, _VP, _VP, _VP], _I),
     "pasfm_resample": ([_VP, _G, _VP, _G, _VP, _VP], _I),
+    "pasfm_lowpass": ([_VP, ctypes.c_int64, _I, ctypes.c_double, _VP, _VP, _VP], _I),
     "pasfm_pose_grad_noalloc": ([_G, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP], _I),
     "pasfm_status": ([_VP, _VP, ctypes.POINTER(ctypes.c_uint32)], _I),
     "pasfm_timing_enable": ([_VP, _I], _I),
@@ -304,6 +305,15 @@ class Context:
         gs, gd = make_geom(src_geom), make_geom(dst_geom)
         _check(lib().pasfm_resample(self.handle, ctypes.byref(gs), _ptr(src, torch.float32, "src"),
                                     ctypes.byref(gd), _ptr(out, torch.float32, "out"), _stream(stream, self.device)))
+        return out
+
+    def lowpass(self, sig, sigma, out=None, stream=None):
+        """Gaussian low-pass (sigma in samples) of every trace of sig [..., Nt]."""
+        out = torch.empty_like(sig) if out is None else out
+        rows = sig.numel() // sig.shape[-1] if sig.numel() else 0
+        _check(lib().pasfm_lowpass(self.handle, int(rows), int(sig.shape[-1]), float(sigma),
+                                   _ptr(sig, torch.float32, "sig"), _ptr(out, torch.float32, "out"),
+                                   _stream(stream, self.device)))
         return out
 
     def status(self, stream=None):

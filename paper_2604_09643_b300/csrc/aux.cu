@@ -400,3 +400,26 @@ __global__ void resample_kernel(const float* __restrict__ src, int sx, int sy, i
 }
 
 }  // namespace pasfm
+
+namespace pasfm {
+
+// Gaussian low-pass along the time axis of every trace (coarse levels of the
+// coarse-to-fine optimiser compare their wider pulses with band-limited data):
+// dst[n] = sum_k w_k src[n + k], |k| <= r, w_k ~ exp(-k^2 / (2 sigma^2)) summing
+// to 1, samples outside the record taken as zero.  One block per trace; the
+// trace is staged in shared memory, so dst may alias src.
+__global__ void __launch_bounds__(256) lowpass_kernel(const float* src, float* dst, int Nt, int r,
+                                                      const float* __restrict__ w) {
+  extern __shared__ float row[];
+  const int64_t base = static_cast<int64_t>(blockIdx.x) * Nt;
+  for (int n = threadIdx.x; n < Nt; n += blockDim.x) row[n] = src[base + n];
+  __syncthreads();
+  for (int n = threadIdx.x; n < Nt; n += blockDim.x) {
+    float acc = 0.f;
+    const int k0 = max(-r, -n), k1 = min(r, Nt - 1 - n);
+    for (int k = k0; k <= k1; ++k) acc = fmaf(w[k + r], row[n + k], acc);
+    dst[base + n] = acc;
+  }
+}
+
+}  // namespace pasfm

@@ -33,6 +33,8 @@ __global__ void resample_kernel(const float* src, int sx, int sy, int sz, double
                                 double sdx, double sdy, double sdz, float* dst, int nx, int ny, int nz, double ox,
                                 double oy, double oz, double dx, double dy, double dz);
 
+__global__ void lowpass_kernel(const float* src, float* dst, int Nt, int r, const float* w);
+
 using FwdLaunch = cudaError_t (*)(int C, const CUtensorMap& map, const FwdParams& P, dim3 grid, int threads,
                                   size_t smem, cudaStream_t st);
 using BwdLaunch = cudaError_t (*)(int C, int mode, const CUtensorMap& map, const BwdParams& P, dim3 grid,

@@ -166,7 +166,7 @@ int frames_per_chunk(size_t per_frame, size_t budget, int F) {
 struct pasfm_ctx {
   int device = 0;
   unsigned* status = nullptr;
-  Buf xw, part, n0, gres, vgrad, gpart, G, grad6, lpart, lscalar;
+  Buf xw, part, n0, gres, vgrad, gpart, G, grad6, lpart, lscalar, taps;
   size_t budget = kDefaultPartialBudget;
   bool timing = false;
   std::vector<Rec> recs;
@@ -500,7 +500,7 @@ int pasfm_destroy(pasfm_ctx* ctx) {
   if (!ctx) return PASFM_OK;
   cudaSetDevice(ctx->device);
   for (Buf* b : {&ctx->xw, &ctx->part, &ctx->n0, &ctx->gres, &ctx->vgrad, &ctx->gpart, &ctx->G, &ctx->grad6,
-                 &ctx->lpart, &ctx->lscalar})
+                 &ctx->lpart, &ctx->lscalar, &ctx->taps})
     if (b->p) cudaFree(b->p);
   for (auto& r : ctx->recs) {
     cudaEventDestroy(r.a);
@@ -769,6 +769,38 @@ int pasfm_resample(pasfm_ctx* ctx, const pasfm_geom* src_geom, const float* src,
       b.dy, b.dz);
   ctx->end("resample", t, st);
   return check_launch("resample");
+}
+
+int pasfm_lowpass(pasfm_ctx* ctx, int64_t n_rows, int n_samples, double sigma, const float* src, float* dst,
+                  void* stream) {
+  if (!ctx) return fail(PASFM_EINVAL, "ctx is NULL");
+  if (n_rows < 0 || n_samples < 0 || !std::isfinite(sigma)) return fail(PASFM_EINVAL, "bad size or sigma");
+  if (n_rows == 0 || n_samples == 0) return PASFM_OK;
+  if (!src || !dst) return fail(PASFM_EINVAL, "NULL array argument");
+  if (n_rows > INT32_MAX) return fail(PASFM_EUNSUPPORTED, "too many traces");
+  if (size_t(n_samples) * 4 > 200 * 1024) return fail(PASFM_EUNSUPPORTED, "trace longer than 51200 samples");
+  TRY(set_device(ctx));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // Gaussian taps, radius int(4 sigma + 0.5), normalised to sum 1 (sigma <= 0: identity)
+  const int r = sigma > 0 ? static_cast<int>(4.0 * sigma + 0.5) : 0;
+  if (r > 4096) return fail(PASFM_EUNSUPPORTED, "sigma too large");
+  std::vector<float> w(2 * r + 1);
+  double tot = 0.0;
+  for (int k = -r; k <= r; ++k) tot += r ? std::exp(-0.5 * k * k / (sigma * sigma)) : 1.0;
+  for (int k = -r; k <= r; ++k)
+    w[k + r] = static_cast<float>((r ? std::exp(-0.5 * k * k / (sigma * sigma)) : 1.0) / tot);
+  TRY(ctx->ensure(ctx->taps, w.size() * sizeof(float)));
+  CUDA_TRY(cudaMemcpyAsync(ctx->taps.p, w.data(), w.size() * sizeof(float), cudaMemcpyHostToDevice, st));
+  const size_t smem = size_t(n_samples) * 4;
+  CUDA_TRY(cudaFuncSetAttribute(lowpass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+  cudaEvent_t t = ctx->begin(st);
+  lowpass_kernel<<<static_cast<unsigned>(n_rows), 256, smem, st>>>(src, dst, n_samples, r,
+                                                                   static_cast<float*>(ctx->taps.p));
+  ctx->end("lowpass", t, st);
+  TRY(check_launch("lowpass"));
+  // the host tap buffer must outlive the asynchronous copy
+  CUDA_TRY(cudaStreamSynchronize(st));
+  return PASFM_OK;
 }
 
 int pasfm_status(pasfm_ctx* ctx, void* stream, uint32_t* bits) {

@@ -120,6 +120,8 @@ class C2FConfig:
     init_value: float = 0.0
     nonneg: bool = True
     fix_frame0: bool = True
+    lowpass: tuple | None = None   # per-level time low-pass sigma (samples); None: (a0_l - a0_fine) / h
+    volume_only: tuple | None = None  # per-level steps with poses frozen before the joint steps
     refine_every: int = 0          # 0 disables the rigid-consensus pass
     elem_step_mm: float = 0.05
     edge_tol_mm: float = 0.05
@@ -178,22 +180,32 @@ def reconstruct(ctx: binding.Context, geom_fine, elem, meas, poses_init, cfg: C2
     history = []
     p0, prev_geom, mask = None, None, None
     loss = torch.zeros((), dtype=torch.float64, device=dev)
+    h = geom_fine["c_mm_per_us"] / geom_fine["fs_mhz"]
     for li, (shape, n_steps) in enumerate(zip(cfg.levels, cfg.steps)):
         geom = level_geometry(geom_fine, shape)
         if p0 is None:
             p0 = torch.full(tuple(shape), cfg.init_value, dtype=torch.float32, device=dev)
         else:
             p0 = ctx.resample(prev_geom, p0, geom)
+        sigma = (cfg.lowpass[li] if cfg.lowpass is not None
+                 else max(0.0, (geom["a0_mm"] - geom_fine["a0_mm"]) / h))
+        meas_l = ctx.lowpass(meas, sigma) if sigma > 0 else meas
         decay = cfg.lr_decay ** li
+        t0 = time.perf_counter()
+        n_vol = cfg.volume_only[li] if cfg.volume_only is not None else 0
+        if n_vol:
+            vadam = binding.AdamState(geom, dev, lr_vol=cfg.lr_vol * decay, nonneg=cfg.nonneg, freeze_poses=True)
+            for _ in range(n_vol):
+                ctx.step(geom, p0, poses, elem_d, meas_l, vadam, mask=mask, loss_out=loss)
         adam = binding.AdamState(geom, dev, lr_vol=cfg.lr_vol * decay, lr_rot=cfg.lr_rot * decay,
                                  lr_trans=cfg.lr_trans * decay, nonneg=cfg.nonneg, fix_frame0=cfg.fix_frame0)
-        t0 = time.perf_counter()
         for k in range(n_steps):
-            ctx.step(geom, p0, poses, elem_d, meas, adam, mask=mask, loss_out=loss)
+            ctx.step(geom, p0, poses, elem_d, meas_l, adam, mask=mask, loss_out=loss)
             if cfg.refine_every and (k + 1) % cfg.refine_every == 0:
-                mask, poses = rigid_consensus(ctx, geom, p0, poses, elem_d, meas, mask, cfg, rng)
+                mask, poses = rigid_consensus(ctx, geom, p0, poses, elem_d, meas_l, mask, cfg, rng)
         torch.cuda.synchronize(dev)
-        rec = {"level": li, "shape": list(shape), "steps": n_steps, "loss": float(loss),
+        rec = {"level": li, "shape": list(shape), "steps": n_steps + n_vol, "lowpass_sigma": sigma,
+               "loss": float(loss),
                "seconds": time.perf_counter() - t0}
         if truth_poses is not None:
             rec["mean_element_error_mm"] = element_errors(elem_np, poses.cpu().numpy(), np.asarray(truth_poses))
