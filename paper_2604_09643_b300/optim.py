@@ -122,6 +122,8 @@ class C2FConfig:
     fix_frame0: bool = True
     lowpass: tuple | None = None   # per-level time low-pass sigma (samples); None: (a0_l - a0_fine) / h
     volume_only: tuple | None = None  # per-level steps with poses frozen before the joint steps
+    reference_steps: int = 0       # coarsest level: volume from the gauge frame alone (Stage 1)
+    register_steps: int = 0        # coarsest level: poses against that map, volume frozen (Stages 2-4)
     refine_every: int = 0          # 0 disables the rigid-consensus pass
     elem_step_mm: float = 0.05
     edge_tol_mm: float = 0.05
@@ -192,6 +194,19 @@ def reconstruct(ctx: binding.Context, geom_fine, elem, meas, poses_init, cfg: C2
         meas_l = ctx.lowpass(meas, sigma) if sigma > 0 else meas
         decay = cfg.lr_decay ** li
         t0 = time.perf_counter()
+        if li == 0 and cfg.reference_steps:
+            # Stage 1: reference map from the gauge frame's traces only
+            ref_mask = torch.zeros((geom["n_frames"], geom["n_elem"]), dtype=torch.uint8, device=dev)
+            ref_mask[0] = 1
+            radam = binding.AdamState(geom, dev, lr_vol=cfg.lr_vol, nonneg=cfg.nonneg, freeze_poses=True)
+            for _ in range(cfg.reference_steps):
+                ctx.step(geom, p0, poses, elem_d, meas_l, radam, mask=ref_mask, loss_out=loss)
+        if li == 0 and cfg.register_steps:
+            # Stages 2-4: every frame registered against the map, volume frozen
+            gadam = binding.AdamState(geom, dev, lr_rot=cfg.lr_rot, lr_trans=cfg.lr_trans,
+                                      fix_frame0=cfg.fix_frame0, freeze_volume=True)
+            for _ in range(cfg.register_steps):
+                ctx.step(geom, p0, poses, elem_d, meas_l, gadam, mask=mask, loss_out=loss)
         n_vol = cfg.volume_only[li] if cfg.volume_only is not None else 0
         if n_vol:
             vadam = binding.AdamState(geom, dev, lr_vol=cfg.lr_vol * decay, nonneg=cfg.nonneg, freeze_poses=True)
@@ -204,7 +219,8 @@ def reconstruct(ctx: binding.Context, geom_fine, elem, meas, poses_init, cfg: C2
             if cfg.refine_every and (k + 1) % cfg.refine_every == 0:
                 mask, poses = rigid_consensus(ctx, geom, p0, poses, elem_d, meas_l, mask, cfg, rng)
         torch.cuda.synchronize(dev)
-        rec = {"level": li, "shape": list(shape), "steps": n_steps + n_vol, "lowpass_sigma": sigma,
+        extra = (cfg.reference_steps + cfg.register_steps) if li == 0 else 0
+        rec = {"level": li, "shape": list(shape), "steps": n_steps + n_vol + extra, "lowpass_sigma": sigma,
                "loss": float(loss),
                "seconds": time.perf_counter() - t0}
         if truth_poses is not None:
