@@ -195,6 +195,15 @@ int pasfm_resample(pasfm_ctx* ctx, const pasfm_geom* src_geom, const float* src,
 int pasfm_lowpass(pasfm_ctx* ctx, int64_t n_rows, int n_samples, double sigma, const float* src, float* dst,
                   void* stream);
 
+/* NC loss of Eq. 3 as a score for candidate poses (the coarse search of Stage
+ * 2): for each of n_cand candidate trace sets sim[k] ([n_elem][n_samples] float)
+ * against one frame's measured traces meas ([n_elem][n_samples] of dtype_meas),
+ * scores_out[k] = mean over elements j with mask[j] != 0 (mask may be NULL) of
+ * -Cov(sim_kj, meas_j) / (sigma(sim_kj) sigma(meas_j)); a trace with zero
+ * variance scores 0.  Lower is better.  Device memory; scores_out: double [n_cand]. */
+int pasfm_nc_scores(pasfm_ctx* ctx, int n_cand, int n_elem, int n_samples, const float* sim, const void* meas,
+                    int dtype_meas, const uint8_t* mask, double* scores_out, void* stream);
+
 /* Allocation-free pose gradient.  No counterpart in the paper: this is a
  * library service for callers that must not allocate device memory while they
  * run -- code hosted inside an application that owns all device memory through

@@ -70,6 +70,7 @@ _SIGS = {
     "pasfm_twist_grad": ([_VP, _I, _VP, _VP, _VP, _VP], _I),
     "pasfm_resample": ([_VP, _G, _VP, _G, _VP, _VP], _I),
     "pasfm_lowpass": ([_VP, ctypes.c_int64, _I, ctypes.c_double, _VP, _VP, _VP], _I),
+    "pasfm_nc_scores": ([_VP, _I, _I, _I, _VP, _VP, _I, _VP, _VP, _VP], _I),
     "pasfm_pose_grad_noalloc": ([_G, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP], _I),
     "pasfm_status": ([_VP, _VP, ctypes.POINTER(ctypes.c_uint32)], _I),
     "pasfm_timing_enable": ([_VP, _I], _I),
@@ -314,6 +315,15 @@ class Context:
         _check(lib().pasfm_lowpass(self.handle, int(rows), int(sig.shape[-1]), float(sigma),
                                    _ptr(sig, torch.float32, "sig"), _ptr(out, torch.float32, "out"),
                                    _stream(stream, self.device)))
+        return out
+
+    def nc_scores(self, sim, meas, mask=None, out=None, stream=None):
+        """NC-loss scores of candidate trace sets sim [K][E][Nt] against meas [E][Nt]."""
+        K, E, T = (int(x) for x in sim.shape)
+        out = torch.empty(K, dtype=torch.float64, device=self.device) if out is None else out
+        _check(lib().pasfm_nc_scores(self.handle, K, E, T, _ptr(sim, torch.float32, "sim"), _ptr(meas, _VOL, "meas"),
+                                     _DTYPE_CODE[meas.dtype], _ptr(mask, torch.uint8, "mask", allow_none=True),
+                                     _ptr(out, torch.float64, "out"), _stream(stream, self.device)))
         return out
 
     def status(self, stream=None):

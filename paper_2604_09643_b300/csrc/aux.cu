@@ -423,3 +423,60 @@ __global__ void __launch_bounds__(256) lowpass_kernel(const float* src, float* d
 }
 
 }  // namespace pasfm
+
+namespace pasfm {
+
+// Negative-correlation scores (Eq. 3) of K candidate trace sets against one
+// frame's measured traces: score[k] = mean over kept elements j of
+//   -Cov(sim_kj, meas_j) / (sigma(sim_kj) sigma(meas_j)).
+// One block per candidate, one warp per element at a time; per-lane FP32 runs
+// of at most ceil(Nt / 32) terms, carried to FP64 for the moments.
+__global__ void __launch_bounds__(256) nc_scores_kernel(const float* __restrict__ sim, const void* meas,
+                                                        int dtype, const uint8_t* __restrict__ mask, int E,
+                                                        int Nt, double* __restrict__ out) {
+  __shared__ double wsum[8];
+  __shared__ int wcnt[8];
+  const int k = blockIdx.x, warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  double acc = 0.0;
+  int cnt = 0;
+  for (int j = warp; j < E; j += nw) {
+    if (mask && !mask[j]) continue;
+    const float* s = sim + (static_cast<int64_t>(k) * E + j) * Nt;
+    const int64_t mb = static_cast<int64_t>(j) * Nt;
+    float a = 0.f, b = 0.f, aa = 0.f, bb = 0.f, ab = 0.f;
+    for (int n = lane; n < Nt; n += 32) {
+      const float x = s[n], y = load_elem(meas, mb + n, dtype);
+      a += x;
+      b += y;
+      aa = fmaf(x, x, aa);
+      bb = fmaf(y, y, bb);
+      ab = fmaf(x, y, ab);
+    }
+    double m[5] = {a, b, aa, bb, ab};
+#pragma unroll
+    for (int q = 0; q < 5; ++q)
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) m[q] += __shfl_xor_sync(0xffffffffu, m[q], o);
+    const double cov = m[4] - m[0] * m[1] / Nt;
+    const double vx = m[2] - m[0] * m[0] / Nt, vy = m[3] - m[1] * m[1] / Nt;
+    const double den = sqrt(fmax(vx, 0.0) * fmax(vy, 0.0));
+    acc += den > 0.0 ? -cov / den : 0.0;
+    ++cnt;
+  }
+  if (lane == 0) {
+    wsum[warp] = acc;
+    wcnt[warp] = cnt;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    int c = 0;
+    for (int w = 0; w < nw; ++w) {
+      t += wsum[w];
+      c += wcnt[w];
+    }
+    out[k] = c ? t / c : 0.0;
+  }
+}
+
+}  // namespace pasfm

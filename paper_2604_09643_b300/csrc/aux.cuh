@@ -35,6 +35,9 @@ __global__ void resample_kernel(const float* src, int sx, int sy, int sz, double
 
 __global__ void lowpass_kernel(const float* src, float* dst, int Nt, int r, const float* w);
 
+__global__ void nc_scores_kernel(const float* sim, const void* meas, int dtype, const uint8_t* mask, int E, int Nt,
+                                 double* out);
+
 using FwdLaunch = cudaError_t (*)(int C, const CUtensorMap& map, const FwdParams& P, dim3 grid, int threads,
                                   size_t smem, cudaStream_t st);
 using BwdLaunch = cudaError_t (*)(int C, int mode, const CUtensorMap& map, const BwdParams& P, dim3 grid,

@@ -803,6 +803,22 @@ int pasfm_lowpass(pasfm_ctx* ctx, int64_t n_rows, int n_samples, double sigma, c
   return PASFM_OK;
 }
 
+int pasfm_nc_scores(pasfm_ctx* ctx, int n_cand, int n_elem, int n_samples, const float* sim, const void* meas,
+                    int dtype_meas, const uint8_t* mask, double* scores_out, void* stream) {
+  if (!ctx) return fail(PASFM_EINVAL, "ctx is NULL");
+  if (n_cand < 0 || n_elem < 0 || n_samples < 0) return fail(PASFM_EINVAL, "negative size");
+  if (dtype_meas != PASFM_F32 && dtype_meas != PASFM_BF16 && dtype_meas != PASFM_F16)
+    return fail(PASFM_EINVAL, "unknown dtype %d", dtype_meas);
+  if (n_cand == 0) return PASFM_OK;
+  if (!sim || !meas || !scores_out) return fail(PASFM_EINVAL, "NULL array argument");
+  TRY(set_device(ctx));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaEvent_t t = ctx->begin(st);
+  nc_scores_kernel<<<n_cand, 256, 0, st>>>(sim, meas, dtype_meas, mask, n_elem, n_samples, scores_out);
+  ctx->end("nc_scores", t, st);
+  return check_launch("nc_scores");
+}
+
 int pasfm_status(pasfm_ctx* ctx, void* stream, uint32_t* bits) {
   if (!ctx) return fail(PASFM_EINVAL, "ctx is NULL");
   TRY(set_device(ctx));

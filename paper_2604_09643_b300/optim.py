@@ -16,6 +16,11 @@ Here those pieces drive a joint optimisation over every frame:
   adjoint + pose gradient, Adam on the volume (projected to p0 >= 0) and on the
   frame twists.  Frame 0 is the gauge, held at its known pose like the paper's
   Pose A.
+* Coarse search (Stage 2): on the coarsest level, after its joint steps, each
+  frame's translation is re-chosen from a cubic grid of candidates scored by
+  the NC loss of Eq. 3 against that frame's (band-limited) traces, Top-1, and
+  joint steps resume; this widens the capture range beyond what gradients alone
+  reach (about half a pulse width per level).
 * Rigid consensus, every ``refine_every`` steps:
   1. Each element proposes a position one fixed-length step down its own
      gradient (the per-sensor gradient step of Stage 2).
@@ -32,6 +37,7 @@ sampler unstated; they are fields of :class:`C2FConfig`.
 from __future__ import annotations
 
 import dataclasses
+import itertools
 import math
 import time
 
@@ -124,6 +130,11 @@ class C2FConfig:
     volume_only: tuple | None = None  # per-level steps with poses frozen before the joint steps
     reference_steps: int = 0       # coarsest level: volume from the gauge frame alone (Stage 1)
     register_steps: int = 0        # coarsest level: poses against that map, volume frozen (Stages 2-4)
+    search_rounds: int = 0         # coarsest level: Stage 2 grid searches after its joint steps
+    search_radius_mm: float = 0.8  # half-width of the cubic translation grid
+    search_step_mm: float = 0.1
+    search_joint_steps: int = 150  # joint steps after each search round
+    search_batch: int = 512        # candidates per forward call
     refine_every: int = 0          # 0 disables the rigid-consensus pass
     elem_step_mm: float = 0.05
     edge_tol_mm: float = 0.05
@@ -168,6 +179,35 @@ def rigid_consensus(ctx, geom, p0, poses, elem, meas, mask, cfg: C2FConfig, rng)
             P[f, :, 3] = tr
     poses.copy_(torch.from_numpy(P))
     return torch.from_numpy(new_mask).to(poses.device), poses
+
+
+def search_translations(ctx, geom, p0, poses, elem, meas, radius_mm, step_mm, first_frame=1, batch=512,
+                        mask=None):
+    """Stage 2 coarse search: for every frame from `first_frame` on, translation
+    offsets on a cubic grid of half-width radius_mm are scored by the NC loss of
+    Eq. 3 (candidates are evaluated as extra frames of one forward call) and the
+    frame takes the best candidate (Top-1).  Returns the per-frame best scores."""
+    ax = np.arange(-radius_mm, radius_mm + 1e-9, step_mm)
+    offs = np.array(list(itertools.product(ax, ax, ax)))
+    P = poses.cpu().numpy()
+    dev = poses.device
+    best_scores = []
+    for f in range(first_frame, geom["n_frames"]):
+        best, best_pose = math.inf, None
+        for c0 in range(0, len(offs), batch):
+            o = offs[c0:c0 + batch]
+            cand = np.repeat(P[f:f + 1], len(o), axis=0)
+            cand[:, :, 3] += o
+            gk = dict(geom, n_frames=len(o))
+            sim = ctx.forward(gk, p0, elem, torch.from_numpy(cand).to(dev))
+            sc = ctx.nc_scores(sim, meas[f], None if mask is None else mask[f]).cpu().numpy()
+            i = int(np.argmin(sc))
+            if sc[i] < best:
+                best, best_pose = float(sc[i]), cand[i]
+        P[f] = best_pose
+        best_scores.append(best)
+    poses.copy_(torch.from_numpy(P).to(dev))
+    return best_scores
 
 
 def reconstruct(ctx: binding.Context, geom_fine, elem, meas, poses_init, cfg: C2FConfig = C2FConfig(),
@@ -218,9 +258,21 @@ def reconstruct(ctx: binding.Context, geom_fine, elem, meas, poses_init, cfg: C2
             ctx.step(geom, p0, poses, elem_d, meas_l, adam, mask=mask, loss_out=loss)
             if cfg.refine_every and (k + 1) % cfg.refine_every == 0:
                 mask, poses = rigid_consensus(ctx, geom, p0, poses, elem_d, meas_l, mask, cfg, rng)
+        n_search = 0
+        if li == 0:
+            for _ in range(cfg.search_rounds):
+                search_translations(ctx, geom, p0, poses, elem_d, meas_l, cfg.search_radius_mm,
+                                    cfg.search_step_mm, first_frame=1 if cfg.fix_frame0 else 0,
+                                    batch=cfg.search_batch, mask=mask)
+                adam = binding.AdamState(geom, dev, lr_vol=cfg.lr_vol * decay, lr_rot=cfg.lr_rot * decay,
+                                         lr_trans=cfg.lr_trans * decay, nonneg=cfg.nonneg,
+                                         fix_frame0=cfg.fix_frame0)
+                for _ in range(cfg.search_joint_steps):
+                    ctx.step(geom, p0, poses, elem_d, meas_l, adam, mask=mask, loss_out=loss)
+                n_search += cfg.search_joint_steps
         torch.cuda.synchronize(dev)
         extra = (cfg.reference_steps + cfg.register_steps) if li == 0 else 0
-        rec = {"level": li, "shape": list(shape), "steps": n_steps + n_vol + extra, "lowpass_sigma": sigma,
+        rec = {"level": li, "shape": list(shape), "steps": n_steps + n_vol + extra + n_search, "lowpass_sigma": sigma,
                "loss": float(loss),
                "seconds": time.perf_counter() - t0}
         if truth_poses is not None:

@@ -160,3 +160,15 @@ def test_kink_band_reduces_to_strict_gradient_and_contains_it():
     mid2, half2 = oracle.element_gradient_bounds(geom, p0, g, xw, rows, 5e-3)
     assert np.all(np.abs(strict - mid1) <= half1 * (1 + 1e-12) + 1e-15)
     assert half2.sum() >= half1.sum() > 0.0
+
+
+def test_nc_loss_invariances():
+    from oracle import nc as ncmod
+    rng = np.random.default_rng(40)
+    a = rng.standard_normal(500)
+    b = rng.standard_normal(500)
+    assert abs(ncmod.nc(a, a) + 1.0) < 1e-14
+    assert abs(ncmod.nc(a, -a) - 1.0) < 1e-14
+    assert abs(ncmod.nc(3.0 * a + 2.0, b - 5.0) - ncmod.nc(a, b)) < 1e-14
+    assert abs(ncmod.nc(a, b) + np.corrcoef(a, b)[0, 1]) < 1e-14
+    assert ncmod.nc(np.ones(10), a[:10]) == 0.0
