@@ -241,7 +241,7 @@ def run_native(args):
     import torch
     import torch.distributed as dist
 
-    from paper_2604_09643_b300 import binding
+    from paper_2604_09643_b300 import binding, replicas
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -312,12 +312,9 @@ def run_native(args):
     if rc != 0:
         raise RuntimeError(f"device status {bits:#x} in the timed region")
 
-    if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = replicas.max_over_ranks(ms, dev)
     ms_per_step = ms / args.steps
-    value = world * args.steps / (ms / 1e3)
+    value = replicas.job_throughput(args.steps, ms / 1e3, world)
 
     # ---- end to end through the public API with host buffers
     meas_host = meas.cpu().pin_memory()
@@ -336,11 +333,8 @@ def run_native(args):
         poses_host.copy_(poses, non_blocking=True)
         stream.synchronize()
     e2e_s = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = {"value": world * e2e_steps / e2e_s, "unit": UNIT,
+    e2e_s = replicas.max_over_ranks(e2e_s, dev)
+    e2e = {"value": replicas.job_throughput(e2e_steps, e2e_s, world), "unit": UNIT,
            "h2d_bytes_per_step": int(meas.numel() * meas.element_size()),
            "d2h_bytes_per_step": int(loss.element_size() + poses.numel() * poses.element_size())}
 

@@ -37,13 +37,13 @@ namespace pasfm {
 struct PairMath {
   float rs;       // 1 / d
   unsigned idx;   // first slot's index in the window (before clamping)
-  float beta0;    // lower boundary of the first slot (mm), <= -a0
+  float beta1;    // boundary between slots 0 and 1 (mm); boundary 0 is <= -a0 and never used
 };
 
 // idx_bias = kMagicBits + (window slot 0 relative to N_c), so that
 // idx = n_s - (slot 0) comes out of the rounding trick with one integer op.
 __device__ __forceinline__ PairMath pair_math(float A, float dc2, float dcf, float phim, float inv_h, float h,
-                                              float cb, int idx_bias) {
+                                              float cb1, int idx_bias) {
   PairMath m;
   const float D2 = dc2 + A;
   m.rs = rsqrtf(D2);
@@ -51,7 +51,7 @@ __device__ __forceinline__ PairMath pair_math(float A, float dc2, float dcf, flo
   const float psi = fmaf(del, inv_h, phim);               // psi_c - N_c - 1/2 + delta / h
   const float t = psi + kMagic;                           // round to nearest = floor(psi + 1/2)
   m.idx = static_cast<unsigned>(__float_as_int(t) - idx_bias);
-  m.beta0 = fmaf((t - kMagic) - psi, h, cb);              // (n_s - psi_full) h - a0
+  m.beta1 = fmaf((t - kMagic) - psi, h, cb1);             // (n_s - psi_full) h - a0 + h
   return m;
 }
 
@@ -157,11 +157,11 @@ __global__ void __launch_bounds__(256, 2)
         const float pv[4] = {pv4.x, pv4.y, pv4.z, pv4.w};
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-          const PairMath m = pair_math(Pix[i4 + u] + Crow, R.dc2, R.dcf, R.phim, P.inv_hf, P.h, P.cb, idx_bias);
+          const PairMath m = pair_math(Pix[i4 + u] + Crow, R.dc2, R.dcf, R.phim, P.inv_hf, P.h, P.cb1, idx_bias);
           seen = max(seen, m.idx);
           float* slot = col + min(m.idx, max_idx) * kWarp;
           const float s = pv[u] * m.rs;
-          float beta = m.beta0;
+          float beta = m.beta1;
           float bprev = P.a0sq;
 #pragma unroll
           for (int k = 0; k < S; ++k) {
@@ -169,7 +169,7 @@ __global__ void __launch_bounds__(256, 2)
             if (k == S - 1) {
               bk = P.a0sq;
             } else {
-              beta += P.h;
+              if (k > 0) beta += P.h;
               const float bc = (k == S - 2) ? fminf(beta, P.a0f) : beta;
               bk = bc * bc;
             }
@@ -357,18 +357,18 @@ __global__ void __launch_bounds__(C* C, (C == 16 ? 2 : 8))
 #pragma unroll
       for (int k = 0; k < C; ++k) {
         const float A = fmaf(qx[k], qx[k] + ra.x, Crow);
-        const PairMath m = pair_math(A, ra.w, rb.x, rb.y, P.inv_hf, P.h, P.cb, idx_bias);
+        const PairMath m = pair_math(A, ra.w, rb.x, rb.y, P.inv_hf, P.h, P.cb1, idx_bias);
         seen = max(seen, m.idx);
         const float* gw = wv + min(m.idx, max_idx);
         float g[S];
 #pragma unroll
         for (int s = 0; s < S; ++s) g[s] = gw[s];
-        float beta = m.beta0;
+        float beta = m.beta1;
         float S1 = P.a0sq * (g[0] - g[S - 1]);
         float S2 = 0.f;
 #pragma unroll
         for (int s = 1; s < S; ++s) {
-          beta += P.h;
+          if (s > 1) beta += P.h;
           const float dg = g[s] - g[s - 1];
           const float bc = (s == S - 1) ? fminf(beta, P.a0f) : beta;
           S1 = fmaf(bc * bc, dg, S1);
@@ -386,15 +386,18 @@ __global__ void __launch_bounds__(C* C, (C == 16 ? 2 : 8))
         }
       }
       if (POSE) {
-        float R2 = qy * R0, R3 = qz * R0;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          R0 += __shfl_xor_sync(0xffffffffu, R0, o);
-          R1 += __shfl_xor_sync(0xffffffffu, R1, o);
-          R2 += __shfl_xor_sync(0xffffffffu, R2, o);
-          R3 += __shfl_xor_sync(0xffffffffu, R3, o);
-        }
-        if (lane == 0) red[(buf * L::NW + warp) * kBatch + e] = make_float4(R0, R1, R2, R3);
+        // reduce-scatter: lanes 0-7 end with sum(R0), 8-15 sum(R1), 16-23 sum(qy R0), 24-31 sum(qz R0)
+        const float R2 = qy * R0, R3 = qz * R0;
+        const bool hi16 = lane & 16, hi8 = lane & 8;
+        const float ka = hi16 ? R2 : R0, kb = hi16 ? R3 : R1;
+        const float sa = hi16 ? R0 : R2, sb = hi16 ? R1 : R3;
+        const float A2 = ka + __shfl_xor_sync(0xffffffffu, sa, 16);
+        const float B2 = kb + __shfl_xor_sync(0xffffffffu, sb, 16);
+        float Cv = (hi8 ? B2 : A2) + __shfl_xor_sync(0xffffffffu, hi8 ? A2 : B2, 8);
+        Cv += __shfl_xor_sync(0xffffffffu, Cv, 4);
+        Cv += __shfl_xor_sync(0xffffffffu, Cv, 2);
+        Cv += __shfl_xor_sync(0xffffffffu, Cv, 1);
+        if ((lane & 7) == 0) reinterpret_cast<float*>(&red[(buf * L::NW + warp) * kBatch + e])[lane >> 3] = Cv;
       }
     }
     if (ADJ) {  // fold the batch partial (<= 32 traces x S terms) into the voxel sum

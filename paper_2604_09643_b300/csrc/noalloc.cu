@@ -198,7 +198,7 @@ extern "C" int pasfm_pose_grad_noalloc(const pasfm_geom* geom, const void* p0, c
   P.nb_shift = pl.nb_shift;
   P.scale = static_cast<float>(0.25 / pl.h);
   P.inv_hf = static_cast<float>(pl.inv_h);
-  P.cb = static_cast<float>(-a0 - 0.5 * pl.h);
+  P.cb1 = static_cast<float>(-a0 + 0.5 * pl.h);
   P.use_tma = use_tma;
   P.status = status;
   const size_t smem = pl.C == 16 ? BwdLayout<16>::total(pl.WP) : BwdLayout<8>::total(pl.WP);

@@ -310,7 +310,7 @@ int run_forward(pasfm_ctx* ctx, const Geo& G, const Plan& pl, const void* p0, co
   P.nb_shift = pl.nb_shift;
   P.p0_scale = static_cast<float>(0.25 / pl.h);
   P.inv_hf = static_cast<float>(pl.inv_h);
-  P.cb = static_cast<float>(-G.a0 - 0.5 * pl.h);
+  P.cb1 = static_cast<float>(-G.a0 + 0.5 * pl.h);
   P.use_tma = use_tma;
   P.status = ctx->status;
 
@@ -423,7 +423,7 @@ int run_backward(pasfm_ctx* ctx, const Geo& G, const Plan& pl, int mode, const v
   P.nb_shift = pl.nb_shift;
   P.scale = static_cast<float>(0.25 / pl.h);
   P.inv_hf = static_cast<float>(pl.inv_h);
-  P.cb = static_cast<float>(-G.a0 - 0.5 * pl.h);
+  P.cb1 = static_cast<float>(-G.a0 + 0.5 * pl.h);
   P.use_tma = use_tma;
   P.status = ctx->status;
   const size_t smem = pl.C == 16 ? BwdLayout<16>::total(pl.WP) : BwdLayout<8>::total(pl.WP);

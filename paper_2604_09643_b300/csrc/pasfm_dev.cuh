@@ -53,7 +53,7 @@ struct FwdParams {
   int W;
   double ox, oy, oz, dx, dy, dz;
   double tau0, inv_h, a0;
-  float h, a0f, a0sq, nb_shift, p0_scale, inv_hf, cb;
+  float h, a0f, a0sq, nb_shift, p0_scale, inv_hf, cb1;
   int use_tma;
   unsigned* status;
 };
@@ -84,7 +84,7 @@ struct BwdParams {
   int WP, accumulate;   // accumulate: add into vol instead of overwriting
   double ox, oy, oz, dx, dy, dz;
   double tau0, inv_h, a0;
-  float h, a0f, a0sq, nb_shift, scale, inv_hf, cb;
+  float h, a0f, a0sq, nb_shift, scale, inv_hf, cb1;
   int use_tma;
   unsigned* status;
 };
