@@ -33,7 +33,10 @@ class OracleGeom(ctypes.Structure):
                 ("ox", ctypes.c_double), ("oy", ctypes.c_double), ("oz", ctypes.c_double),
                 ("fs", ctypes.c_double), ("t0", ctypes.c_double), ("c", ctypes.c_double),
                 ("a0", ctypes.c_double), ("point_sampling", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("vol_pose", ctypes.c_double * 12)]
+                ("kernel", ctypes.c_int32), ("vol_pose", ctypes.c_double * 12),
+                ("sigma", ctypes.c_double)]
+
+KERNELS = {"sphere": 0, "gauss": 1}
 
 
 def build(force: bool = False) -> str:
@@ -51,6 +54,8 @@ def load(path: str):
     g = ctypes.POINTER(OracleGeom)
     dp = np.ctypeslib.ndpointer(np.float64, flags="C")
     fp = np.ctypeslib.ndpointer(np.float32, flags="C")
+    L.oracle_support.argtypes = [g]
+    L.oracle_support.restype = ctypes.c_double
     L.oracle_pulse.argtypes = [g, ctypes.c_double, ctypes.c_int]
     L.oracle_pulse.restype = ctypes.c_double
     L.oracle_pulse_dd.argtypes = [g, ctypes.c_double, ctypes.c_int]
@@ -86,6 +91,10 @@ def make_geom(geom: dict, *, point_sampling: bool = False, vol_pose=None) -> Ora
     g.fs, g.t0, g.c, g.a0 = (float(geom["fs_mhz"]), float(geom["t0_us"]),
                              float(geom["c_mm_per_us"]), float(geom["a0_mm"]))
     g.point_sampling = int(point_sampling)
+    g.kernel = KERNELS[geom.get("kernel", "sphere")]
+    g.sigma = float(geom.get("sigma_mm", 0.0))
+    if g.kernel == 1 and not g.sigma > 0:
+        raise ValueError("the Gaussian kernel needs sigma_mm > 0")
     vp = np.eye(3, 4) if vol_pose is None else np.asarray(vol_pose, dtype=np.float64)
     for k, v in enumerate(vp.reshape(12)):
         g.vol_pose[k] = float(v)
@@ -101,6 +110,11 @@ def _opt_ptr(a, dtype):
         return None, None
     arr = np.ascontiguousarray(a, dtype=dtype)
     return arr, arr.ctypes.data_as(ctypes.c_void_p)
+
+
+def support(geom) -> float:
+    """Half-width (mm) of a voxel's pulse in the distance variable: a0, or 4 sigma."""
+    return lib().oracle_support(ctypes.byref(make_geom(geom)))
 
 
 def pulse(geom, d, n, **kw) -> float:

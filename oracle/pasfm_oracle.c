@@ -24,6 +24,16 @@
  *    (Reading: the paper samples on a (detector, time) grid without saying how;
  *    point samples of a discontinuous pulse are ill-posed for gradients, so
  *    samples are interval averages.  A point-sample flag is kept for comparison.)
+ *  - Gaussian kernel (Eq. 1 and Appendix A, Eq. gaussian_far_field with the
+ *    kernel K_G of Eq. gpu_forward_model): each voxel radiates the outgoing
+ *    Gaussian pulse P(d, tau) = -w / (2 d) exp(-w^2 / (2 sigma^2)), w = tau - d,
+ *    truncated to |w| <= rho = 4 sigma (reading: the paper states no support).
+ *    Averaged over a sample interval, with E(w) = exp(-w^2 / (2 sigma^2)) and
+ *    wl, wh clamped to [-rho, rho] as above (the antiderivative of
+ *    -w E(w) / (2 d) is sigma^2 E(w) / (2 d)):
+ *        W(d, n) = sigma^2 (E(wh) - E(wl)) / (2 d h).
+ *    The uniform sphere is the same formula with the antiderivative -w^2/(4 d)
+ *    and rho = a0.
  *  - Element j of frame f sits at x_fj = R_f e_j + t_f (rigid model, Stage 4).
  *    Voxel centres are r_i = Rv (o + D (ix, iy, iz)) + tv; (Rv, tv) is identity
  *    in normal use and exists only for the rigid-invariance check.
@@ -51,43 +61,67 @@ typedef struct {
   double ox, oy, oz;
   double fs, t0, c, a0;
   int32_t point_sampling; /* 0: interval averages (default); 1: point samples */
-  int32_t reserved;
+  int32_t kernel;         /* 0: uniform sphere of radius a0; 1: Gaussian of width sigma */
   double vol_pose[12];    /* [Rv | tv] row-major; identity for normal use      */
+  double sigma;           /* Gaussian width (mm), kernel 1 only                */
 } oracle_geom;
 
 static double clampd(double w, double a) { return w < -a ? -a : (w > a ? a : w); }
+
+/* Half-width of a voxel's pulse in the distance variable: a0, or 4 sigma. */
+double oracle_support(const oracle_geom* g) { return g->kernel == 1 ? 4.0 * g->sigma : g->a0; }
+
+/* Unit-amplitude pulse at w = tau - d (zero outside the support). */
+static double point_pulse(const oracle_geom* g, double d, double w) {
+  const double rho = oracle_support(g);
+  if (fabs(w) > rho) return 0.0;
+  if (g->kernel == 1) return -w / (2.0 * d) * exp(-w * w / (2.0 * g->sigma * g->sigma));
+  return -w / (2.0 * d);
+}
+
+/* Antiderivative in w of the pulse times 2 d, at a clamped w:
+ * sphere -w^2 / 2, Gaussian sigma^2 E(w). */
+static double prim(const oracle_geom* g, double w) {
+  if (g->kernel == 1) return g->sigma * g->sigma * exp(-w * w / (2.0 * g->sigma * g->sigma));
+  return -0.5 * w * w;
+}
+
+/* Its w-derivative, -w for the sphere and -w E(w) for the Gaussian. */
+static double prim_dw(const oracle_geom* g, double w) {
+  if (g->kernel == 1) return -w * exp(-w * w / (2.0 * g->sigma * g->sigma));
+  return -w;
+}
 
 /* Sample n of the pulse of a unit-amplitude voxel observed at distance d. */
 double oracle_pulse(const oracle_geom* g, double d, int n) {
   const double h = g->c / g->fs;
   const double tau = g->c * (g->t0 + (double)n / g->fs);
-  if (g->point_sampling) {
-    const double w = tau - d;
-    return fabs(w) <= g->a0 ? -w / (2.0 * d) : 0.0;
-  }
-  const double wl = clampd(tau - 0.5 * h - d, g->a0);
-  const double wh = clampd(tau + 0.5 * h - d, g->a0);
-  return (wl * wl - wh * wh) / (4.0 * d * h);
+  if (g->point_sampling) return point_pulse(g, d, tau - d);
+  const double rho = oracle_support(g);
+  const double wl = clampd(tau - 0.5 * h - d, rho);
+  const double wh = clampd(tau + 0.5 * h - d, rho);
+  return (prim(g, wh) - prim(g, wl)) / (2.0 * d * h);
 }
 
 /* d/dd of oracle_pulse (interval averages).  A clamped end contributes nothing;
- * an end strictly inside the support moves with d. */
+ * an end strictly inside the support moves with d (dw/dd = -1). */
 double oracle_pulse_dd(const oracle_geom* g, double d, int n) {
   const double h = g->c / g->fs;
   const double tau = g->c * (g->t0 + (double)n / g->fs);
+  const double rho = oracle_support(g);
   const double rl = tau - 0.5 * h - d, rh = tau + 0.5 * h - d;
-  const double wl = clampd(rl, g->a0), wh = clampd(rh, g->a0);
-  const double W = (wl * wl - wh * wh) / (4.0 * d * h);
-  const double dl = fabs(rl) < g->a0 ? -2.0 * wl : 0.0; /* d(wl^2)/dd */
-  const double dh = fabs(rh) < g->a0 ? -2.0 * wh : 0.0; /* d(wh^2)/dd */
-  return (dl - dh) / (4.0 * d * h) - W / d;
+  const double wl = clampd(rl, rho), wh = clampd(rh, rho);
+  const double W = (prim(g, wh) - prim(g, wl)) / (2.0 * d * h);
+  const double dl = fabs(rl) < rho ? -prim_dw(g, wl) : 0.0; /* d prim(wl) / dd */
+  const double dh = fabs(rh) < rho ? -prim_dw(g, wh) : 0.0; /* d prim(wh) / dd */
+  return (dh - dl) / (2.0 * d * h) - W / d;
 }
 
-/* Superset [*lo, *hi] of the samples whose interval meets [d - a0, d + a0]. */
+/* Superset [*lo, *hi] of the samples whose interval meets [d - rho, d + rho]. */
 static int sample_range(const oracle_geom* g, double d, int* lo, int* hi) {
-  const double h = g->c / g->fs, tau0 = g->c * g->t0;
-  double a = floor((d - g->a0 - tau0) / h - 0.5) - 1.0;
-  double b = ceil((d + g->a0 - tau0) / h + 0.5) + 1.0;
+  const double h = g->c / g->fs, tau0 = g->c * g->t0, rho = oracle_support(g);
+  double a = floor((d - rho - tau0) / h - 0.5) - 1.0;
+  double b = ceil((d + rho - tau0) / h + 0.5) + 1.0;
   if (a < 0) a = 0;
   if (b > g->n_samples - 1) b = g->n_samples - 1;
   if (a > b) return 0;
@@ -118,8 +152,8 @@ void oracle_element_positions(const oracle_geom* g, const double* elem, const do
     }
 }
 
-/* Returns the number of pairs with d <= a0 (observation point inside a voxel's
- * sphere, where the exterior closed form does not hold). */
+/* Returns the number of pairs with d <= rho (observation point inside a voxel's
+ * support, where the exterior / far-field form does not hold). */
 static int64_t count_inside(const oracle_geom* g, const double* xw, int64_t fj0, int64_t fj1) {
   int64_t bad = 0;
   for (int64_t fj = fj0; fj < fj1; ++fj)
@@ -128,7 +162,7 @@ static int64_t count_inside(const oracle_geom* g, const double* xw, int64_t fj0,
         for (int ix = 0; ix < g->nx; ++ix) {
           double r[3];
           voxel_centre(g, ix, iy, iz, r);
-          if (dist3(xw + 3 * fj, r) <= g->a0) ++bad;
+          if (dist3(xw + 3 * fj, r) <= oracle_support(g)) ++bad;
         }
   return bad;
 }
@@ -227,9 +261,10 @@ void oracle_element_gradient_rows(const oracle_geom* g, const float* p0, const d
 
 /* Element gradients with their one-sided ambiguity at the support edges.
  * dW/dd jumps where a sample-interval boundary w_b = tau_b - h/2 - d crosses
- * +-a0 (the strict rule counts a boundary as moving with d only if |w_b| < a0).
- * For boundaries within eps (mm) of +-a0 both one-sided values are admissible:
- * boundary b then adds c_b = (g_b - g_{b-1}) (-2 clamp(w_b)) / (4 d h) to
+ * +-rho (the strict rule counts a boundary as moving with d only if |w_b| < rho).
+ * For boundaries within eps (mm) of +-rho both one-sided values are admissible:
+ * boundary b then adds c_b = (g_b - g_{b-1}) F'(clamp(w_b)) / (2 d h) to
+ * (F' the w-derivative of the pulse antiderivative: -w, or -w E(w))
  * sum_n g_n dW_n/dd, or nothing.  Gmid takes half of every such c_b and Ghalf
  * their half-magnitudes (componentwise, times |x - r| / d), so every choice of
  * sides lies in [Gmid - Ghalf, Gmid + Ghalf].  With eps = 0, Gmid equals the
@@ -237,7 +272,7 @@ void oracle_element_gradient_rows(const oracle_geom* g, const float* p0, const d
 void oracle_element_gradient_bounds(const oracle_geom* g, const float* p0, const double* gsig,
                                     const double* xw, const int64_t* rows, int64_t n_rows, double eps,
                                     double* Gmid, double* Ghalf) {
-  const double h = g->c / g->fs;
+  const double h = g->c / g->fs, rho = oracle_support(g);
 #pragma omp parallel for schedule(dynamic, 1)
   for (int64_t k = 0; k < n_rows; ++k) {
     const double* x = xw + 3 * rows[k];
@@ -257,10 +292,10 @@ void oracle_element_gradient_bounds(const oracle_geom* g, const float* p0, const
           for (int n = lo; n <= hi; ++n) s += gs[n] * oracle_pulse_dd(g, d, n);
           for (int b = lo; b <= hi + 1; ++b) {
             const double wb = g->c * (g->t0 + (double)b / g->fs) - 0.5 * h - d;
-            if (fabs(fabs(wb) - g->a0) >= eps) continue;
+            if (fabs(fabs(wb) - rho) >= eps) continue;
             const double gb = b <= hi ? gs[b] : 0.0, gbm = b - 1 >= lo ? gs[b - 1] : 0.0;
-            const double cb = (gb - gbm) * (-2.0 * clampd(wb, g->a0)) / (4.0 * d * h);
-            const double strict = fabs(wb) < g->a0 ? cb : 0.0;
+            const double cb = (gb - gbm) * prim_dw(g, clampd(wb, rho)) / (2.0 * d * h);
+            const double strict = fabs(wb) < rho ? cb : 0.0;
             s += 0.5 * cb - strict;
             amb += 0.5 * fabs(cb);
           }
@@ -322,4 +357,4 @@ double oracle_loss(const oracle_geom* g, const double* sig, const double* meas, 
   return L;
 }
 
-int oracle_abi_version(void) { return 1; }
+int oracle_abi_version(void) { return 2; }

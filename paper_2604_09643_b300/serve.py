@@ -82,6 +82,29 @@ class Result:
     step_ms: list
     admitted_s: float = 0.0
     finished_s: float = 0.0
+    launches: int = 0
+
+
+def request_from_spec(spec: dict, context, *, steps=4, spacing_mm=0.1, standoff_mm=4.0,
+                      rot_sigma_deg=0.5, trans_sigma_mm=0.05) -> Request:
+    """A reconstruction request from one entry of a request stream (volume side ``n``,
+    ``n_frames``, an ``m`` x ``m`` array at ``pitch`` mm, ``n_samples``, ``n_tubes``,
+    ``seed``): a vessel-tree phantom, a sweep trajectory, measurements simulated by
+    ``context.forward`` on its device at the true poses, and perturbed starting poses."""
+    from . import synth
+
+    n, F, m, T = int(spec["n"]), int(spec["n_frames"]), int(spec["m"]), int(spec["n_samples"])
+    geom = synth.make_geom((n, n, n), spacing_mm, m * m, F, T)
+    rng = np.random.default_rng(int(spec["seed"]))
+    p0 = synth.vessel_tree_phantom(geom, int(spec["n_tubes"]), rng)
+    elem = synth.planar_array(m, m, float(spec["pitch"]))
+    poses = synth.sweep_poses(F, n * spacing_mm / F, synth.top_face_z(geom) + standoff_mm, rng)  # spans the volume
+    d = context.device
+    meas = context.forward(geom, torch.as_tensor(p0).to(d), torch.as_tensor(elem).to(d),
+                           torch.as_tensor(poses).to(d))
+    init = synth.perturb_poses(poses, rng, rot_sigma_deg, trans_sigma_mm, keep_first=True)
+    return Request(int(spec["id"]), float(spec["arrival_s"]), geom, elem, meas, init, steps=steps,
+                   p0_init=np.full(p0.shape, 0.05, np.float32))
 
 
 class _Scan:
@@ -137,7 +160,7 @@ class _Scan:
         ok = status == "ok"
         res = Result(self.req.id, status, self.issued, self.p0.cpu().numpy() if ok else None,
                      self.poses.cpu().numpy() if ok else None, loss, wait_s, list(self.step_ms),
-                     self.admitted_s, now)
+                     self.admitted_s, now, self.ctx.launch_count())
         self.release()
         return res
 
@@ -224,5 +247,6 @@ class Server:
                 "rejected": sum(r.status.startswith("rejected") for r in self.results),
                 "failed": sum(r.status.startswith("failed") for r in self.results),
                 "steps": steps, "wall_s": wall, "steps_per_s": steps / wall if wall > 0 else None,
+                "gpu_launches": sum(r.launches for r in self.results),
                 "step_ms_p50": pct(lat, 50), "step_ms_p99": pct(lat, 99),
                 "queue_wait_s_p50": pct(waits, 50), "queue_wait_s_p99": pct(waits, 99)}

@@ -58,8 +58,9 @@ class Scan:
 
 
 def make_geom(shape, spacing, n_elem, n_frames, n_samples, *, fs=FS_MHZ,
-              c=C_MM_PER_US, a0=None, t0=0.0) -> dict:
-    """Acquisition scalars for a grid of ``shape = (nz, ny, nx)`` centred at 0."""
+              c=C_MM_PER_US, a0=None, t0=0.0, kernel="sphere", sigma=None) -> dict:
+    """Acquisition scalars for a grid of ``shape = (nz, ny, nx)`` centred at 0.
+    ``kernel`` names the voxel pulse: "sphere" (radius a0) or "gauss" (width sigma, mm)."""
     nz, ny, nx = (int(s) for s in shape)
     if np.isscalar(spacing):
         dz = dy = dx = float(spacing)
@@ -67,12 +68,15 @@ def make_geom(shape, spacing, n_elem, n_frames, n_samples, *, fs=FS_MHZ,
         dz, dy, dx = (float(s) for s in spacing)
     if a0 is None:
         a0 = 0.5 * min(dx, dy, dz)
+    if kernel not in ("sphere", "gauss") or (kernel == "gauss" and not (sigma and sigma > 0)):
+        raise ValueError("kernel must be 'sphere', or 'gauss' with sigma > 0")
     return dict(nx=nx, ny=ny, nz=nz, dx=dx, dy=dy, dz=dz,
                 ox=-0.5 * (nx - 1) * dx, oy=-0.5 * (ny - 1) * dy,
                 oz=-0.5 * (nz - 1) * dz,
                 n_elem=int(n_elem), n_frames=int(n_frames),
                 n_samples=int(n_samples), fs_mhz=float(fs), t0_us=float(t0),
-                c_mm_per_us=float(c), a0_mm=float(a0))
+                c_mm_per_us=float(c), a0_mm=float(a0),
+                kernel=kernel, sigma_mm=float(sigma) if kernel == "gauss" else 0.0)
 
 
 def voxel_axes(geom):

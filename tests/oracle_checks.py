@@ -18,6 +18,17 @@ fail at least one of them.  Pins used:
   components and in the element positions;
 * convergence of a voxelised ball to pi/6 times the ball's own closed-form pulse
   (each voxel sphere fills pi/6 of its cell).
+
+For the Gaussian kernel (Eq. 1, Appendix A Eq. gaussian_far_field):
+
+* the exact solution of the 3-D wave equation for a Gaussian initial pressure,
+  from Poisson's spherical-means formula p = d/dt [t M(ct)] evaluated by
+  numerical quadrature (no closed form involved), against the point-sampled
+  pulse;
+* quadrature of the truncated far-field pulse over each sample interval against
+  the interval averages;
+* central finite differences of the pulse in the distance;
+* the adjoint identity, rigid invariance and loss finite differences as above.
 """
 from __future__ import annotations
 
@@ -46,9 +57,88 @@ def _golden_module():
     return mod
 
 
-def _scalar_geom(c, fs, a0, t0, n_samples=100000):
-    return synth.make_geom((1, 1, 1), 1.0, 1, 1, n_samples, fs=float(fs), c=float(c),
-                           a0=float(a0), t0=float(t0))
+def _scalar_geom(c, fs, a0, t0, n_samples=100000, sigma=None):
+    g = synth.make_geom((1, 1, 1), 1.0, 1, 1, n_samples, fs=float(fs), c=float(c),
+                        a0=float(a0), t0=float(t0))
+    if sigma is not None:
+        g.update(kernel="gauss", sigma_mm=float(sigma))
+    return g
+
+
+GAUSS_TRUNC = 4.0  # support half-width in units of sigma (reading: the paper states none)
+
+
+def _gauss_far_field(r, tau, sigma):
+    """Outgoing Gaussian pulse at distance r and tau = c t, truncated at 4 sigma."""
+    w = r - tau
+    return w / (2 * r) * math.exp(-w * w / (2 * sigma * sigma)) if abs(w) <= GAUSS_TRUNC * sigma else 0.0
+
+
+def _poisson_gauss(r, t, c, sigma):
+    """Pressure at distance r, time t for p(x, 0) = exp(-|x|^2 / (2 sigma^2)),
+    p_t(x, 0) = 0, from Poisson's formula p = d/dt [t M(ct)], with M(R) the mean of
+    the initial field over the sphere of radius R about the observation point.
+    M and dM/dR are integrated numerically over u = cos(polar angle)."""
+    R = c * t
+    f = lambda u: math.exp(-(r * r + R * R - 2 * r * R * u) / (2 * sigma * sigma))
+    dfdR = lambda u: -(R - r * u) / (sigma * sigma) * f(u)
+    # the integrand is concentrated near u = 1 when R ~ r; give quad the scale
+    pts = [max(-1.0, 1.0 - (8 * sigma) ** 2 / max(2 * r * R, 1e-300))]
+    M = 0.5 * scipy.integrate.quad(f, -1, 1, points=pts, epsabs=1e-15, epsrel=1e-12, limit=400)[0]
+    dM = 0.5 * scipy.integrate.quad(dfdR, -1, 1, points=pts, epsabs=1e-15, epsrel=1e-12, limit=400)[0]
+    return M + t * c * dM
+
+
+def check_wave_equation_gauss(seed=12):
+    """Returns (max |oracle - Poisson| / peak inside the 4-sigma support,
+    max |Poisson| / peak outside it).  The point-sampled Gaussian pulse is the
+    far-field form, which differs from the exact solution only by the inward
+    wave (exp(-(r + ct)^2 / 2 sigma^2), nil at r >= 3 mm) and the truncation."""
+    rng = np.random.default_rng(seed)
+    c, fs = 1.5, 40.0
+    inside, outside = 0.0, 0.0
+    for _ in range(6):
+        sigma = float(rng.choice([0.03, 0.05, 0.08]))
+        r = float(rng.uniform(3.0, 12.0))
+        t0 = float(rng.uniform(0.0, 0.3))
+        geom = _scalar_geom(c, fs, 0.05, t0, sigma=sigma)
+        peak = sigma / (2 * r) * math.exp(-0.5)
+        h = c / fs
+        n0 = int(math.floor((r - 6 * sigma - c * t0) / h))
+        n1 = int(math.ceil((r + 6 * sigma - c * t0) / h))
+        for n in range(n0, n1 + 1):
+            t = t0 + n / fs
+            exact = _poisson_gauss(r, t, c, sigma)
+            got = oracle.pulse(geom, r, n, point_sampling=True)
+            w = abs(c * t - r)
+            if w < GAUSS_TRUNC * sigma:
+                inside = max(inside, abs(got - exact) / peak)
+            else:
+                outside = max(outside, abs(exact) / peak)
+                if w > GAUSS_TRUNC * sigma:  # truncated: the oracle must give exactly zero
+                    inside = max(inside, abs(got) / peak)
+    return inside, outside
+
+
+def check_quadrature_gauss(seed=13) -> float:
+    """Interval averages against quadrature of the truncated far-field pulse."""
+    rng = np.random.default_rng(seed)
+    worst = 0.0
+    c, fs = 1.5, 40.0
+    h = c / fs
+    for _ in range(10):
+        sigma = float(rng.choice([0.02, 0.04, 0.08, 0.15]))
+        t0, r = float(rng.uniform(0, 0.5)), float(rng.uniform(3.0, 20.0))
+        geom = _scalar_geom(c, fs, 0.05, t0, sigma=sigma)
+        rho = GAUSS_TRUNC * sigma
+        peak = sigma / (2 * r) * math.exp(-0.5)
+        for n in range(int(math.floor((r - rho - c * t0) / h)) - 2, int(math.ceil((r + rho - c * t0) / h)) + 3):
+            ta, tb = c * (t0 + (n - 0.5) / fs), c * (t0 + (n + 0.5) / fs)
+            pts = [x for x in (r - rho, r, r + rho) if ta < x < tb]
+            val = scipy.integrate.quad(lambda tau: _gauss_far_field(r, tau, sigma), ta, tb, points=pts or None,
+                                       epsabs=1e-15, epsrel=1e-12, limit=200)[0] / h
+            worst = max(worst, abs(oracle.pulse(geom, r, n) - val) / peak)
+    return worst
 
 
 def check_closed_form() -> float:
@@ -95,17 +185,19 @@ def check_quadrature(seed=5) -> float:
     return worst
 
 
-def check_pulse_dd(seed=6) -> float:
+def check_pulse_dd(seed=6, gauss=False) -> float:
     """Max relative gap between pulse_dd and a central difference of pulse."""
     rng = np.random.default_rng(seed)
     worst = 0.0
     eps = 1e-7
     for _ in range(20):
         a0 = float(rng.choice([0.05, 0.1]))
-        geom = _scalar_geom(1.5, 40.0, a0, 0.0)
+        sigma = float(rng.choice([0.02, 0.05])) if gauss else None
+        geom = _scalar_geom(1.5, 40.0, a0, 0.0, sigma=sigma)
+        rho = GAUSS_TRUNC * sigma if gauss else a0
         r = float(rng.uniform(3.0, 15.0))
         h = 1.5 / 40.0
-        ns = range(int((r - a0) / h) - 1, int((r + a0) / h) + 2)
+        ns = range(int((r - rho) / h) - 1, int((r + rho) / h) + 2)
         scale = max(abs(oracle.pulse_dd(geom, r, n)) for n in ns) + 1e-300
         for n in ns:
             fd = (oracle.pulse(geom, r + eps, n) - oracle.pulse(geom, r - eps, n)) / (2 * eps)
@@ -124,9 +216,12 @@ def check_point_sampling() -> float:
     return worst / (0.1 / 10.0)
 
 
-def small_geom(shape=(5, 6, 7), spacing=0.25, m=2, n_frames=2, n_samples=256, a0=None, seed=0):
-    """Small volume with an m x m array 3 mm above it and slightly tilted frames."""
+def small_geom(shape=(5, 6, 7), spacing=0.25, m=2, n_frames=2, n_samples=256, a0=None, seed=0, sigma=None):
+    """Small volume with an m x m array 3 mm above it and slightly tilted frames
+    (Gaussian kernel of width ``sigma`` if given)."""
     geom = synth.make_geom(shape, spacing, m * m, n_frames, n_samples, a0=a0)
+    if sigma is not None:
+        geom.update(kernel="gauss", sigma_mm=float(sigma))
     rng = np.random.default_rng(seed)
     elem = synth.planar_array(m, m, 0.7)
     poses = np.zeros((n_frames, 3, 4))
@@ -167,8 +262,8 @@ def check_superposition() -> float:
     return worst / scale
 
 
-def check_adjoint_identity(seed=7) -> float:
-    geom, elem, poses = small_geom(shape=(6, 7, 8), spacing=0.2, m=3, n_frames=2, n_samples=320)
+def check_adjoint_identity(seed=7, sigma=None) -> float:
+    geom, elem, poses = small_geom(shape=(6, 7, 8), spacing=0.2, m=3, n_frames=2, n_samples=320, sigma=sigma)
     rng = np.random.default_rng(seed)
     xw = oracle.element_positions(geom, elem, poses)
     x = rng.uniform(0, 1, size=(6, 7, 8)).astype(np.float32)
@@ -181,8 +276,8 @@ def check_adjoint_identity(seed=7) -> float:
     return abs(lhs - rhs) / max(abs(lhs), abs(rhs))
 
 
-def check_rigid_invariance(seed=8) -> float:
-    geom, elem, poses = small_geom(shape=(6, 6, 5), spacing=0.2, m=3, n_frames=2, n_samples=320)
+def check_rigid_invariance(seed=8, sigma=None) -> float:
+    geom, elem, poses = small_geom(shape=(6, 6, 5), spacing=0.2, m=3, n_frames=2, n_samples=320, sigma=sigma)
     rng = np.random.default_rng(seed)
     p0 = rng.uniform(0, 1, size=(5, 6, 6)).astype(np.float32)
     G = synth.axis_angle_matrix(synth.random_unit(rng), math.radians(rng.uniform(5, 30)))
@@ -214,9 +309,9 @@ def _loss_at(geom, p0, elem, poses, meas, mask=None):
     return 0.5 * math.fsum((r * r).ravel())
 
 
-def check_pose_fd(seed=9, eps=1e-6, use_mask=False):
+def check_pose_fd(seed=9, eps=1e-6, use_mask=False, sigma=None):
     """Returns (max rel err rotation block, translation block, element gradient)."""
-    geom, elem, poses = small_geom(shape=(4, 5, 5), spacing=0.25, m=2, n_frames=2, n_samples=256)
+    geom, elem, poses = small_geom(shape=(4, 5, 5), spacing=0.25, m=2, n_frames=2, n_samples=256, sigma=sigma)
     rng = np.random.default_rng(seed)
     p0 = rng.uniform(0.2, 1, size=(4, 5, 5)).astype(np.float32)
     meas = 0.02 * rng.standard_normal((2, 4, 256))

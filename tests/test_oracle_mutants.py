@@ -15,16 +15,16 @@ from tests import oracle_checks as oc
 SRC = os.path.join(os.path.dirname(oracle.__file__), "pasfm_oracle.c")
 
 MUTANTS = {
-    "pulse_sign_flipped": ("return (wl * wl - wh * wh) / (4.0 * d * h);",
-                           "return (wh * wh - wl * wl) / (4.0 * d * h);"),
-    "pulse_amplitude_drops_1_over_d": ("return (wl * wl - wh * wh) / (4.0 * d * h);",
-                                       "return (wl * wl - wh * wh) / (4.0 * 10.0 * h);"),
+    "pulse_sign_flipped": ("return (prim(g, wh) - prim(g, wl)) / (2.0 * d * h);",
+                           "return (prim(g, wl) - prim(g, wh)) / (2.0 * d * h);"),
+    "pulse_amplitude_drops_1_over_d": ("return (prim(g, wh) - prim(g, wl)) / (2.0 * d * h);",
+                                       "return (prim(g, wh) - prim(g, wl)) / (2.0 * 10.0 * h);"),
     "sample_time_off_by_half": ("const double tau = g->c * (g->t0 + (double)n / g->fs);\n  if",
                                 "const double tau = g->c * (g->t0 + ((double)n + 0.5) / g->fs);\n  if"),
-    "derivative_drops_W_over_d": ("return (dl - dh) / (4.0 * d * h) - W / d;",
-                                  "return (dl - dh) / (4.0 * d * h);"),
-    "derivative_sign_flipped": ("return (dl - dh) / (4.0 * d * h) - W / d;",
-                                "return (dh - dl) / (4.0 * d * h) - W / d;"),
+    "derivative_drops_W_over_d": ("return (dh - dl) / (2.0 * d * h) - W / d;",
+                                  "return (dh - dl) / (2.0 * d * h);"),
+    "derivative_sign_flipped": ("return (dh - dl) / (2.0 * d * h) - W / d;",
+                                "return (dl - dh) / (2.0 * d * h) - W / d;"),
     "rotation_transposed": ("x[a] = P[4 * a] * e[0] + P[4 * a + 1] * e[1] + P[4 * a + 2] * e[2] + P[4 * a + 3];",
                             "x[a] = P[a] * e[0] + P[4 + a] * e[1] + P[8 + a] * e[2] + P[4 * a + 3];"),
     "voxel_axes_swapped": ("g->ox + g->dx * ix, g->oy + g->dy * iy, g->oz + g->dz * iz",
@@ -33,9 +33,21 @@ MUTANTS = {
                            "w[0] += x[2] * Gj[1] - x[1] * Gj[2];"),
     "adjoint_reads_reversed_samples": ("for (int n = lo; n <= hi; ++n) acc += gs[n] * oracle_pulse(g, d, n);",
                                        "for (int n = lo; n <= hi; ++n) acc += gs[lo + hi - n] * oracle_pulse(g, d, n);"),
-    "sample_range_too_narrow": ("double a = floor((d - g->a0 - tau0) / h - 0.5) - 1.0;",
-                                "double a = floor((d - g->a0 - tau0) / h - 0.5) + 2.0;"),
+    "sample_range_too_narrow": ("double a = floor((d - rho - tau0) / h - 0.5) - 1.0;",
+                                "double a = floor((d - rho - tau0) / h - 0.5) + 2.0;"),
     "pose_grad_ignores_mask": ("if (!mask || mask[fj]) {", "if (1) {"),
+    # Gaussian kernel
+    "gauss_prefactor_sigma_not_squared": ("if (g->kernel == 1) return g->sigma * g->sigma * exp(",
+                                          "if (g->kernel == 1) return g->sigma * exp("),
+    "gauss_antiderivative_width_doubled": (
+        "return g->sigma * g->sigma * exp(-w * w / (2.0 * g->sigma * g->sigma));",
+        "return g->sigma * g->sigma * exp(-w * w / (4.0 * g->sigma * g->sigma));"),
+    "gauss_point_pulse_drops_amplitude_w": ("if (g->kernel == 1) return -w / (2.0 * d) * exp(",
+                                            "if (g->kernel == 1) return -1.0 / (2.0 * d) * exp("),
+    "gauss_derivative_drops_E": ("if (g->kernel == 1) return -w * exp(-w * w / (2.0 * g->sigma * g->sigma));",
+                                 "if (g->kernel == 1) return -w;"),
+    "gauss_support_two_sigma": ("return g->kernel == 1 ? 4.0 * g->sigma : g->a0;",
+                                "return g->kernel == 1 ? 2.0 * g->sigma : g->a0;"),
 }
 
 
@@ -55,6 +67,15 @@ def failing_pins():
         out.append("pose_fd")
     if max(oc.check_pose_fd(use_mask=True, seed=11)) > 1e-6:
         out.append("pose_fd_masked")
+    inside, outside = oc.check_wave_equation_gauss()
+    if inside > 1e-8:
+        out.append("gauss_wave_equation")
+    if oc.check_quadrature_gauss() > 1e-9:
+        out.append("gauss_quadrature")
+    if oc.check_pulse_dd(gauss=True) > 1e-6:
+        out.append("gauss_pulse_dd")
+    if max(oc.check_pose_fd(sigma=0.06)) > 1e-6:
+        out.append("gauss_pose_fd")
     return out
 
 

@@ -2,6 +2,7 @@
 import math
 
 import numpy as np
+import pytest
 import scipy.linalg
 
 from oracle import adam, rigid
@@ -44,6 +45,33 @@ def test_pose_gradient_fd():
 def test_pose_gradient_fd_masked():
     rot, trans, elem = oc.check_pose_fd(use_mask=True, seed=11)
     assert rot < 1e-6 and trans < 1e-6 and elem < 1e-6, (rot, trans, elem)
+
+
+# ---- Gaussian kernel (Eq. 1, Appendix A Eq. gaussian_far_field)
+
+def test_gauss_pulse_solves_the_wave_equation():
+    inside, outside = oc.check_wave_equation_gauss()
+    assert inside < 1e-8          # far-field form = exact solution at r >= 3 mm, sigma <= 0.08 mm
+    assert outside < 2.3e-3       # what the 4-sigma truncation drops: 4 exp(-7.5) of the peak
+
+
+def test_gauss_pulse_quadrature():
+    assert oc.check_quadrature_gauss() < 1e-9
+
+
+def test_gauss_pulse_derivative_fd():
+    assert oc.check_pulse_dd(gauss=True) < 1e-6
+
+
+def test_gauss_adjoint_identity_and_rigid_invariance():
+    assert oc.check_adjoint_identity(sigma=0.06) < 1e-12
+    assert oc.check_rigid_invariance(sigma=0.06) < 1e-12
+
+
+@pytest.mark.parametrize("use_mask", [False, True])
+def test_gauss_pose_gradient_fd(use_mask):
+    rot, trans, elem = oc.check_pose_fd(sigma=0.06, use_mask=use_mask, seed=11 if use_mask else 9)
+    assert rot < 1e-6 and trans < 1e-6 and elem < 1e-6
 
 
 def test_big_ball_converges_to_pi_over_6():
