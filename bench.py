@@ -48,6 +48,20 @@ def flops_pose(m):
     return 26 + 13 * m
 
 
+# Gaussian kernel (Eq. 1): m = 8 sigma / h + 1 in-support samples per pair; three
+# exp2 per pair and the two-multiply ratio recurrence per sample boundary.
+def flops_fwd_gauss(m):
+    return 28 + 5 * m
+
+
+def flops_adj_gauss(m):
+    return 30 + 5 * m
+
+
+def flops_pose_gauss(m):
+    return 37 + 10 * m
+
+
 def peaks():
     p = {}
     try:
@@ -154,13 +168,15 @@ class ClockSampler:
 WORKLOAD_MIXED = "mixed_precision_256x256x128_0.1mm_vessel150_32x32_0.3mm_400f_3072s"
 
 
-def make_workload(seed_offset=0, n_frames=64, workload="full_scan"):
+def make_workload(seed_offset=0, n_frames=64, workload="full_scan", sigma=None):
     from paper_2604_09643_b300 import synth
 
     if workload == "mixed_precision":
         scan = synth.mixed_precision_scan(n_frames=n_frames, seed_offset=seed_offset)
     else:
         scan = synth.full_scan(seed_offset=seed_offset, n_frames=n_frames)
+    if sigma:
+        scan.geom.update(kernel="gauss", sigma_mm=float(sigma))
     rng = np.random.default_rng(synth.SEED_NOISE + 20 + seed_offset)
     # dense starting iterate: damped truth plus a uniform background
     p_init = (0.5 * scan.p0 + rng.uniform(0.02, 0.08, size=scan.p0.shape)).astype(np.float32)
@@ -170,7 +186,8 @@ def make_workload(seed_offset=0, n_frames=64, workload="full_scan"):
 
 def pairs_and_m(geom):
     h = geom["c_mm_per_us"] / geom["fs_mhz"]
-    m = 2 * geom["a0_mm"] / h + 1
+    sup = 4 * geom["sigma_mm"] if geom.get("kernel") == "gauss" else geom["a0_mm"]
+    m = 2 * sup / h + 1
     pairs = geom["nx"] * geom["ny"] * geom["nz"] * geom["n_elem"] * geom["n_frames"]
     return pairs, m
 
@@ -252,7 +269,8 @@ def run_native(args):
     dev = torch.device("cuda", local)
 
     frames = args.frames if args.frames else (400 if args.workload == "mixed_precision" else 64)
-    scan, p_init, poses_init = make_workload(seed_offset=rank, n_frames=frames, workload=args.workload)
+    scan, p_init, poses_init = make_workload(seed_offset=rank, n_frames=frames, workload=args.workload,
+                                             sigma=args.sigma if args.kernel == "gauss" else None)
     store = {"f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16}[args.storage]
     geom = scan.geom
     pairs, m = pairs_and_m(geom)
@@ -341,25 +359,30 @@ def run_native(args):
     # ---- roofline of the dominant kernel (algorithmic flops / live CUDA-event duration)
     pk = peaks()
     dom = max(per_kernel, key=lambda k: per_kernel[k]["ms_total"])
-    fpp = {"bwd_cube": flops_adj(m) + flops_pose(m), "fwd_cube": flops_fwd(m)}.get(dom)
+    gauss = args.kernel == "gauss"
+    f_fwd, f_adj, f_pose = ((flops_fwd_gauss, flops_adj_gauss, flops_pose_gauss) if gauss
+                            else (flops_fwd, flops_adj, flops_pose))
+    fpp = {"bwd_cube": f_adj(m) + f_pose(m), "fwd_cube": f_fwd(m)}.get(dom)
     roofline = None
     if fpp:
         launches_per_step = per_kernel[dom]["launches"] / args.steps
         flops_per_launch = pairs * fpp / launches_per_step
         achieved = flops_per_launch / (per_kernel[dom]["ms_avg"] * 1e-3) / 1e12
         roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": pk["fp32_tflops"],
-                    "unit": "TFLOP/s", "frac": achieved / pk["fp32_tflops"], "traffic": traffic_for(dom),
+                    "unit": "TFLOP/s", "frac": achieved / pk["fp32_tflops"], "traffic": traffic_for(dom + ("_gauss" if gauss else "")),
                     "peak_source": f"FP32 148 SM x 128 lanes x 2 flops x {pk['sm_max_mhz']:.0f} MHz "
                                    f"({pk['source']} clock)",
                     "flops_per_pair": fpp, "pairs_per_launch": pairs / launches_per_step}
-    step_flops = pairs * (flops_fwd(m) + flops_adj(m) + flops_pose(m))
+    step_flops = pairs * (f_fwd(m) + f_adj(m) + f_pose(m))
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if args.storage == "f32" else f"f32 (volume and measurements stored {args.storage})",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD if args.workload == "full_scan" else WORKLOAD_MIXED,
+        "config": {"workload": (WORKLOAD if args.workload == "full_scan" else WORKLOAD_MIXED)
+                   + (f"_gauss_sigma{args.sigma:g}mm" if gauss else ""),
+                   "kernel": "gauss" if gauss else "sphere",
                    "voxels": [geom["nz"], geom["ny"], geom["nx"]],
                    "elements": geom["n_elem"], "frames": geom["n_frames"], "samples": geom["n_samples"],
                    "global_batch": world, "parallelism": f"replicas{world}",
@@ -377,7 +400,7 @@ def run_native(args):
     }
     if args.frames:
         out["config"]["workload"] += f" (profiling case: {args.frames} frames, not a bench line)"
-    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "full_scan":
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "full_scan" and not gauss:
         out["cpu_baseline"] = cpu_baseline(scan, p_init, poses_init)
     if rank == 0:
         print(json.dumps(out))
@@ -449,6 +472,9 @@ def main():
     ap.add_argument("--workload", choices=["full_scan", "mixed_precision", "serving"], default="full_scan",
                     help="full_scan: the benchmark; mixed_precision: 256x256x128, 32x32 elements, 400 frames; "
                          "serving: continuous batching over the seeded request stream")
+    ap.add_argument("--kernel", choices=["sphere", "gauss"], default="sphere",
+                    help="voxel pulse: uniform sphere (a0 = spacing / 2) or the Gaussian of Eq. 1")
+    ap.add_argument("--sigma", type=float, default=0.05, help="Gaussian width (mm) for --kernel gauss")
     ap.add_argument("--serve-requests", type=int, default=12, help="serving: requests taken from the stream")
     ap.add_argument("--serve-steps", type=int, default=4, help="serving: gradient steps per request")
     ap.add_argument("--storage", choices=["f32", "bf16", "f16"], default="f32",

@@ -12,6 +12,13 @@
  * t_n = t0 + n / fs, so with h = c / fs, tau_n = c t_n and
  *     W(d, n) = (w_lo^2 - w_hi^2) / (4 d h),
  *     w_lo = clamp(tau_n - h/2 - d, -a0, a0),  w_hi = clamp(tau_n + h/2 - d, -a0, a0):
+ * With kernel = PASFM_KERNEL_GAUSS the voxel instead radiates the outgoing
+ * Gaussian pulse of Eq. 1 (Appendix A, far-field Gaussian source, kernel K_G):
+ * p0_i (d - c t) / (2 d) exp(-(c t - d)^2 / (2 sigma^2)), cut to |c t - d| <= 4 sigma,
+ * and its sample-interval average is, with E(w) = exp(-w^2 / (2 sigma^2)) and the
+ * same clamped ends (support 4 sigma instead of a0),
+ *     W(d, n) = sigma^2 (E(w_hi) - E(w_lo)) / (2 d h).
+ * Everything below holds for either kernel.
  *   forward    s[f][j][n] = sum_i p0_i W(d_fji, n)
  *   adjoint    v_i        = sum_{f,j,n} g[f][j][n] W(d_fji, n)            (exact transpose)
  *   pose grad  G_fj = sum_i p0_i sum_n g[f][j][n] dW/dd (x_fj - r_i) / d,
@@ -31,7 +38,7 @@
  *  - Return value: PASFM_OK or a negative code; pasfm_last_error() gives a
  *    message for the calling thread.  Argument errors are detected on the host
  *    before any launch.  Geometry errors that depend on device data (an element
- *    within a0 of the voxel grid, a device wait that ran out) set the context's
+ *    within the pulse support of the voxel grid, a device wait that ran out) set the context's
  *    device status word; read it with pasfm_status().  Outputs of a call that
  *    set the status word are unspecified but every access stays in bounds.
  *  - A context owns its workspace and may be used by one host thread and one
@@ -63,8 +70,12 @@ extern "C" {
 #define PASFM_BF16 1
 #define PASFM_F16 2
 
+/* voxel pulse (pasfm_geom.kernel) */
+#define PASFM_KERNEL_SPHERE 0 /* uniform sphere of radius a0 (Appendix A closed form)          */
+#define PASFM_KERNEL_GAUSS 1  /* Gaussian of width sigma_mm (Eq. 1, kernel K_G), support 4 sigma */
+
 /* device status word bits (pasfm_status) */
-#define PASFM_STATUS_ELEMENT_INSIDE 1u /* an element lies within a0 of the voxel grid */
+#define PASFM_STATUS_ELEMENT_INSIDE 1u /* an element lies within the pulse support of the voxel grid */
 #define PASFM_STATUS_TIMEOUT 2u        /* a bounded shared-memory barrier wait expired */
 #define PASFM_STATUS_INDEX_CLAMPED 4u  /* a sample index fell outside its window (clamped) */
 
@@ -82,6 +93,12 @@ typedef struct pasfm_geom {
   double a0_mm;                        /* voxel sphere radius (mm); <= 0 means min(d)/2 */
   int32_t dtype_vol;                   /* PASFM_F32 | PASFM_BF16 | PASFM_F16 (p0)       */
   int32_t dtype_sig;                   /* PASFM_F32 | PASFM_BF16 | PASFM_F16 (meas, g)  */
+  int32_t kernel;                      /* PASFM_KERNEL_SPHERE (0) | PASFM_KERNEL_GAUSS  */
+  int32_t reserved;                    /* must be 0                                     */
+  double sigma_mm;                     /* Gaussian width (mm), > 0 for PASFM_KERNEL_GAUSS;
+                                          a pair then spans floor(8 sigma / h) + 2 <= 32
+                                          samples (sigma <= 0.14 mm at h = 0.0375 mm);
+                                          the sphere allows floor(2 a0 / h) + 2 <= 16   */
 } pasfm_geom;
 
 typedef struct pasfm_ctx pasfm_ctx;
@@ -185,15 +202,18 @@ int pasfm_twist_grad(pasfm_ctx* ctx, int n_frames, const double* xi, const doubl
 int pasfm_resample(pasfm_ctx* ctx, const pasfm_geom* src_geom, const float* src, const pasfm_geom* dst_geom,
                    float* dst, void* stream);
 
-/* A8 support -- Gaussian low-pass of every trace along time: the coarse levels
- * of the coarse-to-fine optimiser fit their wider pulses to band-limited data
- * (the data-side counterpart of the paper's decaying kernel width, Stage 2).
- * dst[r][n] = sum_k w_k src[r][n + k], |k| <= int(4 sigma + 0.5), w_k ~
- * exp(-k^2 / (2 sigma^2)) normalised to sum 1, zero outside the record
- * (sigma in samples; sigma <= 0 copies).  src, dst: float [n_rows][n_samples]
- * device memory; dst may alias src.  Synchronises `stream` before returning. */
-int pasfm_lowpass(pasfm_ctx* ctx, int64_t n_rows, int n_samples, double sigma, const float* src, float* dst,
-                  void* stream);
+/* A8 support -- Gaussian low-pass of every trace along time, optionally
+ * decimated: the coarse levels of the coarse-to-fine optimiser fit their wider
+ * pulses to band-limited data (the data-side counterpart of the paper's
+ * decaying kernel width, Stage 2), on a time grid `decim` times coarser.
+ * dst[r][m] = sum_k w_k src[r][m decim + k], |k| <= int(4 sigma + 0.5), w_k ~
+ * exp(-k^2 / (2 sigma^2)) normalised to sum 1, zero outside the record (sigma
+ * in input samples; sigma <= 0 takes the samples as they are).
+ * src: float [n_rows][n_samples], dst: float [n_rows][ceil(n_samples / decim)],
+ * device memory; dst may alias src only when decim == 1.  decim >= 1.
+ * Synchronises `stream` before returning. */
+int pasfm_lowpass(pasfm_ctx* ctx, int64_t n_rows, int n_samples, double sigma, int decim, const float* src,
+                  float* dst, void* stream);
 
 /* NC loss of Eq. 3 as a score for candidate poses (the coarse search of Stage
  * 2): for each of n_cand candidate trace sets sim[k] ([n_elem][n_samples] float)

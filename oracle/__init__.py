@@ -5,8 +5,8 @@ Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 or calls it, and it imports nothing from the product package.
 
 ``pasfm_oracle.c`` holds the operator (forward, adjoint, pose gradient, loss
-head) written pair by pair in FP64 from the paper's Appendix A closed form and
-Eq. 1; ``rigid.py`` holds the host-side rigid-body pieces (SO(3) exponential,
+head) written pair by pair in FP64 from the paper's Appendix A closed forms
+(uniform sphere; outgoing Gaussian of Eq. 1 with kernel K_G) and Eq. 1; ``rigid.py`` holds the host-side rigid-body pieces (SO(3) exponential,
 Kabsch fit, RANSAC consensus with the pairwise-edge pre-check of Stage 3) and
 ``adam.py`` the textbook Adam step.  Parity status of every function is listed
 in each module's header; all are pinned by ``tests/test_oracle_*.py``.

@@ -39,7 +39,11 @@ class PasfmGeom(ctypes.Structure):
                 ("ox", ctypes.c_double), ("oy", ctypes.c_double), ("oz", ctypes.c_double),
                 ("fs_mhz", ctypes.c_double), ("t0_us", ctypes.c_double),
                 ("c_mm_per_us", ctypes.c_double), ("a0_mm", ctypes.c_double),
-                ("dtype_vol", ctypes.c_int32), ("dtype_sig", ctypes.c_int32)]
+                ("dtype_vol", ctypes.c_int32), ("dtype_sig", ctypes.c_int32),
+                ("kernel", ctypes.c_int32), ("reserved", ctypes.c_int32), ("sigma_mm", ctypes.c_double)]
+
+
+KERNEL_CODE = {"sphere": 0, "gauss": 1}   # PASFM_KERNEL_SPHERE, PASFM_KERNEL_GAUSS
 
 
 class PasfmAdam(ctypes.Structure):
@@ -69,7 +73,7 @@ _SIGS = {
     "pasfm_apply_twists": ([_VP, _I, _VP, _VP, _VP, _VP], _I),
     "pasfm_twist_grad": ([_VP, _I, _VP, _VP, _VP, _VP], _I),
     "pasfm_resample": ([_VP, _G, _VP, _G, _VP, _VP], _I),
-    "pasfm_lowpass": ([_VP, ctypes.c_int64, _I, ctypes.c_double, _VP, _VP, _VP], _I),
+    "pasfm_lowpass": ([_VP, ctypes.c_int64, _I, ctypes.c_double, _I, _VP, _VP, _VP], _I),
     "pasfm_nc_scores": ([_VP, _I, _I, _I, _VP, _VP, _I, _VP, _VP, _VP], _I),
     "pasfm_pose_grad_noalloc": ([_G, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP], _I),
     "pasfm_status": ([_VP, _VP, ctypes.POINTER(ctypes.c_uint32)], _I),
@@ -117,6 +121,8 @@ def make_geom(geom: dict, dtype_vol=torch.float32, dtype_sig=torch.float32) -> P
         setattr(g, k, float(geom[k]))
     g.dtype_vol = _DTYPE_CODE[dtype_vol]
     g.dtype_sig = _DTYPE_CODE[dtype_sig]
+    g.kernel = KERNEL_CODE[geom.get("kernel", "sphere")]
+    g.sigma_mm = float(geom.get("sigma_mm", 0.0))
     return g
 
 
@@ -308,11 +314,14 @@ class Context:
                                     ctypes.byref(gd), _ptr(out, torch.float32, "out"), _stream(stream, self.device)))
         return out
 
-    def lowpass(self, sig, sigma, out=None, stream=None):
-        """Gaussian low-pass (sigma in samples) of every trace of sig [..., Nt]."""
-        out = torch.empty_like(sig) if out is None else out
-        rows = sig.numel() // sig.shape[-1] if sig.numel() else 0
-        _check(lib().pasfm_lowpass(self.handle, int(rows), int(sig.shape[-1]), float(sigma),
+    def lowpass(self, sig, sigma, out=None, stream=None, decim=1):
+        """Gaussian low-pass (sigma in input samples) of every trace of sig [..., Nt],
+        keeping every `decim`-th sample: out [..., ceil(Nt / decim)]."""
+        T = int(sig.shape[-1])
+        n_out = -(-T // int(decim))
+        out = torch.empty(*sig.shape[:-1], n_out, dtype=torch.float32, device=sig.device) if out is None else out
+        rows = sig.numel() // T if sig.numel() else 0
+        _check(lib().pasfm_lowpass(self.handle, int(rows), T, float(sigma), int(decim),
                                    _ptr(sig, torch.float32, "sig"), _ptr(out, torch.float32, "out"),
                                    _stream(stream, self.device)))
         return out

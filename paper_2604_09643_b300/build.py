@@ -1,7 +1,8 @@
 """Build ``lib/libpasfm.so`` (sm_103a) from ``csrc/`` with nvcc.
 
-The hot kernels are instantiated once per sample-slot count S (2..16) from
-``kernels_s.cu``; those translation units compile in parallel.  The library is
+The hot kernels are instantiated once per pulse profile and sample-slot count
+from ``kernels_s.cu`` (sphere: S = 2..16, Gaussian: S = 2..32); those
+translation units compile in parallel.  The library is
 built in-tree so that it travels with the source tree.
 
     python -m paper_2604_09643_b300.build [--force]
@@ -22,7 +23,8 @@ CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "lib", "libpasfm.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-S_VALUES = range(2, 17)
+# (pulse profile, slot count) pairs: the sphere (0) for S = 2..16, the Gaussian (1) for S = 2..32
+KS_VALUES = [(0, s) for s in range(2, 17)] + [(1, s) for s in range(2, 33)]
 
 
 def nvcc() -> str:
@@ -63,9 +65,10 @@ def build(force: bool = False, jobs: int | None = None, verbose: bool = False) -
         return LIB
     os.makedirs(OBJ, exist_ok=True)
     os.makedirs(os.path.dirname(LIB), exist_ok=True)
-    work = [(os.path.join(CSRC, "kernels_s.cu"), os.path.join(OBJ, f"kernels_s{s}.o"), [f"-DPASFM_S={s}"])
-            for s in S_VALUES]
+    work = [(os.path.join(CSRC, "kernels_s.cu"), os.path.join(OBJ, f"kernels_k{k}_s{s}.o"),
+             [f"-DPASFM_K={k}", f"-DPASFM_S={s}"]) for k, s in KS_VALUES]
     work += [(os.path.join(CSRC, "aux.cu"), os.path.join(OBJ, "aux.o"), []),
+             (os.path.join(CSRC, "launchers.cu"), os.path.join(OBJ, "launchers.o"), []),
              (os.path.join(CSRC, "pasfm.cu"), os.path.join(OBJ, "pasfm.o"), []),
              (os.path.join(CSRC, "noalloc.cu"), os.path.join(OBJ, "noalloc.o"), [])]
     jobs = jobs or max(1, min(len(work), os.cpu_count() or 1))

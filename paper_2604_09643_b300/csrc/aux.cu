@@ -408,17 +408,29 @@ namespace pasfm {
 // dst[n] = sum_k w_k src[n + k], |k| <= r, w_k ~ exp(-k^2 / (2 sigma^2)) summing
 // to 1, samples outside the record taken as zero.  One block per trace; the
 // trace is staged in shared memory, so dst may alias src.
-__global__ void __launch_bounds__(256) lowpass_kernel(const float* src, float* dst, int Nt, int r,
-                                                      const float* __restrict__ w) {
+__global__ void __launch_bounds__(256) sum_parts_kernel(const float* __restrict__ parts, int n_parts, int64_t nvox,
+                                                        float* __restrict__ vol, int accumulate) {
+  for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < nvox;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    float acc = parts[i];
+    for (int p = 1; p < n_parts; ++p) acc += parts[p * nvox + i];
+    vol[i] = accumulate ? vol[i] + acc : acc;
+  }
+}
+
+__global__ void __launch_bounds__(256) lowpass_kernel(const float* src, float* dst, int Nt, int r, int decim,
+                                                      int Nout, const float* __restrict__ w) {
   extern __shared__ float row[];
   const int64_t base = static_cast<int64_t>(blockIdx.x) * Nt;
   for (int n = threadIdx.x; n < Nt; n += blockDim.x) row[n] = src[base + n];
   __syncthreads();
-  for (int n = threadIdx.x; n < Nt; n += blockDim.x) {
+  const int64_t obase = static_cast<int64_t>(blockIdx.x) * Nout;
+  for (int m = threadIdx.x; m < Nout; m += blockDim.x) {
+    const int n = m * decim;
     float acc = 0.f;
     const int k0 = max(-r, -n), k1 = min(r, Nt - 1 - n);
     for (int k = k0; k <= k1; ++k) acc = fmaf(w[k + r], row[n + k], acc);
-    dst[base + n] = acc;
+    dst[obase + m] = acc;
   }
 }
 

@@ -9,7 +9,7 @@ namespace pasfm {
 constexpr int kRedChunk = 2048;  // samples per warp accumulator in fwd_reduce_kernel
 constexpr int kRedUnroll = 4;    // cubes loaded per step
 constexpr int kRedLanes = 8;     // ceil(W_max / 32), W_max = 256
-constexpr int kMinS = 2, kMaxS = 16;
+constexpr int kMinS = 2, kMaxSSphere = 16, kMaxSGauss = 32;
 
 __global__ void elem_pos_kernel(const double* elem, const double* pose, double* xw, int F, int E, double lox,
                                 double loy, double loz, double hix, double hiy, double hiz, double a0,
@@ -33,7 +33,7 @@ __global__ void resample_kernel(const float* src, int sx, int sy, int sz, double
                                 double sdx, double sdy, double sdz, float* dst, int nx, int ny, int nz, double ox,
                                 double oy, double oz, double dx, double dy, double dz);
 
-__global__ void lowpass_kernel(const float* src, float* dst, int Nt, int r, const float* w);
+__global__ void lowpass_kernel(const float* src, float* dst, int Nt, int r, int decim, int Nout, const float* w);
 
 __global__ void nc_scores_kernel(const float* sim, const void* meas, int dtype, const uint8_t* mask, int E, int Nt,
                                  double* out);
@@ -43,26 +43,15 @@ using FwdLaunch = cudaError_t (*)(int C, const CUtensorMap& map, const FwdParams
 using BwdLaunch = cudaError_t (*)(int C, int mode, const CUtensorMap& map, const BwdParams& P, dim3 grid,
                                   size_t smem, cudaStream_t st);
 
-#define PASFM_DECL_S(S)                                                                              \
-  cudaError_t fwd_launch_s##S(int C, const CUtensorMap& map, const FwdParams& P, dim3 grid, int threads, \
-                              size_t smem, cudaStream_t st);                                           \
-  cudaError_t bwd_launch_s##S(int C, int mode, const CUtensorMap& map, const BwdParams& P, dim3 grid,  \
-                              size_t smem, cudaStream_t st);
-PASFM_DECL_S(2)
-PASFM_DECL_S(3)
-PASFM_DECL_S(4)
-PASFM_DECL_S(5)
-PASFM_DECL_S(6)
-PASFM_DECL_S(7)
-PASFM_DECL_S(8)
-PASFM_DECL_S(9)
-PASFM_DECL_S(10)
-PASFM_DECL_S(11)
-PASFM_DECL_S(12)
-PASFM_DECL_S(13)
-PASFM_DECL_S(14)
-PASFM_DECL_S(15)
-PASFM_DECL_S(16)
-#undef PASFM_DECL_S
+// Launchers of the hot kernels for pulse profile K and slot count S; null when
+// (K, S) is not compiled (sphere: S = 2..16, Gaussian: S = 2..32).
+using BwdOccupancy = int (*)(int C, int mode, size_t smem);
+
+FwdLaunch fwd_launcher(int K, int S);
+BwdLaunch bwd_launcher(int K, int S);
+BwdOccupancy bwd_occupancy(int K, int S);
+
+// Adds the n_parts per-part adjoint sums in part order into vol (or overwrites it).
+__global__ void sum_parts_kernel(const float* parts, int n_parts, int64_t nvox, float* vol, int accumulate);
 
 }  // namespace pasfm

@@ -25,6 +25,12 @@
 // boundary S-1 needs a clamp.  Sample n_s + k then gets
 //     W = (b_k - b_{k+1}) / (4 d h),  b_k = clamp(beta_k)^2,  b_0 = b_S = a0^2,
 // which is the interval average of the uniform-sphere pulse (Appendix A).
+//
+// The Gaussian kernel (Eq. 1, K_G) has the same slot structure with a0 replaced
+// by the support half-width sup = 4 sigma: sample n_s + k gets
+//     W = sigma^2 (E_{k+1} - E_k) / (2 d h),  E_k = exp(-clamp(beta_k)^2 / (2 sigma^2)),
+// E_0 = E_S = exp(-8).  In the code a0 below stands for sup; template parameter K
+// selects the profile (PASFM_KERNEL_SPHERE or PASFM_KERNEL_GAUSS).
 #pragma once
 
 #include "pasfm_dev.cuh"
@@ -56,6 +62,43 @@ __device__ __forceinline__ PairMath pair_math(float A, float dc2, float dcf, flo
 }
 
 // ------------------------------------------------------------------------
+// Gaussian boundary values
+// ------------------------------------------------------------------------
+// Index of the boundary the recurrences start from: the one nearest the pulse
+// centre (beta_k = beta1 + (k - 1) h with beta1 in (-sup, -sup + h] and
+// sup ~ (S - 1) h / 2).
+template <int S>
+__host__ __device__ constexpr int gauss_centre() { return S / 2 < 1 ? 1 : S / 2; }
+
+// E[k] = exp(-beta_k^2 / (2 sigma^2)) for the boundaries k = 1..S-1 (E[0] is
+// not set).  Three exp2f per pair; the other values come from the ratio
+// recurrence of a Gaussian on an equispaced grid, E_{k+1} = E_k r_k with
+// r_{k+1} = r_k q (the device of "fast Gaussian gridding", Greengard & Lee,
+// SIAM Rev. 2004), run outward both ways from the centre boundary so that
+// rounding grows only toward the tails, where E is small.  Boundary S-1 can
+// lie past the support edge; E decreases for beta > 0, so the max with the
+// edge value is its clamp.
+template <int S>
+__device__ __forceinline__ void gauss_boundaries(float beta1, float h, const GaussConst& G, float (&E)[S]) {
+  constexpr int kc = gauss_centre<S>();
+  const float bc = fmaf(static_cast<float>(kc - 1), h, beta1);
+  E[kc] = exp2f(G.c1 * (bc * bc));
+  float up = exp2f(fmaf(bc, G.c2, G.c3));   // E_{kc+1} / E_kc
+  float dn = exp2f(fmaf(-bc, G.c2, G.c3));  // E_{kc-1} / E_kc
+#pragma unroll
+  for (int k = kc + 1; k < S; ++k) {
+    E[k] = E[k - 1] * up;
+    up *= G.q;
+  }
+#pragma unroll
+  for (int k = kc - 1; k >= 1; --k) {
+    E[k] = E[k + 1] * dn;
+    dn *= G.q;
+  }
+  E[S - 1] = fmaxf(E[S - 1], G.e_clamp);
+}
+
+// ------------------------------------------------------------------------
 // forward
 // ------------------------------------------------------------------------
 template <int C>
@@ -65,7 +108,7 @@ __host__ __device__ constexpr int fwd_win_offset() {
   return ((fwd_tile_bytes<C>() + C * C + 16 + 127) / 128) * 128;
 }
 
-template <int C, int S>
+template <int C, int S, int K>
 __global__ void __launch_bounds__(256, 2)
     fwd_cube_kernel(const __grid_constant__ CUtensorMap p0map, const FwdParams P) {
   extern __shared__ __align__(128) unsigned char smem[];
@@ -114,7 +157,7 @@ __global__ void __launch_bounds__(256, 2)
   const double* xp = P.xw + (static_cast<int64_t>(f) * P.E + jj) * 3;
   const double hc = 0.5 * (C - 1);
   const PairRef R = make_ref(xp[0], xp[1], xp[2], P.ox + P.dx * (cx * C + hc), P.oy + P.dy * (cy * C + hc),
-                             P.oz + P.dz * (cz * C + hc), P.a0, P.tau0, P.inv_h);
+                             P.oz + P.dz * (cz * C + hc), P.sup, P.tau0, P.inv_h);
   const int nb_rel = static_cast<int>(floorf(R.phim - P.nb_shift)) - 1;
   const float dxf = static_cast<float>(P.dx), dyf = static_cast<float>(P.dy), dzf = static_cast<float>(P.dz);
   float Pix[C];
@@ -161,20 +204,32 @@ __global__ void __launch_bounds__(256, 2)
           seen = max(seen, m.idx);
           float* slot = col + min(m.idx, max_idx) * kWarp;
           const float s = pv[u] * m.rs;
-          float beta = m.beta1;
-          float bprev = P.a0sq;
+          if constexpr (K == PASFM_KERNEL_GAUSS) {
+            float E[S];
+            gauss_boundaries<S>(m.beta1, P.h, P.gs, E);
+            float eprev = P.gs.e_clamp;
 #pragma unroll
-          for (int k = 0; k < S; ++k) {
-            float bk;
-            if (k == S - 1) {
-              bk = P.a0sq;
-            } else {
-              if (k > 0) beta += P.h;
-              const float bc = (k == S - 2) ? fminf(beta, P.a0f) : beta;
-              bk = bc * bc;
+            for (int k = 0; k < S; ++k) {
+              const float ek = (k == S - 1) ? P.gs.e_clamp : E[k + 1];
+              slot[k * kWarp] = fmaf(s, ek - eprev, slot[k * kWarp]);
+              eprev = ek;
             }
-            slot[k * kWarp] = fmaf(s, bprev - bk, slot[k * kWarp]);
-            bprev = bk;
+          } else {
+            float beta = m.beta1;
+            float bprev = P.sup2;
+#pragma unroll
+            for (int k = 0; k < S; ++k) {
+              float bk;
+              if (k == S - 1) {
+                bk = P.sup2;
+              } else {
+                if (k > 0) beta += P.h;
+                const float bc = (k == S - 2) ? fminf(beta, P.supf) : beta;
+                bk = bc * bc;
+              }
+              slot[k * kWarp] = fmaf(s, bprev - bk, slot[k * kWarp]);
+              bprev = bk;
+            }
           }
         }
       }
@@ -182,7 +237,7 @@ __global__ void __launch_bounds__(256, 2)
   }
   if (seen > max_idx) atomicOr(P.status, PASFM_STATUS_INDEX_CLAMPED);
 
-  // 6. flush the window as this cube's partial trace (scaled by 1 / (4 h))
+  // 6. flush the window as this cube's partial trace (scaled by 1 / (4 h), or sigma^2 / (2 h))
   __syncwarp();
   if (valid) {
     const int64_t row = static_cast<int64_t>(fl) * P.E + j;
@@ -230,7 +285,7 @@ __device__ __forceinline__ void bwd_thread_row(int tid, int& ty, int& tz) {
   }
 }
 
-template <int C, int S, bool ADJ, bool POSE>
+template <int C, int S, int K, bool ADJ, bool POSE>
 __global__ void __launch_bounds__(C* C, (C == 16 ? 2 : 8))
     bwd_cube_kernel(const __grid_constant__ CUtensorMap gmap, const BwdParams P) {
   using L = BwdLayout<C>;
@@ -278,7 +333,10 @@ __global__ void __launch_bounds__(C* C, (C == 16 ? 2 : 8))
   const double hc = 0.5 * (C - 1);
   const double rcx = P.ox + P.dx * (cx * C + hc), rcy = P.oy + P.dy * (cy * C + hc),
                rcz = P.oz + P.dz * (cz * C + hc);
-  const int nb = (P.n_items + kBatch - 1) / kBatch;
+  // this CTA's share of the (frame, element) items: [ib, ib + nl)
+  const int ib = blockIdx.y * P.part_items;
+  const int nl = max(0, min(P.n_items - ib, P.part_items));
+  const int nb = (nl + kBatch - 1) / kBatch;
 
   if (tid == 0) {
     mbar_init(&bar[0], 1);
@@ -289,16 +347,16 @@ __global__ void __launch_bounds__(C* C, (C == 16 ? 2 : 8))
 
   // producer: one warp stages batch b into buffer buf (lane l handles trace l)
   auto issue = [&](int b, int buf) {
-    const int it = b * kBatch + lane;
-    const int cnt = min(kBatch, P.n_items - b * kBatch);
+    const int it = ib + b * kBatch + lane;
+    const int cnt = min(kBatch, nl - b * kBatch);
     float* wdst = win + (buf * kBatch + lane) * WP;
     int x0 = 0, row = 0;
-    if (it < P.n_items) {
+    if (it < ib + nl) {
       const int fl = it / P.E, j = it % P.E;
       const int f = P.f_begin + fl;
       row = f * P.E + j;
       const double* xp = P.xw + static_cast<int64_t>(row) * 3;
-      const PairRef R = make_ref(xp[0], xp[1], xp[2], rcx, rcy, rcz, P.a0, P.tau0, P.inv_h);
+      const PairRef R = make_ref(xp[0], xp[1], xp[2], rcx, rcy, rcz, P.sup, P.tau0, P.inv_h);
       const int n0 = R.Nc + static_cast<int>(floorf(R.phim - P.nb_shift)) - 1;
       x0 = n0 & ~3;
       const float mk = (POSE && P.mask) ? (P.mask[row] ? 1.f : 0.f) : 1.f;
@@ -320,7 +378,7 @@ __global__ void __launch_bounds__(C* C, (C == 16 ? 2 : 8))
     if (P.use_tma) {
       if (lane == 0) mbar_arrive_expect_tx(&bar[buf], static_cast<uint32_t>(cnt * WP * 4));
       __syncwarp();
-      if (it < P.n_items) tma_load_2d(wdst, &gmap, &bar[buf], x0, row);
+      if (it < ib + nl) tma_load_2d(wdst, &gmap, &bar[buf], x0, row);
     } else {
       __threadfence_block();
       __syncwarp();
@@ -328,7 +386,7 @@ __global__ void __launch_bounds__(C* C, (C == 16 ? 2 : 8))
     }
   };
 
-  if (warp == 0) {
+  if (warp == 0 && nb > 0) {
     issue(0, 0);
     if (nb > 1) issue(1, 1);
   }
@@ -345,7 +403,7 @@ __global__ void __launch_bounds__(C* C, (C == 16 ? 2 : 8))
   for (int b = 0; b < nb; ++b) {
     const int buf = b & 1;
     const bool ok = mbar_wait_bounded(&bar[buf], (b >> 1) & 1, P.status);
-    const int cnt = min(kBatch, P.n_items - b * kBatch);
+    const int cnt = min(kBatch, nl - b * kBatch);
     const float* wb = win + buf * kBatch * WP;
     for (int e = 0; ok && e < cnt; ++e) {
       const float4 ra = refa[buf * kBatch + e];
@@ -360,27 +418,73 @@ __global__ void __launch_bounds__(C* C, (C == 16 ? 2 : 8))
         const PairMath m = pair_math(A, ra.w, rb.x, rb.y, P.inv_hf, P.h, P.cb1, idx_bias);
         seen = max(seen, m.idx);
         const float* gw = wv + min(m.idx, max_idx);
-        float g[S];
+        // S1 = sum_k g_k (b_k - b_{k+1}) by parts; S2 = the boundary-motion term of dW/dd
+        float S1, S2 = 0.f, lam;
+        if constexpr (K == PASFM_KERNEL_GAUSS) {
+          // b_s = -E_s (sign folded into P.scale < 0); visited outward from the centre
+          // boundary as in gauss_boundaries, without an array of values
+          constexpr int kc = gauss_centre<S>();
+          const float bc = fmaf(static_cast<float>(kc - 1), P.h, m.beta1);
+          const float Ec = exp2f(P.gs.c1 * (bc * bc));
+          float up = exp2f(fmaf(bc, P.gs.c2, P.gs.c3));
+          float dn = exp2f(fmaf(-bc, P.gs.c2, P.gs.c3));
+          float E = Ec, gp = gw[kc - 1];
+          S1 = 0.f;
 #pragma unroll
-        for (int s = 0; s < S; ++s) g[s] = gw[s];
-        float beta = m.beta1;
-        float S1 = P.a0sq * (g[0] - g[S - 1]);
-        float S2 = 0.f;
-#pragma unroll
-        for (int s = 1; s < S; ++s) {
-          if (s > 1) beta += P.h;
-          const float dg = g[s] - g[s - 1];
-          const float bc = (s == S - 1) ? fminf(beta, P.a0f) : beta;
-          S1 = fmaf(bc * bc, dg, S1);
-          if (POSE) {
-            const float D = (s == S - 1) ? (beta < P.a0f ? beta : 0.f) : beta;
-            S2 = fmaf(-D, dg, S2);
+          for (int s = kc; s < S; ++s) {
+            if (s > kc) {
+              E *= up;
+              up *= P.gs.q;
+            }
+            const float gs = gw[s];
+            const float dg = gs - gp;
+            gp = gs;
+            const float Es = (s == S - 1) ? fmaxf(E, P.gs.e_clamp) : E;
+            S1 = fmaf(Es, dg, S1);
+            if (POSE) {
+              const float beta = fmaf(static_cast<float>(s - 1), P.h, m.beta1);
+              const float D = (s == S - 1) ? (beta < P.supf ? beta * Es : 0.f) : beta * Es;
+              S2 = fmaf(D, dg, S2);
+            }
           }
+          const float g_last = gp;
+          E = Ec;
+          float gn = gw[kc - 1];
+#pragma unroll
+          for (int s = kc - 1; s >= 1; --s) {
+            E *= dn;
+            dn *= P.gs.q;
+            const float gs = gw[s - 1];
+            const float dg = gn - gs;
+            gn = gs;
+            S1 = fmaf(E, dg, S1);
+            if (POSE) S2 = fmaf(fmaf(static_cast<float>(s - 1), P.h, m.beta1) * E, dg, S2);
+          }
+          S1 = fmaf(P.gs.e_clamp, gn - g_last, S1);
+          lam = P.lam;
+        } else {
+          float g[S];
+#pragma unroll
+          for (int s = 0; s < S; ++s) g[s] = gw[s];
+          float beta = m.beta1;
+          S1 = P.sup2 * (g[0] - g[S - 1]);
+#pragma unroll
+          for (int s = 1; s < S; ++s) {
+            if (s > 1) beta += P.h;
+            const float dg = g[s] - g[s - 1];
+            const float bc = (s == S - 1) ? fminf(beta, P.supf) : beta;
+            S1 = fmaf(bc * bc, dg, S1);
+            if (POSE) {
+              const float D = (s == S - 1) ? (beta < P.supf ? beta : 0.f) : beta;
+              S2 = fmaf(-D, dg, S2);
+            }
+          }
+          lam = 2.f;
         }
         const float t1 = m.rs * S1;
         if (ADJ) bacc[k] += t1;
         if (POSE) {
-          const float coef = p0s[k] * (m.rs * m.rs) * fmaf(2.f, S2, -t1);
+          const float coef = p0s[k] * (m.rs * m.rs) * fmaf(lam, S2, -t1);
           R0 += coef;
           R1 = fmaf(coef, qx[k], R1);
         }
@@ -426,7 +530,7 @@ __global__ void __launch_bounds__(C* C, (C == 16 ? 2 : 8))
         }
         const float mk = refb[buf * kBatch + lane].w;
         const double* u = refu + (buf * kBatch + lane) * 3;
-        double* gp = P.gpart + (static_cast<int64_t>(b * kBatch + lane) * ncubes + c) * 3;
+        double* gp = P.gpart + (static_cast<int64_t>(ib + b * kBatch + lane) * ncubes + c) * 3;
         gp[0] = mk * (u[0] * r0 - r1);
         gp[1] = mk * (u[1] * r0 - r2);
         gp[2] = mk * (u[2] * r0 - r3);
@@ -438,13 +542,18 @@ __global__ void __launch_bounds__(C* C, (C == 16 ? 2 : 8))
   if (seen > max_idx) atomicOr(P.status, PASFM_STATUS_INDEX_CLAMPED);
 
   if (ADJ && row_in) {
-    float* out = P.vol + (static_cast<int64_t>(iz) * P.ny + iy) * P.nx;
+    // one part: straight into the volume; several: into this part's slice of vol_parts,
+    // summed in part order by sum_parts_kernel
+    const int64_t nvox = static_cast<int64_t>(P.nx) * P.ny * P.nz;
+    float* out = (P.n_parts > 1 ? P.vol_parts + blockIdx.y * nvox : P.vol) +
+                 (static_cast<int64_t>(iz) * P.ny + iy) * P.nx;
+    const bool add = P.n_parts == 1 && P.accumulate;
 #pragma unroll
     for (int k = 0; k < C; ++k) {
       const int ix = cx * C + k;
       if (ix < P.nx) {
         const float v = acc[k] * P.scale;
-        out[ix] = P.accumulate ? out[ix] + v : v;
+        out[ix] = add ? out[ix] + v : v;
       }
     }
   }

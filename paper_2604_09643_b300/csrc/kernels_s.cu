@@ -1,20 +1,23 @@
-// Instantiates the forward and backward hot kernels for one slot count S
-// (compiled once per S = 2..16 with -DPASFM_S=<S>) and exports their launchers.
+// Instantiates the forward and backward hot kernels for one pulse profile K and
+// one slot count S (compiled once per pair with -DPASFM_K=<K> -DPASFM_S=<S>:
+// the sphere for S = 2..16, the Gaussian for S = 2..32) and exports their
+// launchers fwd_launch_k<K>_s<S> and bwd_launch_k<K>_s<S>.
 #include "aux.cuh"
 #include "kernels.cuh"
 
-#ifndef PASFM_S
-#error "compile with -DPASFM_S=<slots per pair>"
+#if !defined(PASFM_S) || !defined(PASFM_K)
+#error "compile with -DPASFM_K=<pulse profile> -DPASFM_S=<slots per pair>"
 #endif
 #define PASFM_CAT2(a, b) a##b
 #define PASFM_CAT(a, b) PASFM_CAT2(a, b)
+#define PASFM_NAME(what) PASFM_CAT(PASFM_CAT(PASFM_CAT(what, _k), PASFM_K), PASFM_CAT(_s, PASFM_S))
 
 namespace pasfm {
 
 template <int C>
 static cudaError_t fwd_launch_c(const CUtensorMap& map, const FwdParams& P, dim3 grid, int threads, size_t smem,
                                 cudaStream_t st) {
-  auto k = fwd_cube_kernel<C, PASFM_S>;
+  auto k = fwd_cube_kernel<C, PASFM_S, PASFM_K>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (e != cudaSuccess) return e;
   k<<<grid, threads, smem, st>>>(map, P);
@@ -24,14 +27,26 @@ static cudaError_t fwd_launch_c(const CUtensorMap& map, const FwdParams& P, dim3
 template <int C, bool ADJ, bool POSE>
 static cudaError_t bwd_launch_c(const CUtensorMap& map, const BwdParams& P, dim3 grid, size_t smem,
                                 cudaStream_t st) {
-  auto k = bwd_cube_kernel<C, PASFM_S, ADJ, POSE>;
+  auto k = bwd_cube_kernel<C, PASFM_S, PASFM_K, ADJ, POSE>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (e != cudaSuccess) return e;
   k<<<grid, C * C, smem, st>>>(map, P);
   return cudaPeekAtLastError();
 }
 
-cudaError_t PASFM_CAT(fwd_launch_s, PASFM_S)(int C, const CUtensorMap& map, const FwdParams& P, dim3 grid,
+template <int C, bool ADJ, bool POSE>
+static int bwd_occupancy_c(size_t smem) {
+  auto k = bwd_cube_kernel<C, PASFM_S, PASFM_K, ADJ, POSE>;
+  int n = 0;
+  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, C * C, smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
+}
+
+cudaError_t PASFM_NAME(fwd_launch)(int C, const CUtensorMap& map, const FwdParams& P, dim3 grid,
                                              int threads, size_t smem, cudaStream_t st) {
   if (C == 16) return fwd_launch_c<16>(map, P, grid, threads, smem, st);
   if (C == 8) return fwd_launch_c<8>(map, P, grid, threads, smem, st);
@@ -39,7 +54,7 @@ cudaError_t PASFM_CAT(fwd_launch_s, PASFM_S)(int C, const CUtensorMap& map, cons
 }
 
 // mode: 1 = adjoint, 2 = pose gradient, 3 = both
-cudaError_t PASFM_CAT(bwd_launch_s, PASFM_S)(int C, int mode, const CUtensorMap& map, const BwdParams& P,
+cudaError_t PASFM_NAME(bwd_launch)(int C, int mode, const CUtensorMap& map, const BwdParams& P,
                                              dim3 grid, size_t smem, cudaStream_t st) {
   if (C == 16) {
     if (mode == 1) return bwd_launch_c<16, true, false>(map, P, grid, smem, st);
@@ -51,6 +66,20 @@ cudaError_t PASFM_CAT(bwd_launch_s, PASFM_S)(int C, int mode, const CUtensorMap&
     if (mode == 3) return bwd_launch_c<8, true, true>(map, P, grid, smem, st);
   }
   return cudaErrorInvalidValue;
+}
+
+// Resident CTAs per SM of the backward kernel (0 if the query fails).
+int PASFM_NAME(bwd_occupancy)(int C, int mode, size_t smem) {
+  if (C == 16) {
+    if (mode == 1) return bwd_occupancy_c<16, true, false>(smem);
+    if (mode == 2) return bwd_occupancy_c<16, false, true>(smem);
+    if (mode == 3) return bwd_occupancy_c<16, true, true>(smem);
+  } else if (C == 8) {
+    if (mode == 1) return bwd_occupancy_c<8, true, false>(smem);
+    if (mode == 2) return bwd_occupancy_c<8, false, true>(smem);
+    if (mode == 3) return bwd_occupancy_c<8, true, true>(smem);
+  }
+  return 0;
 }
 
 }  // namespace pasfm

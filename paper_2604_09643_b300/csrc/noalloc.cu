@@ -21,7 +21,8 @@
 #include "kernels.cuh"
 
 namespace pasfm {
-int plan_geometry(const pasfm_geom* geom, Plan* pl, double* a0);
+int plan_geometry(const pasfm_geom* geom, Plan* pl);
+void set_bwd_profile(const Plan& pl, BwdParams* P);
 int report_error(int code, const char* msg);
 }  // namespace pasfm
 
@@ -38,12 +39,6 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[PASFM_NOALLOC_S
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 void* g_scratch_ptr[kMaxDevices] = {};
-
-const BwdLaunch kBwdTab[kMaxS + 1] = {nullptr,        nullptr,        bwd_launch_s2,  bwd_launch_s3,
-                                      bwd_launch_s4,  bwd_launch_s5,  bwd_launch_s6,  bwd_launch_s7,
-                                      bwd_launch_s8,  bwd_launch_s9,  bwd_launch_s10, bwd_launch_s11,
-                                      bwd_launch_s12, bwd_launch_s13, bwd_launch_s14, bwd_launch_s15,
-                                      bwd_launch_s16};
 
 // Device address of the scratch on the current device (looked up once per device).
 int scratch_address(void** out) {
@@ -94,8 +89,7 @@ extern "C" int pasfm_pose_grad_noalloc(const pasfm_geom* geom, const void* p0, c
                                        const double* pose, const void* g, const uint8_t* mask, double* grad6_out,
                                        double* gelem_out, void* stream) {
   Plan pl;
-  double a0 = 0.0;
-  int rc = plan_geometry(geom, &pl, &a0);
+  int rc = plan_geometry(geom, &pl);
   if (rc != PASFM_OK) return rc;
   const int F = geom->n_frames, E = geom->n_elem, Nt = geom->n_samples;
   const int64_t rows = int64_t(F) * E;
@@ -144,7 +138,7 @@ extern "C" int pasfm_pose_grad_noalloc(const pasfm_geom* geom, const void* p0, c
   const double hix = geom->ox + geom->dx * (geom->nx - 1), hiy = geom->oy + geom->dy * (geom->ny - 1),
                hiz = geom->oz + geom->dz * (geom->nz - 1);
   elem_pos_kernel<<<static_cast<unsigned>((rows + 255) / 256), 256, 0, st>>>(
-      elem, pose, xw, F, E, geom->ox, geom->oy, geom->oz, hix, hiy, hiz, a0, status);
+      elem, pose, xw, F, E, geom->ox, geom->oy, geom->oz, hix, hiy, hiz, pl.sup, status);
   rc = launch_ok("pasfm_pose_grad_noalloc: elem_pos launch failed");
   if (rc != PASFM_OK) return rc;
 
@@ -180,6 +174,9 @@ extern "C" int pasfm_pose_grad_noalloc(const pasfm_geom* geom, const void* p0, c
   P.E = E;
   P.f_begin = 0;
   P.n_items = static_cast<int>(rows);
+  P.n_parts = 1;  // one CTA per cube: no per-part adjoint buffer is needed (pose gradient only)
+  P.part_items = static_cast<int>(rows);
+  P.vol_parts = nullptr;
   P.Nt = Nt;
   P.WP = pl.WP;
   P.accumulate = 0;
@@ -189,20 +186,11 @@ extern "C" int pasfm_pose_grad_noalloc(const pasfm_geom* geom, const void* p0, c
   P.dx = geom->dx;
   P.dy = geom->dy;
   P.dz = geom->dz;
-  P.tau0 = pl.tau0;
-  P.inv_h = pl.inv_h;
-  P.a0 = a0;
-  P.h = static_cast<float>(pl.h);
-  P.a0f = static_cast<float>(a0);
-  P.a0sq = P.a0f * P.a0f;
-  P.nb_shift = pl.nb_shift;
-  P.scale = static_cast<float>(0.25 / pl.h);
-  P.inv_hf = static_cast<float>(pl.inv_h);
-  P.cb1 = static_cast<float>(-a0 + 0.5 * pl.h);
+  set_bwd_profile(pl, &P);
   P.use_tma = use_tma;
   P.status = status;
   const size_t smem = pl.C == 16 ? BwdLayout<16>::total(pl.WP) : BwdLayout<8>::total(pl.WP);
-  const cudaError_t e = kBwdTab[pl.S](pl.C, 2, map, P, dim3(pl.ncubes), smem, st);
+  const cudaError_t e = bwd_launcher(pl.K, pl.S)(pl.C, 2, map, P, dim3(pl.ncubes), smem, st);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return report_error(PASFM_ECUDA, "pasfm_pose_grad_noalloc: bwd_cube launch failed");

@@ -57,18 +57,8 @@ struct Rec {
   cudaEvent_t a, b;
 };
 
-const FwdLaunch kFwd[kMaxS + 1] = {nullptr,        nullptr,        fwd_launch_s2,  fwd_launch_s3,
-                                   fwd_launch_s4,  fwd_launch_s5,  fwd_launch_s6,  fwd_launch_s7,
-                                   fwd_launch_s8,  fwd_launch_s9,  fwd_launch_s10, fwd_launch_s11,
-                                   fwd_launch_s12, fwd_launch_s13, fwd_launch_s14, fwd_launch_s15,
-                                   fwd_launch_s16};
-const BwdLaunch kBwd[kMaxS + 1] = {nullptr,        nullptr,        bwd_launch_s2,  bwd_launch_s3,
-                                   bwd_launch_s4,  bwd_launch_s5,  bwd_launch_s6,  bwd_launch_s7,
-                                   bwd_launch_s8,  bwd_launch_s9,  bwd_launch_s10, bwd_launch_s11,
-                                   bwd_launch_s12, bwd_launch_s13, bwd_launch_s14, bwd_launch_s15,
-                                   bwd_launch_s16};
-
 constexpr size_t kDefaultPartialBudget = size_t(4) << 30;
+constexpr int kMaxParts = 4;  // backward CTAs per cube (item parts); bounds the per-part adjoint buffer
 constexpr int kFwdWmax16 = 128;  // forward window cap for 16^3 cubes (8 warps x W x 128 B)
 constexpr int kFwdWmax8 = 200;   // forward window cap for 8^3 cubes
 
@@ -90,9 +80,12 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 struct Geo {  // validated geometry with defaults applied
   pasfm_geom g;
   double a0;
+  double sup;      // pulse support half-width (mm): a0, or 4 sigma for the Gaussian
   int64_t nvox;
   int64_t n_rows;  // F * E
 };
+
+constexpr double kGaussSupport = 4.0;  // Gaussian support half-width in sigmas (reading: unstated)
 
 int check_geom(const pasfm_geom* g, Geo* out) {
   if (!g) return fail(PASFM_EINVAL, "geom is NULL");
@@ -104,8 +97,14 @@ int check_geom(const pasfm_geom* g, Geo* out) {
     return fail(PASFM_EINVAL, "non-finite origin or t0");
   for (int d : {g->dtype_vol, g->dtype_sig})
     if (d != PASFM_F32 && d != PASFM_BF16 && d != PASFM_F16) return fail(PASFM_EINVAL, "unknown dtype %d", d);
+  if (g->kernel != PASFM_KERNEL_SPHERE && g->kernel != PASFM_KERNEL_GAUSS)
+    return fail(PASFM_EINVAL, "unknown kernel %d", g->kernel);
+  if (g->reserved != 0) return fail(PASFM_EINVAL, "geom.reserved must be 0");
+  if (g->kernel == PASFM_KERNEL_GAUSS && !(g->sigma_mm > 0 && std::isfinite(g->sigma_mm)))
+    return fail(PASFM_EINVAL, "the Gaussian kernel needs a finite sigma_mm > 0");
   out->g = *g;
   out->a0 = g->a0_mm > 0 ? g->a0_mm : 0.5 * std::min(g->dx, std::min(g->dy, g->dz));
+  out->sup = g->kernel == PASFM_KERNEL_GAUSS ? kGaussSupport * g->sigma_mm : out->a0;
   out->nvox = int64_t(g->nx) * g->ny * g->nz;
   out->n_rows = int64_t(g->n_frames) * g->n_elem;
   if (out->n_rows > INT32_MAX / 2) return fail(PASFM_EUNSUPPORTED, "F * E too large");
@@ -117,11 +116,15 @@ int make_plan(const Geo& G, Plan* pl) {
   pl->h = g.c_mm_per_us / g.fs_mhz;
   pl->inv_h = 1.0 / pl->h;
   pl->tau0 = g.c_mm_per_us * g.t0_us;
-  const double L = 2.0 * G.a0 / pl->h;
+  pl->K = g.kernel;
+  pl->sup = G.sup;
+  pl->sigma = g.kernel == PASFM_KERNEL_GAUSS ? g.sigma_mm : 0.0;
+  const double L = 2.0 * G.sup / pl->h;
   pl->S = static_cast<int>(std::floor(L)) + 2;
-  if (pl->S > kMaxS)
-    return fail(PASFM_EUNSUPPORTED, "a0 / h = %.3f: a pair spans %d samples, more than the %d compiled", L / 2,
-                pl->S, kMaxS);
+  const int smax = g.kernel == PASFM_KERNEL_GAUSS ? kMaxSGauss : kMaxSSphere;
+  if (pl->S > smax)
+    return fail(PASFM_EUNSUPPORTED, "support / h = %.3f: a pair spans %d samples, more than the %d compiled",
+                L / 2, pl->S, smax);
   const double diag = std::sqrt(g.dx * g.dx + g.dy * g.dy + g.dz * g.dz);
   auto window = [&](int C) {
     const double rho = 0.5 * (C - 1) * diag;
@@ -166,7 +169,8 @@ int frames_per_chunk(size_t per_frame, size_t budget, int F) {
 struct pasfm_ctx {
   int device = 0;
   unsigned* status = nullptr;
-  Buf xw, part, n0, gres, vgrad, gpart, G, grad6, lpart, lscalar, taps;
+  Buf xw, part, n0, gres, vgrad, gpart, G, grad6, lpart, lscalar, taps, vparts;
+  int sms = 0;  // streaming multiprocessors of the device
   size_t budget = kDefaultPartialBudget;
   bool timing = false;
   std::vector<Rec> recs;
@@ -233,6 +237,78 @@ int set_device(pasfm_ctx* ctx) {
 
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
+// Factor of the slot sums: W = kappa (b_k - b_{k+1}) / d with kappa = 1 / (4 h) for
+// the sphere (b = beta^2) and sigma^2 / (2 h) for the Gaussian (b = -E).
+double pulse_scale(const Plan& pl) {
+  return pl.K == PASFM_KERNEL_GAUSS ? pl.sigma * pl.sigma / (2.0 * pl.h) : 0.25 / pl.h;
+}
+
+}  // namespace
+
+namespace pasfm {
+
+// Time-of-flight and pulse-profile fields shared by the forward and backward parameters.
+template <class Params>
+void set_profile(const Plan& pl, Params& P) {
+  P.tau0 = pl.tau0;
+  P.inv_h = pl.inv_h;
+  P.sup = pl.sup;
+  P.h = static_cast<float>(pl.h);
+  P.supf = static_cast<float>(pl.sup);
+  P.sup2 = P.supf * P.supf;
+  P.nb_shift = pl.nb_shift;
+  P.inv_hf = static_cast<float>(pl.inv_h);
+  P.cb1 = static_cast<float>(-pl.sup + 0.5 * pl.h);
+  P.gs = GaussConst{};
+  if (pl.K == PASFM_KERNEL_GAUSS) {
+    const double s2 = pl.sigma * pl.sigma, log2e = 1.4426950408889634;
+    P.gs.c1 = static_cast<float>(-log2e / (2.0 * s2));
+    P.gs.c2 = static_cast<float>(-log2e * pl.h / s2);
+    P.gs.c3 = static_cast<float>(-log2e * pl.h * pl.h / (2.0 * s2));
+    P.gs.q = static_cast<float>(std::exp(-pl.h * pl.h / s2));
+    P.gs.e_clamp = static_cast<float>(std::exp(-pl.sup * pl.sup / (2.0 * s2)));
+  }
+}
+
+// Profile fields of the backward parameters, including the sign-folded scale
+// (the Gaussian slot sums run over +E, i.e. -b) and the pose-term weight.
+void set_bwd_profile(const Plan& pl, BwdParams* P) {
+  set_profile(pl, *P);
+  const double k = pulse_scale(pl);
+  P->scale = static_cast<float>(pl.K == PASFM_KERNEL_GAUSS ? -k : k);
+  P->lam = static_cast<float>(pl.K == PASFM_KERNEL_GAUSS ? 1.0 / (pl.sigma * pl.sigma) : 2.0);
+}
+
+}  // namespace pasfm
+
+namespace {
+
+// CTAs per cube for the backward: the item list of every cube is split into
+// `parts` runs (whole 32-item batches) so that ncubes * parts CTAs fill the
+// resident slots in whole waves.  A last partial wave leaves SMs idle (512
+// cubes on 296 slots use 86% of them); the split is taken when it gains more
+// than 1% and every part keeps at least 4 batches.
+int choose_parts(int ncubes, int n_items, int slots) {
+  if (slots <= 0 || ncubes <= 0) return 1;
+  auto eff = [&](int p) {
+    const int64_t ctas = int64_t(ncubes) * p;
+    const int64_t waves = (ctas + slots - 1) / slots;
+    return double(ctas) / double(waves * slots);
+  };
+  int best = 1;
+  double best_eff = eff(1);
+  for (int p = 2; p <= kMaxParts; ++p) {
+    const int per = ((n_items + p - 1) / p + 31) / 32 * 32;
+    if (per < 4 * 32 || int64_t(per) * (p - 1) >= n_items) break;
+    const double e = eff(p);
+    if (e > best_eff + 0.01) {
+      best = p;
+      best_eff = e;
+    }
+  }
+  return best;
+}
+
 // A1: element positions into `out`.
 int run_elem_pos(pasfm_ctx* ctx, const Geo& G, const double* elem, const double* pose, double* out,
                  cudaStream_t st) {
@@ -243,10 +319,10 @@ int run_elem_pos(pasfm_ctx* ctx, const Geo& G, const double* elem, const double*
   const double hix = g.ox + g.dx * std::max(g.nx - 1, 0), hiy = g.oy + g.dy * std::max(g.ny - 1, 0),
                hiz = g.oz + g.dz * std::max(g.nz - 1, 0);
   // an empty grid has no voxel an element could be inside
-  const double a0chk = G.nvox > 0 ? G.a0 : -1.0;
+  const double supchk = G.nvox > 0 ? G.sup : -1.0;
   cudaEvent_t t = ctx->begin(st);
   elem_pos_kernel<<<static_cast<unsigned>((n + 255) / 256), 256, 0, st>>>(
-      elem, pose, out, g.n_frames, g.n_elem, lox, loy, loz, hix, hiy, hiz, a0chk, ctx->status);
+      elem, pose, out, g.n_frames, g.n_elem, lox, loy, loz, hix, hiy, hiz, supchk, ctx->status);
   ctx->end("elem_pos", t, st);
   return check_launch("elem_pos");
 }
@@ -301,16 +377,8 @@ int run_forward(pasfm_ctx* ctx, const Geo& G, const Plan& pl, const void* p0, co
   P.dx = g.dx;
   P.dy = g.dy;
   P.dz = g.dz;
-  P.tau0 = pl.tau0;
-  P.inv_h = pl.inv_h;
-  P.a0 = G.a0;
-  P.h = static_cast<float>(pl.h);
-  P.a0f = static_cast<float>(G.a0);
-  P.a0sq = P.a0f * P.a0f;
-  P.nb_shift = pl.nb_shift;
-  P.p0_scale = static_cast<float>(0.25 / pl.h);
-  P.inv_hf = static_cast<float>(pl.inv_h);
-  P.cb1 = static_cast<float>(-G.a0 + 0.5 * pl.h);
+  set_profile(pl, P);
+  P.p0_scale = static_cast<float>(pulse_scale(pl));
   P.use_tma = use_tma;
   P.status = ctx->status;
 
@@ -326,7 +394,7 @@ int run_forward(pasfm_ctx* ctx, const Geo& G, const Plan& pl, const void* p0, co
     P.f_begin = fb;
     dim3 grid(pl.ncubes, fc, pl.n_egroups);
     cudaEvent_t t = ctx->begin(st);
-    cudaError_t e = kFwd[pl.S](pl.C, map, P, grid, threads, smem, st);
+    cudaError_t e = fwd_launcher(pl.K, pl.S)(pl.C, map, P, grid, threads, smem, st);
     ctx->end("fwd_cube", t, st);
     if (e != cudaSuccess) {
       cudaGetLastError();
@@ -414,31 +482,36 @@ int run_backward(pasfm_ctx* ctx, const Geo& G, const Plan& pl, int mode, const v
   P.dx = g.dx;
   P.dy = g.dy;
   P.dz = g.dz;
-  P.tau0 = pl.tau0;
-  P.inv_h = pl.inv_h;
-  P.a0 = G.a0;
-  P.h = static_cast<float>(pl.h);
-  P.a0f = static_cast<float>(G.a0);
-  P.a0sq = P.a0f * P.a0f;
-  P.nb_shift = pl.nb_shift;
-  P.scale = static_cast<float>(0.25 / pl.h);
-  P.inv_hf = static_cast<float>(pl.inv_h);
-  P.cb1 = static_cast<float>(-G.a0 + 0.5 * pl.h);
+  set_bwd_profile(pl, &P);
   P.use_tma = use_tma;
   P.status = ctx->status;
   const size_t smem = pl.C == 16 ? BwdLayout<16>::total(pl.WP) : BwdLayout<8>::total(pl.WP);
+  const int per_sm = bwd_occupancy(pl.K, pl.S)(pl.C, mode, smem);
+  const bool adj = mode & 1;
+  if (adj) TRY(ctx->ensure(ctx->vparts, size_t(G.nvox) * 4 * kMaxParts));
 
   for (int fb = 0; fb < F; fb += Fc) {
     const int fc = std::min(Fc, F - fb);
     P.f_begin = fb;
     P.n_items = fc * E;
     P.accumulate = fb > 0;
+    P.n_parts = choose_parts(pl.ncubes, P.n_items, per_sm * ctx->sms);
+    P.part_items = P.n_parts > 1 ? ((P.n_items + P.n_parts - 1) / P.n_parts + 31) / 32 * 32 : P.n_items;
+    P.vol_parts = static_cast<float*>(ctx->vparts.p);
     cudaEvent_t t = ctx->begin(st);
-    cudaError_t e = kBwd[pl.S](pl.C, mode, map, P, dim3(pl.ncubes), smem, st);
+    cudaError_t e = bwd_launcher(pl.K, pl.S)(pl.C, mode, map, P, dim3(pl.ncubes, P.n_parts), smem, st);
     ctx->end("bwd_cube", t, st);
     if (e != cudaSuccess) {
       cudaGetLastError();
       return fail(PASFM_ECUDA, "bwd_cube launch: %s", cudaGetErrorString(e));
+    }
+    if (adj && P.n_parts > 1) {
+      const int64_t nv = G.nvox;
+      const unsigned blocks = static_cast<unsigned>(std::min<int64_t>((nv + 255) / 256, 148 * 16));
+      t = ctx->begin(st);
+      sum_parts_kernel<<<blocks, 256, 0, st>>>(P.vol_parts, P.n_parts, nv, vol, P.accumulate);
+      ctx->end("sum_parts", t, st);
+      TRY(check_launch("sum_parts"));
     }
     if (pose) {
       const int rows = fc * E;
@@ -471,7 +544,7 @@ int prepare(pasfm_ctx* ctx, const pasfm_geom* geom, Geo* G, Plan* pl) {
 
 extern "C" {
 
-int pasfm_abi_version(void) { return 1; }
+int pasfm_abi_version(void) { return 2; }
 
 const char* pasfm_last_error(void) { return g_err.c_str(); }
 
@@ -486,6 +559,10 @@ int pasfm_create(pasfm_ctx** out, int device) {
   CUDA_TRY(cudaSetDevice(device));
   pasfm_ctx* ctx = new pasfm_ctx();
   ctx->device = device;
+  if (cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+    cudaGetLastError();
+    ctx->sms = 0;
+  }
   if (cudaMalloc(&ctx->status, sizeof(unsigned)) != cudaSuccess ||
       cudaMemset(ctx->status, 0, sizeof(unsigned)) != cudaSuccess) {
     cudaGetLastError();
@@ -500,7 +577,7 @@ int pasfm_destroy(pasfm_ctx* ctx) {
   if (!ctx) return PASFM_OK;
   cudaSetDevice(ctx->device);
   for (Buf* b : {&ctx->xw, &ctx->part, &ctx->n0, &ctx->gres, &ctx->vgrad, &ctx->gpart, &ctx->G, &ctx->grad6,
-                 &ctx->lpart, &ctx->lscalar, &ctx->taps})
+                 &ctx->lpart, &ctx->lscalar, &ctx->taps, &ctx->vparts})
     if (b->p) cudaFree(b->p);
   for (auto& r : ctx->recs) {
     cudaEventDestroy(r.a);
@@ -533,6 +610,7 @@ int pasfm_workspace_size(const pasfm_geom* geom, size_t* bytes) {
   b += size_t(Fb) * bwd_per_frame(G, pl);                                   // gpart
   b += size_t(G.n_rows) * G.g.n_samples * 4;                                // residual (step)
   b += size_t(G.nvox) * 4;                                                  // volume gradient (step)
+  b += size_t(G.nvox) * 4 * kMaxParts;                                      // per-part adjoint sums
   b += size_t(G.n_rows) * 24 + size_t(F) * 48;                              // G, grad6
   b += (size_t(G.n_rows + 7) / 8 + (F + Ff - 1) / std::max(Ff, 1) + 2) * 8;  // loss partials
   *bytes = b;
@@ -552,6 +630,7 @@ int pasfm_reserve(pasfm_ctx* ctx, const pasfm_geom* geom) {
   TRY(ctx->ensure(ctx->gpart, size_t(Fb) * G.g.n_elem * pl.ncubes * 24));
   TRY(ctx->ensure(ctx->gres, size_t(G.n_rows) * G.g.n_samples * 4));
   TRY(ctx->ensure(ctx->vgrad, size_t(G.nvox) * 4));
+  TRY(ctx->ensure(ctx->vparts, size_t(G.nvox) * 4 * kMaxParts));
   TRY(ctx->ensure(ctx->G, size_t(G.n_rows) * 24));
   TRY(ctx->ensure(ctx->grad6, size_t(F) * 48));
   TRY(ctx->ensure(ctx->lpart, (size_t(G.n_rows + 7) / 8 + (F + Ff - 1) / std::max(Ff, 1) + 2) * 8));
@@ -681,6 +760,7 @@ int pasfm_step(pasfm_ctx* ctx, const pasfm_geom* geom, void* p0, double* pose, c
   TRY(ctx->ensure(ctx->xw, size_t(G.n_rows) * 24));
   TRY(ctx->ensure(ctx->gres, size_t(G.n_rows) * G.g.n_samples * 4));
   TRY(ctx->ensure(ctx->vgrad, size_t(G.nvox) * 4));
+  TRY(ctx->ensure(ctx->vparts, size_t(G.nvox) * 4 * kMaxParts));
   TRY(ctx->ensure(ctx->G, size_t(G.n_rows) * 24));
   TRY(ctx->ensure(ctx->grad6, size_t(G.g.n_frames) * 48));
   double* xw = static_cast<double*>(ctx->xw.p);
@@ -771,12 +851,14 @@ int pasfm_resample(pasfm_ctx* ctx, const pasfm_geom* src_geom, const float* src,
   return check_launch("resample");
 }
 
-int pasfm_lowpass(pasfm_ctx* ctx, int64_t n_rows, int n_samples, double sigma, const float* src, float* dst,
-                  void* stream) {
+int pasfm_lowpass(pasfm_ctx* ctx, int64_t n_rows, int n_samples, double sigma, int decim, const float* src,
+                  float* dst, void* stream) {
   if (!ctx) return fail(PASFM_EINVAL, "ctx is NULL");
   if (n_rows < 0 || n_samples < 0 || !std::isfinite(sigma)) return fail(PASFM_EINVAL, "bad size or sigma");
+  if (decim < 1) return fail(PASFM_EINVAL, "decim must be >= 1");
   if (n_rows == 0 || n_samples == 0) return PASFM_OK;
   if (!src || !dst) return fail(PASFM_EINVAL, "NULL array argument");
+  if (decim > 1 && src == dst) return fail(PASFM_EINVAL, "dst may alias src only without decimation");
   if (n_rows > INT32_MAX) return fail(PASFM_EUNSUPPORTED, "too many traces");
   if (size_t(n_samples) * 4 > 200 * 1024) return fail(PASFM_EUNSUPPORTED, "trace longer than 51200 samples");
   TRY(set_device(ctx));
@@ -794,7 +876,8 @@ int pasfm_lowpass(pasfm_ctx* ctx, int64_t n_rows, int n_samples, double sigma, c
   const size_t smem = size_t(n_samples) * 4;
   CUDA_TRY(cudaFuncSetAttribute(lowpass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
   cudaEvent_t t = ctx->begin(st);
-  lowpass_kernel<<<static_cast<unsigned>(n_rows), 256, smem, st>>>(src, dst, n_samples, r,
+  const int n_out = (n_samples + decim - 1) / decim;
+  lowpass_kernel<<<static_cast<unsigned>(n_rows), 256, smem, st>>>(src, dst, n_samples, r, decim, n_out,
                                                                    static_cast<float*>(ctx->taps.p));
   ctx->end("lowpass", t, st);
   TRY(check_launch("lowpass"));
@@ -874,11 +957,10 @@ namespace pasfm {
 
 // Geometry validation and planning for entry points defined in other
 // translation units (the allocation-free pose gradient in noalloc.cu).
-int plan_geometry(const pasfm_geom* geom, Plan* pl, double* a0) {
+int plan_geometry(const pasfm_geom* geom, Plan* pl) {
   Geo G;
   TRY(check_geom(geom, &G));
   TRY(make_plan(G, pl));
-  *a0 = G.a0;
   return PASFM_OK;
 }
 

@@ -23,8 +23,11 @@ constexpr long long kWaitCycles = 2000000000LL;  // ~1 s at 2 GHz: bound of ever
 // Plan: how a geometry maps onto cubes of voxels and time windows (host-built).
 // ---------------------------------------------------------------------------
 struct Plan {
+  int K;          // voxel pulse: PASFM_KERNEL_SPHERE or PASFM_KERNEL_GAUSS
+  double sup;     // pulse support half-width in distance (mm): a0, or 4 sigma
+  double sigma;   // Gaussian width (mm); 0 for the sphere
   int C;          // cube side in voxels (8 or 16)
-  int S;          // sample slots per voxel-element pair: floor(2 a0 / h) + 2
+  int S;          // sample slots per voxel-element pair: floor(2 sup / h) + 2
   int W;          // forward window length per element and cube (multiple of 4)
   int WP;         // backward staged window length (W + 4, multiple of 32)
   int ncx, ncy, ncz, ncubes;
@@ -36,10 +39,20 @@ struct Plan {
 
 // Per-(cube, element) reference quantities, computed in FP64 and rounded.
 //   u = x - r_c (element relative to the cube centre), d_c = |u|,
-//   psi_c = (d_c - a0 - tau0) / h + 1/2 = N_c + phi_c  (N_c integer).
+//   psi_c = (d_c - sup - tau0) / h + 1/2 = N_c + phi_c  (N_c integer; sup = the
+//   pulse support half-width, a0 for the sphere and 4 sigma for the Gaussian).
 // A voxel at r_c + q then has  A = |q|^2 - 2 q.u,  d = sqrt(d_c^2 + A),
 // delta = d - d_c = A / (d + d_c), and its first touched sample is
 // N_c + floor(phi_c + delta / h).  Only small quantities are kept in FP32.
+
+// Constants of the Gaussian boundary values E(beta) = exp(-beta^2 / (2 sigma^2)),
+// in base 2 for exp2f, and of their ratio recurrence on the sample grid.
+struct GaussConst {
+  float c1;       // -log2(e) / (2 sigma^2):        E(beta)           = 2^(c1 beta^2)
+  float c2, c3;   // -log2(e) h / sigma^2, c1 h^2:  E(beta+h)/E(beta) = 2^(c2 beta + c3)
+  float q;        // exp(-h^2 / sigma^2): ratio of consecutive such ratios
+  float e_clamp;  // E at the support edge, exp(-8)
+};
 
 struct FwdParams {
   const double* xw;     // [F][E][3]
@@ -52,8 +65,9 @@ struct FwdParams {
   int E, f_begin;
   int W;
   double ox, oy, oz, dx, dy, dz;
-  double tau0, inv_h, a0;
-  float h, a0f, a0sq, nb_shift, p0_scale, inv_hf, cb1;
+  double tau0, inv_h, sup;
+  float h, supf, sup2, nb_shift, p0_scale, inv_hf, cb1;
+  GaussConst gs;
   int use_tma;
   unsigned* status;
 };
@@ -77,14 +91,19 @@ struct BwdParams {
   const void* g;        // [F][E][Nt] of dtype_sig (fallback loads)
   const uint8_t* mask;  // [F][E] or null (POSE)
   float* vol;           // [nz][ny][nx] adjoint output (ADJ)
+  float* vol_parts;     // [n_parts][nz][ny][nx] per-part adjoint sums when n_parts > 1 (ADJ)
+  int n_parts;          // CTAs per cube (grid.y); each takes part_items consecutive items
+  int part_items;       // multiple of the 32-item batch
   double* gpart;        // [Fc * E][ncubes][3] per-cube element gradients (POSE)
   int dtype_vol, dtype_sig;
   int nx, ny, nz, ncx, ncy;
   int E, f_begin, n_items, Nt;
   int WP, accumulate;   // accumulate: add into vol instead of overwriting
   double ox, oy, oz, dx, dy, dz;
-  double tau0, inv_h, a0;
-  float h, a0f, a0sq, nb_shift, scale, inv_hf, cb1;
+  double tau0, inv_h, sup;
+  float h, supf, sup2, nb_shift, scale, inv_hf, cb1;
+  float lam;            // pose-coefficient weight of the boundary term: 2 (sphere), 1 / sigma^2 (Gaussian)
+  GaussConst gs;
   int use_tma;
   unsigned* status;
 };
@@ -179,14 +198,14 @@ struct PairRef {
 };
 
 __device__ __forceinline__ PairRef make_ref(double x0, double x1, double x2, double rcx, double rcy, double rcz,
-                                            double a0, double tau0, double inv_h) {
+                                            double sup, double tau0, double inv_h) {
   PairRef r;
   r.ux = x0 - rcx;
   r.uy = x1 - rcy;
   r.uz = x2 - rcz;
   const double dc2 = r.ux * r.ux + r.uy * r.uy + r.uz * r.uz;
   const double dc = sqrt(dc2);
-  const double psi = (dc - a0 - tau0) * inv_h + 0.5;
+  const double psi = (dc - sup - tau0) * inv_h + 0.5;
   const double N = floor(psi);
   r.Nc = static_cast<int>(N);
   r.phim = static_cast<float>(psi - N) - 0.5f;

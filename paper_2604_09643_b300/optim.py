@@ -12,6 +12,12 @@ Here those pieces drive a joint optimisation over every frame:
   A coarse level has wider pulses, which smooths the loss like the paper's
   decaying kernel width.  Since (4/3) pi a0^3 / spacing^3 = pi / 6 on every level,
   the estimate carries over by trilinear resampling without rescaling.
+* Gaussian kernel (Eq. 1): each level runs one or more widths sigma, largest
+  first (the dynamic smoothing of Stage 2).  The measurements, simulated or
+  recorded at the finest width, are low-passed in time by a Gaussian of width
+  sqrt(sigma^2 - sigma_fine^2), which turns their pulses into exactly the
+  pulses of width sigma; voxel amplitudes are rescaled by (sigma_old / sigma_new)^3
+  (spacing_new / spacing_old)^3 at each change so the represented field is kept.
 * Steps: each is one ``pasfm_step``: forward, inlier-masked loss head, fused
   adjoint + pose gradient, Adam on the volume (projected to p0 >= 0) and on the
   frame twists.  Frame 0 is the gauge, held at its known pose like the paper's
@@ -142,6 +148,51 @@ class C2FConfig:
     reset_mm: float = 0.3
     n_subsets: int = 64
     seed: int = 0
+    # Gaussian kernel (Eq. 1): per-level widths (mm), each level's joint steps split evenly
+    # over its widths, widest first (the dynamic smoothing of Stage 2); None: one
+    # width per level, the data's width scaled by the level's spacing (at most SIGMA_MAX_SAMPLES sample pitches)
+    sigma_schedule: tuple | None = None
+    decimate_time: bool = True     # Gaussian kernel: coarse levels on a time grid coarser by their spacing ratio
+
+
+SIGMA_MAX_SAMPLES = 3.75  # widest Gaussian the compiled kernels take, in sample pitches (8 sigma / h <= 30)
+
+
+def gauss_widths(geom_fine, geom, cfg, li):
+    """The Gaussian widths (mm) of level `li`, largest first."""
+    if cfg.sigma_schedule is not None:
+        return tuple(float(x) for x in cfg.sigma_schedule[li])
+    h = geom["c_mm_per_us"] / geom["fs_mhz"]
+    return (min(SIGMA_MAX_SAMPLES * h, geom_fine["sigma_mm"] * geom["dx"] / geom_fine["dx"]),)
+
+
+def time_decimation(geom_fine, geom, cfg):
+    """Power-of-two factor by which a Gaussian level's time grid is coarser than the
+    data's: the level's spacing ratio rounded down (1 when disabled or for the sphere)."""
+    if not cfg.decimate_time or geom_fine.get("kernel", "sphere") != "gauss":
+        return 1
+    ratio = geom["dx"] / geom_fine["dx"]
+    k = 1
+    while 2 * k <= ratio + 1e-9:
+        k *= 2
+    return k
+
+
+def gauss_lowpass_samples(sigma_level, sigma_data, h_data, decim):
+    """Low-pass width (data samples) that turns data pulses of width sigma_data,
+    averaged over one sample, into pulses of width sigma_level averaged over
+    `decim` samples.  Variances add (a sample average over a width b adds
+    b^2 / 12), so the filter supplies sigma_level^2 + (decim h)^2 / 12 minus
+    sigma_data^2 + h^2 / 12."""
+    var = (sigma_level ** 2 - sigma_data ** 2) / h_data ** 2 + (decim ** 2 - 1) / 12.0
+    return math.sqrt(var) if var > 0 else 0.0
+
+
+def gauss_amplitude_factor(sig_old, d_old, sig_new, d_new):
+    """Rescaling of voxel amplitudes that keeps a sum of Gaussians on a grid the same
+    field when the width or the spacing changes: a voxel of amplitude p and width
+    sigma on spacing D stands for a density p (2 pi)^(3/2) sigma^3 / D^3."""
+    return (sig_old / sig_new) ** 3 * (d_new / d_old) ** 3
 
 
 def element_errors(elem, poses_a, poses_b):
@@ -223,15 +274,30 @@ def reconstruct(ctx: binding.Context, geom_fine, elem, meas, poses_init, cfg: C2
     p0, prev_geom, mask = None, None, None
     loss = torch.zeros((), dtype=torch.float64, device=dev)
     h = geom_fine["c_mm_per_us"] / geom_fine["fs_mhz"]
+    gauss = geom_fine.get("kernel", "sphere") == "gauss"
     for li, (shape, n_steps) in enumerate(zip(cfg.levels, cfg.steps)):
         geom = level_geometry(geom_fine, shape)
+        decim = time_decimation(geom_fine, geom, cfg)
+        if decim > 1:
+            geom["fs_mhz"] = geom_fine["fs_mhz"] / decim
+            geom["n_samples"] = -(-geom_fine["n_samples"] // decim)
+        widths = gauss_widths(geom_fine, geom, cfg, li) if gauss else (None,)
+        if gauss:
+            geom["sigma_mm"] = widths[0]
         if p0 is None:
             p0 = torch.full(tuple(shape), cfg.init_value, dtype=torch.float32, device=dev)
         else:
             p0 = ctx.resample(prev_geom, p0, geom)
-        sigma = (cfg.lowpass[li] if cfg.lowpass is not None
-                 else max(0.0, (geom["a0_mm"] - geom_fine["a0_mm"]) / h))
-        meas_l = ctx.lowpass(meas, sigma) if sigma > 0 else meas
+            if gauss:
+                p0 *= gauss_amplitude_factor(prev_geom["sigma_mm"], prev_geom["dx"], geom["sigma_mm"], geom["dx"])
+        if gauss:
+            # a Gaussian pulse of width s low-passed by a Gaussian of width t is one of width sqrt(s^2 + t^2)
+            sigma = (cfg.lowpass[li] if cfg.lowpass is not None
+                     else gauss_lowpass_samples(geom["sigma_mm"], geom_fine["sigma_mm"], h, decim))
+        else:
+            sigma = (cfg.lowpass[li] if cfg.lowpass is not None
+                     else max(0.0, (geom["a0_mm"] - geom_fine["a0_mm"]) / h))
+        meas_l = ctx.lowpass(meas, sigma, decim=decim) if (sigma > 0 or decim > 1) else meas
         decay = cfg.lr_decay ** li
         t0 = time.perf_counter()
         if li == 0 and cfg.reference_steps:
@@ -254,7 +320,21 @@ def reconstruct(ctx: binding.Context, geom_fine, elem, meas, poses_init, cfg: C2
                 ctx.step(geom, p0, poses, elem_d, meas_l, vadam, mask=mask, loss_out=loss)
         adam = binding.AdamState(geom, dev, lr_vol=cfg.lr_vol * decay, lr_rot=cfg.lr_rot * decay,
                                  lr_trans=cfg.lr_trans * decay, nonneg=cfg.nonneg, fix_frame0=cfg.fix_frame0)
+        phase_len = max(1, -(-n_steps // len(widths)))
         for k in range(n_steps):
+            if gauss and k > 0 and k % phase_len == 0:
+                # next, narrower width: keep the represented field, band-limit the data to match
+                w_new = widths[min(k // phase_len, len(widths) - 1)]
+                if w_new != geom["sigma_mm"]:
+                    p0 *= gauss_amplitude_factor(geom["sigma_mm"], geom["dx"], w_new, geom["dx"])
+                    geom = dict(geom, sigma_mm=w_new)
+                    lp = (gauss_lowpass_samples(w_new, geom_fine["sigma_mm"], h, decim)
+                          if cfg.lowpass is None else cfg.lowpass[li])
+                    meas_l = ctx.lowpass(meas, lp, decim=decim) if (lp > 0 or decim > 1) else meas
+                    sigma = lp
+                    adam = binding.AdamState(geom, dev, lr_vol=cfg.lr_vol * decay, lr_rot=cfg.lr_rot * decay,
+                                             lr_trans=cfg.lr_trans * decay, nonneg=cfg.nonneg,
+                                             fix_frame0=cfg.fix_frame0)
             ctx.step(geom, p0, poses, elem_d, meas_l, adam, mask=mask, loss_out=loss)
             if cfg.refine_every and (k + 1) % cfg.refine_every == 0:
                 mask, poses = rigid_consensus(ctx, geom, p0, poses, elem_d, meas_l, mask, cfg, rng)
@@ -273,6 +353,7 @@ def reconstruct(ctx: binding.Context, geom_fine, elem, meas, poses_init, cfg: C2
         torch.cuda.synchronize(dev)
         extra = (cfg.reference_steps + cfg.register_steps) if li == 0 else 0
         rec = {"level": li, "shape": list(shape), "steps": n_steps + n_vol + extra + n_search, "lowpass_sigma": sigma,
+               "kernel_sigma_mm": geom.get("sigma_mm") if gauss else None, "time_decimation": decim,
                "loss": float(loss),
                "seconds": time.perf_counter() - t0}
         if truth_poses is not None:

@@ -75,3 +75,11 @@ def pose_residual(geom, p0, elem, poses, seed=5, rot_deg=0.5, trans_mm=0.05):
     a = oracle.forward(geom, p0, oracle.element_positions(geom, elem, poses))
     b = oracle.forward(geom, p0, oracle.element_positions(geom, elem, pert))
     return (a - b).astype(np.float32)
+
+
+def gaussian(case, sigma):
+    """The same inputs with the Gaussian kernel of width ``sigma`` (mm) instead of the sphere."""
+    def make(*a, **kw):
+        geom, p0, elem, poses = case(*a, **kw)
+        return dict(geom, kernel="gauss", sigma_mm=float(sigma)), p0, elem, poses
+    return make

@@ -42,7 +42,7 @@ def test_binding_covers_every_declared_symbol():
 
 
 def test_abi_version():
-    assert binding.lib().pasfm_abi_version() == 1
+    assert binding.lib().pasfm_abi_version() == 2
 
 
 def _geom(**kw):

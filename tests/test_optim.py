@@ -1,6 +1,7 @@
 """Host-side pieces of the coarse-to-fine optimiser (CPU): pyramid geometry and the
 Stage 3 rigid consensus against the oracle's independent Kabsch / RANSAC."""
 import numpy as np
+import pytest
 
 from oracle import rigid
 from paper_2604_09643_b300 import optim, synth
@@ -52,3 +53,42 @@ def test_element_errors():
     moved = poses.copy()
     moved[:, 0, 3] += 0.1
     assert abs(optim.element_errors(elem, poses, moved) - 0.1) < 1e-12
+
+
+@pytest.mark.parametrize("d_coarse,decim,tol", [(0.2, 1, 2e-3), (0.2, 2, 2e-3), (0.4, 4, 1e-2)])
+def test_gauss_level_transfer_keeps_the_signals(d_coarse, decim, tol):
+    """A smooth source on a 0.1 mm grid of sigma = 0.08 mm Gaussians, its traces
+    low-passed and decimated as the coarse-to-fine optimiser does, against the
+    same source on a coarser grid (sigma scaled with the spacing, amplitudes
+    rescaled, time grid decimated), both through the FP64 oracle."""
+    import scipy.ndimage
+
+    import oracle
+
+    h = 1.5 / 40.0
+
+    def traces(spacing, sigma, fs, nt):
+        n = int(round(3.6 / spacing)) + 1
+        geom = synth.make_geom((n, n, n), spacing, 1, 1, nt, kernel="gauss", sigma=sigma, fs=fs)
+        geom["t0_us"] = 6.0 / 1.5
+        x, y, z = synth.voxel_axes(geom)
+        zz, yy, xx = np.meshgrid(z, y, x, indexing="ij")
+        f = np.exp(-(xx ** 2 + yy ** 2 + zz ** 2) / (2 * 0.4 ** 2)).astype(np.float32)
+        return oracle.forward(geom, f, np.array([[[0.7, -0.4, 10.0]]]))[0, 0]
+
+    s_fine, s_coarse = 0.08, 0.08 * d_coarse / 0.1
+    fine = traces(0.1, s_fine, 40.0, 400)
+    coarse = traces(d_coarse, s_coarse, 40.0 / decim, -(-400 // decim))
+    lp = optim.gauss_lowpass_samples(s_coarse, s_fine, h, decim)
+    fine_lp = scipy.ndimage.gaussian_filter1d(fine, lp, mode="constant", truncate=6.0)[::decim]
+    fac = optim.gauss_amplitude_factor(s_fine, 0.1, s_coarse, d_coarse)
+    assert np.linalg.norm(fine_lp - fac * coarse) / np.linalg.norm(fine_lp) < tol
+
+
+def test_time_decimation_factor():
+    fine = synth.make_geom((64, 64, 64), 0.1, 4, 1, 100, kernel="gauss", sigma=0.05)
+    cfg = optim.C2FConfig()
+    for n, k in ((64, 1), (32, 2), (16, 4), (21, 2)):
+        assert optim.time_decimation(fine, optim.level_geometry(fine, (n, n, n)), cfg) == k
+    assert optim.time_decimation(synth.make_geom((64, 64, 64), 0.1, 4, 1, 100),
+                                 optim.level_geometry(fine, (16, 16, 16)), cfg) == 1

@@ -19,8 +19,8 @@ import torch
 
 import oracle
 from paper_2604_09643_b300 import binding, synth
-from tests.parity_cases import (REL_L2_POSE, REL_L2_SIG, coarse_case, pose_residual, ragged_case, rel_l2,
-                                residual, tma_case)
+from tests.parity_cases import (REL_L2_POSE, REL_L2_SIG, coarse_case, gaussian, pose_residual, ragged_case,
+                                rel_l2, residual, tma_case)
 
 pytestmark = pytest.mark.gpu
 
@@ -38,6 +38,12 @@ CASES = {
     "ragged_cut": lambda: ragged_case(cut=True),
     "tma": tma_case,
     "coarse": coarse_case,
+    # Gaussian kernel (Eq. 1): slot counts S = floor(8 sigma / h) + 2 of 19, 8, 8, 12 and 32 (the largest compiled)
+    "gauss_single_frame": gaussian(single_frame_case, 0.08),
+    "gauss_ragged": gaussian(ragged_case, 0.03),
+    "gauss_ragged_cut": lambda: gaussian(ragged_case, 0.03)(cut=True),
+    "gauss_tma": gaussian(tma_case, 0.05),
+    "gauss_coarse_s32": gaussian(coarse_case, 0.141),
 }
 
 
@@ -106,7 +112,7 @@ def test_pose_grad(ctx, case, masked):
                                None if mask is None else dev(mask), want_elem=True)
     got6, gotG = got6.cpu().numpy(), gotG.cpu().numpy()
     assert_status_ok(ctx)
-    if name == "ragged_cut":
+    if name.endswith("ragged_cut"):
         gm = g if mask is None else g * mask[:, :, None]
         mid, half = oracle.element_gradient_bounds(geom, p0, gm, xw, np.arange(F * E), EPS_KINK)
         _band_check(gotG.reshape(-1, 3), got6, mid, half,
@@ -291,6 +297,16 @@ def test_unsupported_sphere_radius_is_rejected(ctx):
     with pytest.raises(binding.PasfmError) as e:
         ctx.forward(dict(geom, a0_mm=0.5), dev(p0), dev(elem), dev(poses))
     assert e.value.code == -6
+
+
+def test_gaussian_width_limits(ctx):
+    geom, p0, elem, poses = single_frame_case()
+    with pytest.raises(binding.PasfmError) as e:   # 8 sigma / h = 42.7: a pair spans 44 samples
+        ctx.forward(dict(geom, kernel="gauss", sigma_mm=0.2), dev(p0), dev(elem), dev(poses))
+    assert e.value.code == -6
+    with pytest.raises(binding.PasfmError) as e:
+        ctx.forward(dict(geom, kernel="gauss", sigma_mm=0.0), dev(p0), dev(elem), dev(poses))
+    assert e.value.code == -1
 
 
 # ----------------------------------------------------------------------------- full-size workload, sampled
