@@ -76,11 +76,11 @@ def peaks():
                 source="measured" if p else "fallback")
 
 
-HOT_SOURCES = ("kernels.cuh", "pasfm_dev.cuh", "kernels_s.cu")
+HOT_SOURCES = ("kernels.cuh", "pasfm_dev.cuh", "kernels_s.cu", "aux.cu")
 
 
 def kernel_src_hash():
-    """Hash of the sources that define the hot kernels (bwd_cube, fwd_cube)."""
+    """Hash of the sources that define the measured kernels (bwd_cube, fwd_cube, fwd_reduce)."""
     h = hashlib.sha256()
     for fn in HOT_SOURCES:
         with open(os.path.join(ROOT, "paper_2604_09643_b300", "csrc", fn), "rb") as fh:
@@ -374,6 +374,13 @@ def run_native(args):
                                    f"({pk['source']} clock)",
                     "flops_per_pair": fpp, "pairs_per_launch": pairs / launches_per_step}
     step_flops = pairs * (f_fwd(m) + f_adj(m) + f_pose(m))
+    # achieved DRAM bandwidth of the kernels whose per-launch traffic ncu measured on these sources
+    hbm = {}
+    for name in ("fwd_cube", "bwd_cube", "fwd_reduce"):
+        tb = traffic_for(name + ("_gauss" if gauss else ""))
+        if tb and name in per_kernel:
+            gbs = tb / (per_kernel[name]["ms_avg"] * 1e-3) / 1e9
+            hbm[name] = {"traffic_bytes": tb, "gbs": gbs, "frac": gbs / pk["hbm_gbs"]}
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
@@ -392,6 +399,7 @@ def run_native(args):
         "step_tflops": step_flops * value / world / 1e12,
         "fp32_frac_step": step_flops * value / world / 1e12 / pk["fp32_tflops"],
         "roofline": roofline,
+        "hbm": {"peak_gbs": pk["hbm_gbs"], "peak_source": pk["source"], "kernels": hbm},
         "per_kernel_ms": {k: round(v["ms_avg"], 4) for k, v in per_kernel.items()},
         "clocks": clocks,
         "gpu_launches": launches,
@@ -443,6 +451,8 @@ def run_serving(args):
         torch.cuda.synchronize()
     rep = srv.report()
     pairs = sum(sp["n"] ** 3 * sp["m"] ** 2 * sp["n_frames"] for sp in specs) * args.serve_steps
+    span = max(sp["arrival_s"] for sp in specs) or 1.0
+    offered = len(specs) * args.serve_steps / span  # steps/s asked for while the requests arrive
     out = {"metric": METRIC, "value": rep["steps_per_s"], "unit": UNIT, "n_gpus": 1, "steps": rep["steps"],
            "warmup": max(args.warmup, 3), "ms_per_step": 1e3 / rep["steps_per_s"] if rep["steps_per_s"] else None,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
@@ -450,12 +460,69 @@ def run_serving(args):
            "config": {"workload": WORKLOAD_SERVING, "requests": len(specs), "steps_per_request": args.serve_steps,
                       "arrivals": "seeded Poisson stream, mean 4 scans/s, first requests in arrival order",
                       "l2": "inputs larger than L2 (each scan's measurements 64 MiB-2.4 GiB)"},
+           "offered_steps_per_s": offered, "arrival_span_s": span,
            "step_ms_p50": rep["step_ms_p50"], "step_ms_p99": rep["step_ms_p99"],
            "queue_wait_s_p50": rep["queue_wait_s_p50"], "queue_wait_s_p99": rep["queue_wait_s_p99"],
            "completed": rep["completed"], "rejected": rep["rejected"], "failed": rep["failed"],
            "wall_s": rep["wall_s"], "pairs_per_s": pairs / rep["wall_s"] if rep["wall_s"] else None,
            "clocks": clk.summary(), "gpu_launches": rep["gpu_launches"],
            "e2e": None, "e2e_note": "measurements are simulated on the device before the stream starts"}
+    print(json.dumps(out))
+    return 0
+
+
+# ----------------------------------------------------------------------------- joint reconstruction
+
+WORKLOAD_RECON = "reconstruction_256^3_0.1mm_vessel150_16x16_0.6mm_200f_2048s_c2f_64-128-256"
+
+
+def run_reconstruction(args):
+    """Coarse-to-fine joint reconstruction of volume and poses on the 256^3, 200-frame
+    scan whose initial poses carry N(0, 1.5 deg) rotation and N(0, 0.5 mm) translation
+    noise per axis (frame 0 exact): levels 64^3 -> 128^3 -> 256^3, joint Adam steps on
+    each, one Stage 2 translation search on the coarsest level.  Reports the steps/s
+    over the whole schedule and the mean element error after each level."""
+    import torch
+
+    from paper_2604_09643_b300 import binding, optim, synth
+
+    torch.cuda.set_device(0)
+    scan = synth.reconstruction_scan()
+    geom = scan.geom
+    steps = tuple(int(x) for x in args.recon_steps.split(","))
+    with binding.Context(0) as ctx:
+        dev = ctx.device
+        meas = ctx.forward(geom, torch.as_tensor(scan.p0).to(dev), torch.as_tensor(scan.elem).to(dev),
+                           torch.as_tensor(scan.poses).to(dev))
+        cfg = optim.C2FConfig(levels=((64, 64, 64), (128, 128, 128), (256, 256, 256)), steps=steps,
+                              lr_vol=0.02, lr_rot=1e-3, lr_trans=1e-2, lr_decay=0.5,
+                              search_rounds=args.recon_search, search_radius_mm=1.2, search_step_mm=0.15,
+                              search_joint_steps=steps[0])
+        torch.cuda.synchronize()
+        l0 = ctx.launch_count()
+        with ClockSampler(0) as clk:
+            t0 = time.perf_counter()
+            p0, poses, hist = optim.reconstruct(ctx, geom, scan.elem, meas, scan.poses_init, cfg,
+                                                truth_poses=scan.poses)
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - t0
+        launches = ctx.launch_count() - l0
+        rc, bits = ctx.status()
+        if rc != 0:
+            raise RuntimeError(f"device status {bits:#x}")
+        vol_err = float(np.linalg.norm(p0.cpu().numpy() - scan.p0) / np.linalg.norm(scan.p0))
+    n_steps = sum(h["steps"] for h in hist)
+    out = {"metric": METRIC, "value": n_steps / wall, "unit": UNIT, "n_gpus": 1, "steps": n_steps, "warmup": 0,
+           "ms_per_step": 1e3 * wall / n_steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32", "data": "synthetic",
+           "config": {"workload": WORKLOAD_RECON, "levels": [list(l) for l in cfg.levels], "steps": list(steps),
+                      "search_rounds": args.recon_search,
+                      "note": "mixed-level steps/s over the whole schedule, incl. the search; not a bench line"},
+           "initial_mean_element_error_mm": optim.element_errors(scan.elem, scan.poses_init, scan.poses),
+           "levels": [{k: h[k] for k in ("level", "shape", "steps", "seconds", "mean_element_error_mm",
+                                          "lowpass_sigma", "loss")} for h in hist],
+           "final_mean_element_error_mm": hist[-1]["mean_element_error_mm"],
+           "volume_rel_l2_error": vol_err, "wall_s": wall, "clocks": clk.summary(), "gpu_launches": launches}
     print(json.dumps(out))
     return 0
 
@@ -469,9 +536,13 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--frames", type=int, default=0,
                     help="override the frame count (only for small ncu captures; not a bench line)")
-    ap.add_argument("--workload", choices=["full_scan", "mixed_precision", "serving"], default="full_scan",
+    ap.add_argument("--workload", choices=["full_scan", "mixed_precision", "serving", "reconstruction"],
+                    default="full_scan",
                     help="full_scan: the benchmark; mixed_precision: 256x256x128, 32x32 elements, 400 frames; "
-                         "serving: continuous batching over the seeded request stream")
+                         "serving: continuous batching over the seeded request stream; reconstruction: "
+                         "coarse-to-fine joint volume + pose recovery on 256^3 with 200 frames")
+    ap.add_argument("--recon-steps", default="100,100,100", help="reconstruction: joint steps per level")
+    ap.add_argument("--recon-search", type=int, default=1, help="reconstruction: Stage 2 search rounds")
     ap.add_argument("--kernel", choices=["sphere", "gauss"], default="sphere",
                     help="voxel pulse: uniform sphere (a0 = spacing / 2) or the Gaussian of Eq. 1")
     ap.add_argument("--sigma", type=float, default=0.05, help="Gaussian width (mm) for --kernel gauss")
@@ -484,6 +555,8 @@ def main():
         return run_reference(args)
     if args.workload == "serving":
         return run_serving(args)
+    if args.workload == "reconstruction":
+        return run_reconstruction(args)
     return run_native(args)
 
 

@@ -28,6 +28,7 @@ import math
 
 import numpy as np
 from scipy import ndimage
+from scipy.spatial import cKDTree
 
 SEED_PHANTOM, SEED_TRAJ, SEED_NOISE, SEED_STREAM = 0, 1, 2, 3
 
@@ -166,18 +167,15 @@ def vessel_tree_phantom(geom, n_tubes, rng, radius=(0.05, 0.4), amp=(0.5, 1.0),
                         axis=-1).reshape(-1, 3)
         base = np.rint((pts - o) / d).astype(int)
         cand = (base[:, None, :] + offs[None, :, :]).reshape(-1, 3)
-        cand = np.unique(cand, axis=0)
-        ok = np.all((cand >= 0) & (cand < dims), axis=1)
-        cand = cand[ok]
+        cand = cand[np.all((cand >= 0) & (cand < dims), axis=1)]
+        # unique voxels, in (x, y, z) lexicographic order
+        lin = np.unique((cand[:, 0] * dims[1] + cand[:, 1]) * dims[2] + cand[:, 2])
+        cand = np.stack([lin // (dims[1] * dims[2]), (lin // dims[2]) % dims[1], lin % dims[2]], axis=1)
         if cand.size == 0:
             continue
         centres = o + cand * d
-        # distance from each candidate voxel centre to the sampled curve
-        best = np.full(len(cand), np.inf)
-        for k0 in range(0, len(pts), 256):
-            seg = pts[k0:k0 + 256]
-            dd = np.linalg.norm(centres[:, None, :] - seg[None, :, :], axis=-1).min(axis=1)
-            best = np.minimum(best, dd)
+        # distance from each candidate voxel centre to the nearest sampled curve point
+        best, _ = cKDTree(pts).query(centres, k=1)
         sel = cand[best <= r]
         cur = out[sel[:, 2], sel[:, 1], sel[:, 0]]
         out[sel[:, 2], sel[:, 1], sel[:, 0]] = np.maximum(cur, a)

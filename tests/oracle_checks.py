@@ -350,6 +350,33 @@ def check_pose_fd(seed=9, eps=1e-6, use_mask=False, sigma=None):
     return errs[0], errs[1], ge
 
 
+def check_p0_gradient_fd(seed=14, sigma=None) -> float:
+    """The volume gradient of L = 1/2 |A p0 - S|^2 is A^T (A p0 - S): central
+    differences of L in single voxels (exact for a quadratic up to rounding)
+    against the oracle adjoint of the residual."""
+    geom, elem, poses = small_geom(shape=(4, 5, 5), spacing=0.25, m=2, n_frames=2, n_samples=256, sigma=sigma)
+    rng = np.random.default_rng(seed)
+    p0 = rng.uniform(0.2, 1, size=(4, 5, 5))
+    meas = 0.02 * rng.standard_normal((2, 4, 256))
+    xw = oracle.element_positions(geom, elem, poses)
+    _, g = oracle.loss(geom, oracle.forward(geom, p0.astype(np.float32), xw), meas)
+    grad = oracle.adjoint(geom, g, xw)
+    worst = 0.0
+    eps = 1e-3
+    for _ in range(8):
+        i = tuple(int(rng.integers(0, n)) for n in p0.shape)
+        pp, pm = p0.copy(), p0.copy()
+        # steps exactly representable around float32 voxel values
+        pp[i] = np.float32(p0[i]) + eps
+        pm[i] = np.float32(p0[i]) - eps
+        lp = 0.5 * math.fsum(((oracle.forward(geom, pp.astype(np.float32), xw) - meas) ** 2).ravel())
+        lm = 0.5 * math.fsum(((oracle.forward(geom, pm.astype(np.float32), xw) - meas) ** 2).ravel())
+        dp = float(np.float32(pp[i])) - float(np.float32(pm[i]))
+        fd = (lp - lm) / dp
+        worst = max(worst, abs(fd - grad[i]) / np.abs(grad).max())
+    return worst
+
+
 def check_big_ball(spacing=0.1, radius=1.0, dist=10.0):
     """Returns (ratio of projections, low-passed relative L2) of a voxelised ball
     against pi/6 times the ball's closed-form pulse (quadrature)."""

@@ -47,6 +47,11 @@ def test_pose_gradient_fd_masked():
     assert rot < 1e-6 and trans < 1e-6 and elem < 1e-6, (rot, trans, elem)
 
 
+@pytest.mark.parametrize("sigma", [None, 0.06])
+def test_volume_gradient_fd(sigma):
+    assert oc.check_p0_gradient_fd(sigma=sigma) < 1e-9
+
+
 # ---- Gaussian kernel (Eq. 1, Appendix A Eq. gaussian_far_field)
 
 def test_gauss_pulse_solves_the_wave_equation():
