@@ -408,3 +408,85 @@ def check_loss(seed=10) -> float:
     ref_g = (s - S) * mask[:, :, None]
     ref_L = 0.5 * math.fsum((ref_g ** 2).ravel())
     return max(abs(L - ref_L) / ref_L, float(np.abs(g - ref_g).max()))
+
+
+# ----------------------------------------------------------------------------- TGV regulariser
+
+def _tgv_sparse(u, w, spacing, alpha1, alpha0, eps):
+    """The same energy and gradients from explicit sparse difference matrices
+    (Kronecker products of 1-D forward-difference matrices) and their transposes."""
+    import scipy.sparse as sp
+
+    nz, ny, nx = u.shape
+
+    def d1(n, h):
+        m = sp.lil_matrix((n, n))
+        for i in range(n - 1):
+            m[i, i], m[i, i + 1] = -1.0 / h, 1.0 / h
+        return m.tocsr()
+
+    I = lambda n: sp.identity(n, format="csr")
+    D = [sp.kron(I(nz), sp.kron(I(ny), d1(nx, spacing[0]))),
+         sp.kron(I(nz), sp.kron(d1(ny, spacing[1]), I(nx))),
+         sp.kron(d1(nz, spacing[2]), sp.kron(I(ny), I(nx)))]
+    uf = u.ravel().astype(np.float64)
+    wf = [w[b].ravel().astype(np.float64) for b in range(3)]
+    r = [D[a] @ uf - wf[a] for a in range(3)]
+    phi1 = np.sqrt(sum(x * x for x in r) + eps * eps)
+    E = [[0.5 * (D[a] @ wf[b] + D[b] @ wf[a]) for b in range(3)] for a in range(3)]
+    phi2 = np.sqrt(sum(E[a][b] ** 2 for a in range(3) for b in range(3)) + eps * eps)
+    J = alpha1 * phi1.sum() + alpha0 * phi2.sum()
+    gu = sum(D[a].T @ (alpha1 * r[a] / phi1) for a in range(3))
+    gw = [-(alpha1 * r[b] / phi1) + sum(D[a].T @ (alpha0 * E[a][b] / phi2) for a in range(3)) for b in range(3)]
+    return J, gu.reshape(u.shape), np.stack([g.reshape(u.shape) for g in gw])
+
+
+def _tgv_case(seed=30, shape=(4, 5, 6)):
+    rng = np.random.default_rng(seed)
+    u = rng.uniform(0, 1, size=shape)
+    w = rng.normal(0, 2.0, size=(3,) + shape)
+    return u, w, (0.1, 0.12, 0.15), 0.7, 0.4, 0.05
+
+
+def check_tgv_sparse(seed=30) -> float:
+    """Max relative gap between the oracle and the sparse-matrix formulation."""
+    from oracle import tgv
+    u, w, sp_, a1, a0, eps = _tgv_case(seed)
+    J, gu, gw = tgv.energy_and_grad(u, w, sp_, a1, a0, eps)
+    J2, gu2, gw2 = _tgv_sparse(u, w, sp_, a1, a0, eps)
+    return max(abs(J - J2) / abs(J2), float(np.abs(gu - gu2).max() / np.abs(gu2).max()),
+               float(np.abs(gw - gw2).max() / np.abs(gw2).max()))
+
+
+def check_tgv_fd(seed=31, h=1e-6) -> float:
+    """Central differences of J in random entries of u and w against the gradients."""
+    from oracle import tgv
+    u, w, sp_, a1, a0, eps = _tgv_case(seed)
+    _, gu, gw = tgv.energy_and_grad(u, w, sp_, a1, a0, eps)
+    rng = np.random.default_rng(seed + 1)
+    worst = 0.0
+    scale = max(np.abs(gu).max(), np.abs(gw).max())
+    for _ in range(12):
+        i = tuple(int(rng.integers(0, n)) for n in u.shape)
+        up, um = u.copy(), u.copy()
+        up[i] += h
+        um[i] -= h
+        fd = (tgv.energy_and_grad(up, w, sp_, a1, a0, eps)[0] - tgv.energy_and_grad(um, w, sp_, a1, a0, eps)[0]) / (2 * h)
+        worst = max(worst, abs(fd - gu[i]) / scale)
+        b = int(rng.integers(0, 3))
+        wp, wm = w.copy(), w.copy()
+        wp[(b,) + i] += h
+        wm[(b,) + i] -= h
+        fd = (tgv.energy_and_grad(u, wp, sp_, a1, a0, eps)[0] - tgv.energy_and_grad(u, wm, sp_, a1, a0, eps)[0]) / (2 * h)
+        worst = max(worst, abs(fd - gw[(b,) + i]) / scale)
+    return worst
+
+
+def check_tgv_constant() -> float:
+    """A constant field with w = 0 has only the smoothing floor: J = N (alpha1 + alpha0) eps,
+    zero gradients."""
+    from oracle import tgv
+    u = np.full((3, 4, 5), 0.7)
+    w = np.zeros((3, 3, 4, 5))
+    J, gu, gw = tgv.energy_and_grad(u, w, (0.1, 0.1, 0.1), 0.7, 0.4, 0.05)
+    return max(abs(J - 60 * 1.1 * 0.05) / (60 * 1.1 * 0.05), float(np.abs(gu).max()), float(np.abs(gw).max()))

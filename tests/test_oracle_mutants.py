@@ -93,3 +93,34 @@ def test_mutant_is_caught(name, tmp_path, monkeypatch):
     monkeypatch.setattr(oracle, "_lib", oracle.load(str(so)))
     fails = failing_pins()
     assert fails, f"mutant {name} passed every pin"
+
+
+# ----------------------------------------------------------------------------- TGV oracle (Python)
+
+TGV_MUTANTS = {
+    "transpose_sign": ("out[tuple(dst)] += y[tuple(src)]", "out[tuple(dst)] -= y[tuple(src)]"),
+    "sym_gradient_drops_half": ("E[a, b] = 0.5 * (Dw[a][b] + Dw[b][a])", "E[a, b] = (Dw[a][b] + Dw[b][a])"),
+    "w_gradient_drops_q": ("[-q[b] + sum(", "[sum("),
+    "difference_not_scaled": ("out[tuple(lo)] = (v[tuple(hi)] - v[tuple(lo)]) / d",
+                              "out[tuple(lo)] = (v[tuple(hi)] - v[tuple(lo)])"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(TGV_MUTANTS))
+def test_tgv_mutant_is_caught(name, monkeypatch):
+    import importlib.util
+    import sys
+
+    import oracle.tgv as tgv_mod
+
+    old, new = TGV_MUTANTS[name]
+    src = open(tgv_mod.__file__).read()
+    assert src.count(old) == 1, f"mutation anchor for {name} not found"
+    spec = importlib.util.spec_from_loader("oracle.tgv", loader=None)
+    mod = importlib.util.module_from_spec(spec)
+    exec(compile(src.replace(old, new), tgv_mod.__file__, "exec"), mod.__dict__)
+    monkeypatch.setitem(sys.modules, "oracle.tgv", mod)
+    monkeypatch.setattr(oracle, "tgv", mod, raising=False)
+    fails = [n for n, bad in (("sparse", oc.check_tgv_sparse() > 1e-12), ("fd", oc.check_tgv_fd() > 1e-7),
+                               ("constant", oc.check_tgv_constant() > 1e-14)) if bad]
+    assert fails, f"TGV mutant {name} passed every pin"

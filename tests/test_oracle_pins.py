@@ -205,3 +205,18 @@ def test_nc_loss_invariances():
     assert abs(ncmod.nc(3.0 * a + 2.0, b - 5.0) - ncmod.nc(a, b)) < 1e-14
     assert abs(ncmod.nc(a, b) + np.corrcoef(a, b)[0, 1]) < 1e-14
     assert ncmod.nc(np.ones(10), a[:10]) == 0.0
+
+
+
+# ---- TGV regulariser (Stages 1 and 5, Eq. 2)
+
+def test_tgv_matches_sparse_matrix_formulation():
+    assert oc.check_tgv_sparse() < 1e-12
+
+
+def test_tgv_gradient_fd():
+    assert oc.check_tgv_fd() < 1e-7
+
+
+def test_tgv_constant_field():
+    assert oc.check_tgv_constant() < 1e-14
