@@ -76,7 +76,7 @@ def peaks():
                 source="measured" if p else "fallback")
 
 
-HOT_SOURCES = ("kernels.cuh", "pasfm_dev.cuh", "kernels_s.cu", "aux.cu")
+HOT_SOURCES = ("kernels.cuh", "pasfm_dev.cuh", "kernels_s.cu", "aux.cu", "tgv.cu")
 
 
 def kernel_src_hash():
@@ -471,6 +471,73 @@ def run_serving(args):
     return 0
 
 
+# ----------------------------------------------------------------------------- TGV regulariser
+
+WORKLOAD_TGV = "tgv_256^3_0.1mm"
+TGV_BYTES_PER_VOXEL = 36  # read u 4 + w 12, read-modify-write grad_u 8, write grad_w 12
+
+
+def run_tgv(args):
+    """HBM roofline of the TGV regulariser kernel on a 256^3 volume (u, w, gradients:
+    604 MiB, larger than L2): K timed launches of pasfm_tgv_grad accumulating into the
+    volume gradient as pasfm_step_tgv does."""
+    import torch
+
+    from paper_2604_09643_b300 import binding
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    n = 256
+    geom = {"nx": n, "ny": n, "nz": n, "dx": 0.1, "dy": 0.1, "dz": 0.1, "ox": 0.0, "oy": 0.0, "oz": 0.0,
+            "n_elem": 1, "n_frames": 1, "n_samples": 1, "fs_mhz": 40.0, "t0_us": 0.0, "c_mm_per_us": 1.5,
+            "a0_mm": 0.05}
+    gen = torch.Generator(device=dev).manual_seed(0)
+    u = torch.rand((n, n, n), device=dev, generator=gen)
+    w = torch.randn((3, n, n, n), device=dev, generator=gen)
+    gu = torch.zeros((n, n, n), device=dev)
+    gw = torch.empty((3, n, n, n), device=dev)
+    e = torch.zeros((), dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    with binding.Context(0) as ctx:
+        def launch():
+            binding.pasfm_tgv_grad(ctx.handle, geom, u, w, 0.8, 0.3, 0.05, gu, 1, gw, e)
+        for _ in range(max(args.warmup, 3)):
+            launch()
+        torch.cuda.synchronize()
+        ctx.timing(True)
+        ctx.timing_reset()
+        l0 = ctx.launch_count()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(0) as clk:
+            ev0.record(stream)
+            for _ in range(args.steps):
+                launch()
+            ev1.record(stream)
+            torch.cuda.synchronize()
+        t_k, n_k = ctx.timing_read("tgv")
+        launches = ctx.launch_count() - l0
+        ctx.timing(False)
+        rc, bits = ctx.status()
+        if rc != 0:
+            raise RuntimeError(f"device status {bits:#x}")
+    ms = ev0.elapsed_time(ev1) / args.steps
+    pk = peaks()
+    nvox = n ** 3
+    achieved = TGV_BYTES_PER_VOXEL * nvox / (t_k / n_k * 1e-3) / 1e9
+    out = {"metric": "TGV voxels/s", "value": nvox / (ms * 1e-3), "unit": "voxels/s", "n_gpus": 1,
+           "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": WORKLOAD_TGV, "note": "regulariser kernel alone; not the bench line",
+                      "l2": "inputs larger than L2 (604 MiB touched per launch)"},
+           "roofline": {"bound": "hbm", "kernel": "tgv", "achieved": achieved, "peak": pk["hbm_gbs"],
+                        "unit": "GB/s", "frac": achieved / pk["hbm_gbs"],
+                        "traffic": traffic_for("tgv"), "bytes_per_voxel": TGV_BYTES_PER_VOXEL,
+                        "peak_source": pk["source"]},
+           "clocks": clk.summary(), "gpu_launches": launches}
+    print(json.dumps(out))
+    return 0
+
+
 # ----------------------------------------------------------------------------- joint reconstruction
 
 WORKLOAD_RECON = "reconstruction_256^3_0.1mm_vessel150_16x16_0.6mm_200f_2048s_c2f_64-128-256"
@@ -536,7 +603,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--frames", type=int, default=0,
                     help="override the frame count (only for small ncu captures; not a bench line)")
-    ap.add_argument("--workload", choices=["full_scan", "mixed_precision", "serving", "reconstruction"],
+    ap.add_argument("--workload", choices=["full_scan", "mixed_precision", "serving", "reconstruction", "tgv"],
                     default="full_scan",
                     help="full_scan: the benchmark; mixed_precision: 256x256x128, 32x32 elements, 400 frames; "
                          "serving: continuous batching over the seeded request stream; reconstruction: "
@@ -557,6 +624,8 @@ def main():
         return run_serving(args)
     if args.workload == "reconstruction":
         return run_reconstruction(args)
+    if args.workload == "tgv":
+        return run_tgv(args)
     return run_native(args)
 
 

@@ -182,6 +182,41 @@ int pasfm_step(pasfm_ctx* ctx, const pasfm_geom* geom, void* p0, double* pose, c
                const void* meas, const uint8_t* mask, pasfm_adam* state, double* loss_out,
                void* stream);
 
+/* F3 -- smoothed second-order total generalized variation of the volume, the
+ * regulariser of Stages 1 and 5 (Eq. 2, lambda L_TGV; lambda folded into the
+ * weights):
+ *   J(u, w) = sum_i alpha1 sqrt(|D u - w|^2 + eps^2) + alpha0 sqrt(|E(w)|_F^2 + eps^2),
+ *   E(w)_ab = (D_a w_b + D_b w_a) / 2,
+ * D_a the forward difference along axis a divided by the spacing, zero on the
+ * last index; w = (w_x, w_y, w_z) an auxiliary vector field optimised with u.
+ * u = p0 [nz][ny][nx] of dtype_vol; w, grad_w: float [3][nz][ny][nx];
+ * grad_u: float [nz][ny][nx], dJ/du is added to it when accumulate != 0, else
+ * written; grad_w receives dJ/dw; energy_out: one device double, or NULL.
+ * alpha1, alpha0 >= 0, eps > 0 (units of u per mm). */
+int pasfm_tgv_grad(pasfm_ctx* ctx, const pasfm_geom* geom, const void* p0, const float* w, double alpha1,
+                   double alpha0, double eps, float* grad_u, int accumulate, float* grad_w, double* energy_out,
+                   void* stream);
+
+/* TGV state for pasfm_step_tgv: the auxiliary field and its Adam moments
+ * (caller-owned device memory, [3][nz][ny][nx] floats each, moments zero before
+ * the first step), the weights and the learning rate of w. */
+typedef struct pasfm_tgv {
+  float* w;
+  float* m_w;
+  float* v_w;
+  double alpha1, alpha0, eps;
+  double lr_w;
+} pasfm_tgv;
+
+/* pasfm_step with the TGV term added to the objective (Stages 1 and 5):
+ * L + J(p0, w).  The TGV gradient is added to the volume gradient before the
+ * Adam update of p0; w takes its own Adam step (same betas, eps and step count
+ * as `state`).  tgv NULL is pasfm_step.  tgv_out: device double receiving J at
+ * the pre-update point, or NULL.  Needs p0 updates (no PASFM_ADAM_FREEZE_VOLUME). */
+int pasfm_step_tgv(pasfm_ctx* ctx, const pasfm_geom* geom, void* p0, double* pose, const double* elem,
+                   const void* meas, const uint8_t* mask, pasfm_adam* state, const pasfm_tgv* tgv,
+                   double* loss_out, double* tgv_out, void* stream);
+
 /* A7 support -- twist coordinates for autograd (Stage 4 rigid parameters read
  * as an se(3) left twist xi = (w, v) on top of a base pose).
  * pasfm_apply_twists: pose_out[f] = (Exp(w_f) R_f, Exp(w_f) t_f + v_f).

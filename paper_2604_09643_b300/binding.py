@@ -55,6 +55,12 @@ class PasfmAdam(ctypes.Structure):
                 ("flags", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
 
+class PasfmTgv(ctypes.Structure):
+    _fields_ = [("w", ctypes.c_void_p), ("m_w", ctypes.c_void_p), ("v_w", ctypes.c_void_p),
+                ("alpha1", ctypes.c_double), ("alpha0", ctypes.c_double), ("eps", ctypes.c_double),
+                ("lr_w", ctypes.c_double)]
+
+
 _lib = None
 _VP, _I, _SZ = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t
 _G = ctypes.POINTER(PasfmGeom)
@@ -70,6 +76,10 @@ _SIGS = {
     "pasfm_pose_grad": ([_VP, _G, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP], _I),
     "pasfm_loss": ([_VP, _G, _VP, _VP, _VP, _VP, _VP, _VP], _I),
     "pasfm_step": ([_VP, _G, _VP, _VP, _VP, _VP, _VP, ctypes.POINTER(PasfmAdam), _VP, _VP], _I),
+    "pasfm_tgv_grad": ([_VP, _G, _VP, _VP, ctypes.c_double, ctypes.c_double, ctypes.c_double, _VP, _I, _VP, _VP,
+                        _VP], _I),
+    "pasfm_step_tgv": ([_VP, _G, _VP, _VP, _VP, _VP, _VP, ctypes.POINTER(PasfmAdam), ctypes.POINTER(PasfmTgv),
+                        _VP, _VP, _VP], _I),
     "pasfm_apply_twists": ([_VP, _I, _VP, _VP, _VP, _VP], _I),
     "pasfm_twist_grad": ([_VP, _I, _VP, _VP, _VP, _VP], _I),
     "pasfm_resample": ([_VP, _G, _VP, _G, _VP, _VP], _I),
@@ -198,6 +208,28 @@ def pasfm_step(ctx, geom, p0, pose, elem, meas, mask, adam: PasfmAdam, loss_out=
                             _stream(stream, p0.device)))
 
 
+def pasfm_tgv_grad(ctx, geom, p0, w, alpha1, alpha0, eps, grad_u, accumulate, grad_w, energy_out=None,
+                   stream=None):
+    g = make_geom(geom, dtype_vol=p0.dtype)
+    _check(lib().pasfm_tgv_grad(ctx, ctypes.byref(g), _ptr(p0, _VOL, "p0"), _ptr(w, torch.float32, "w"),
+                                float(alpha1), float(alpha0), float(eps), _ptr(grad_u, torch.float32, "grad_u"),
+                                int(bool(accumulate)), _ptr(grad_w, torch.float32, "grad_w"),
+                                _ptr(energy_out, torch.float64, "energy_out", allow_none=True),
+                                _stream(stream, p0.device)))
+
+
+def pasfm_step_tgv(ctx, geom, p0, pose, elem, meas, mask, adam: PasfmAdam, tgv, loss_out=None, tgv_out=None,
+                   stream=None):
+    g = make_geom(geom, dtype_vol=p0.dtype, dtype_sig=meas.dtype)
+    _check(lib().pasfm_step_tgv(ctx, ctypes.byref(g), _ptr(p0, _VOL, "p0"), _ptr(pose, torch.float64, "pose"),
+                                _ptr(elem, torch.float64, "elem"), _ptr(meas, _VOL, "meas"),
+                                _ptr(mask, torch.uint8, "mask", allow_none=True), ctypes.byref(adam),
+                                None if tgv is None else ctypes.byref(tgv),
+                                _ptr(loss_out, torch.float64, "loss_out", allow_none=True),
+                                _ptr(tgv_out, torch.float64, "tgv_out", allow_none=True),
+                                _stream(stream, p0.device)))
+
+
 def pasfm_pose_grad_noalloc(geom, p0, elem, pose, g_sig, mask, grad6_out, gelem_out=None, stream=None):
     """Pose gradient without any device allocation (fixed in-library scratch)."""
     g = make_geom(geom, dtype_vol=p0.dtype, dtype_sig=g_sig.dtype)
@@ -286,8 +318,22 @@ class Context:
         pasfm_loss(self.handle, geom, sig, meas, mask, g_out, L, stream)
         return L, g_out
 
-    def step(self, geom, p0, pose, elem, meas, adam: "AdamState", mask=None, loss_out=None, stream=None):
-        pasfm_step(self.handle, geom, p0, pose, elem, meas, mask, adam.c, loss_out, stream)
+    def step(self, geom, p0, pose, elem, meas, adam: "AdamState", mask=None, loss_out=None, stream=None,
+             tgv: "TgvState | None" = None, tgv_out=None):
+        """One pasfm_step, or pasfm_step_tgv when a TGV state is given."""
+        if tgv is None:
+            pasfm_step(self.handle, geom, p0, pose, elem, meas, mask, adam.c, loss_out, stream)
+        else:
+            pasfm_step_tgv(self.handle, geom, p0, pose, elem, meas, mask, adam.c, tgv.c, loss_out, tgv_out, stream)
+
+    def tgv_grad(self, geom, p0, w, alpha1, alpha0, eps, grad_u=None, accumulate=False, stream=None):
+        """TGV energy (device double) and gradients (grad_u [nz][ny][nx], grad_w [3][nz][ny][nx])."""
+        shape = (geom["nz"], geom["ny"], geom["nx"])
+        grad_u = torch.zeros(shape, dtype=torch.float32, device=self.device) if grad_u is None else grad_u
+        grad_w = torch.empty((3,) + shape, dtype=torch.float32, device=self.device)
+        energy = torch.zeros((), dtype=torch.float64, device=self.device)
+        pasfm_tgv_grad(self.handle, geom, p0, w, alpha1, alpha0, eps, grad_u, accumulate, grad_w, energy, stream)
+        return energy, grad_u, grad_w
 
     def apply_twists(self, pose, xi, out=None, stream=None):
         """pose (F,3,4) with left twists xi (F,6) applied: (Exp(w) R, Exp(w) t + v)."""
@@ -351,6 +397,18 @@ class Context:
 
     def launch_count(self):
         return int(lib().pasfm_launch_count(self.handle))
+
+
+class TgvState:
+    """Device-resident auxiliary field w of the TGV regulariser with its Adam moments."""
+
+    def __init__(self, geom, device, alpha1, alpha0, eps=1e-3, lr_w=1e-2, w=None):
+        shape = (3, geom["nz"], geom["ny"], geom["nx"])
+        self.w = torch.zeros(shape, dtype=torch.float32, device=device) if w is None else w
+        self.m_w = torch.zeros(shape, dtype=torch.float32, device=device)
+        self.v_w = torch.zeros(shape, dtype=torch.float32, device=device)
+        self.c = PasfmTgv(self.w.data_ptr(), self.m_w.data_ptr(), self.v_w.data_ptr(), float(alpha1), float(alpha0),
+                          float(eps), float(lr_w))
 
 
 class AdamState:

@@ -69,6 +69,7 @@ def build(force: bool = False, jobs: int | None = None, verbose: bool = False) -
              [f"-DPASFM_K={k}", f"-DPASFM_S={s}"]) for k, s in KS_VALUES]
     work += [(os.path.join(CSRC, "aux.cu"), os.path.join(OBJ, "aux.o"), []),
              (os.path.join(CSRC, "launchers.cu"), os.path.join(OBJ, "launchers.o"), []),
+             (os.path.join(CSRC, "tgv.cu"), os.path.join(OBJ, "tgv.o"), []),
              (os.path.join(CSRC, "pasfm.cu"), os.path.join(OBJ, "pasfm.o"), []),
              (os.path.join(CSRC, "noalloc.cu"), os.path.join(OBJ, "noalloc.o"), [])]
     jobs = jobs or max(1, min(len(work), os.cpu_count() or 1))

@@ -169,7 +169,7 @@ int frames_per_chunk(size_t per_frame, size_t budget, int F) {
 struct pasfm_ctx {
   int device = 0;
   unsigned* status = nullptr;
-  Buf xw, part, n0, gres, vgrad, gpart, G, grad6, lpart, lscalar, taps, vparts;
+  Buf xw, part, n0, gres, vgrad, gpart, G, grad6, lpart, lscalar, taps, vparts, gw, tpart;
   int sms = 0;  // streaming multiprocessors of the device
   size_t budget = kDefaultPartialBudget;
   bool timing = false;
@@ -524,6 +524,70 @@ int run_backward(pasfm_ctx* ctx, const Geo& G, const Plan& pl, int mode, const v
   return PASFM_OK;
 }
 
+// F3: TGV energy and gradients (tgv.cu).  energy_out may be null.
+int run_tgv(pasfm_ctx* ctx, const Geo& G, const void* p0, const float* w, double alpha1, double alpha0, double eps,
+            float* grad_u, int accumulate, float* grad_w, double* energy_out, cudaStream_t st) {
+  const pasfm_geom& g = G.g;
+  const dim3 grid = tgv_grid(g.nx, g.ny, g.nz);
+  const size_t nblk = size_t(grid.x) * grid.y * grid.z;
+  TRY(ctx->ensure(ctx->tpart, nblk * 8));
+  CUtensorMap umap, wmap;
+  std::memset(&umap, 0, sizeof umap);
+  std::memset(&wmap, 0, sizeof wmap);
+  int use_tma = 0;
+  auto enc = encode_fn();
+  if (enc && g.dtype_vol == PASFM_F32 && g.nx % 4 == 0 && aligned16(p0) && aligned16(w)) {
+    unsigned b3[3], b4[4];
+    tgv_boxes(b3, b4);
+    cuuint64_t d3[3] = {cuuint64_t(g.nx), cuuint64_t(g.ny), cuuint64_t(g.nz)};
+    cuuint64_t s3[2] = {cuuint64_t(g.nx) * 4, cuuint64_t(g.nx) * g.ny * 4};
+    cuuint32_t bx3[3] = {b3[0], b3[1], b3[2]};
+    cuuint64_t d4[4] = {cuuint64_t(g.nx), cuuint64_t(g.ny), cuuint64_t(g.nz), 3};
+    cuuint64_t s4[3] = {cuuint64_t(g.nx) * 4, cuuint64_t(g.nx) * g.ny * 4, cuuint64_t(G.nvox) * 4};
+    cuuint32_t bx4[4] = {b4[0], b4[1], b4[2], b4[3]};
+    cuuint32_t es[4] = {1, 1, 1, 1};
+    if (enc(&umap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(p0), d3, s3, bx3, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS &&
+        enc(&wmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float*>(w), d4, s4, bx4, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS)
+      use_tma = 1;
+  }
+  TgvParams P{};
+  P.u = p0;
+  P.dtype_u = g.dtype_vol;
+  P.w = w;
+  P.grad_u = grad_u;
+  P.accumulate = accumulate;
+  P.grad_w = grad_w;
+  P.energy_part = static_cast<double*>(ctx->tpart.p);
+  P.nx = g.nx;
+  P.ny = g.ny;
+  P.nz = g.nz;
+  P.inv_dx = static_cast<float>(1.0 / g.dx);
+  P.inv_dy = static_cast<float>(1.0 / g.dy);
+  P.inv_dz = static_cast<float>(1.0 / g.dz);
+  P.alpha1 = static_cast<float>(alpha1);
+  P.alpha0 = static_cast<float>(alpha0);
+  P.eps2 = static_cast<float>(eps * eps);
+  P.use_tma = use_tma;
+  P.status = ctx->status;
+  const size_t smem = tgv_smem_bytes();
+  CUDA_TRY(cudaFuncSetAttribute(tgv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+  cudaEvent_t t = ctx->begin(st);
+  tgv_kernel<<<grid, tgv_threads(), smem, st>>>(umap, wmap, P);
+  ctx->end("tgv", t, st);
+  TRY(check_launch("tgv"));
+  if (energy_out) {
+    t = ctx->begin(st);
+    sum_kernel<<<1, 256, 0, st>>>(P.energy_part, static_cast<int>(nblk), energy_out);
+    ctx->end("tgv_sum", t, st);
+    TRY(check_launch("tgv_sum"));
+  }
+  return PASFM_OK;
+}
+
 int run_grad6(pasfm_ctx* ctx, const Geo& G, const double* xw, const double* Gm, double* grad6, cudaStream_t st) {
   if (G.g.n_frames == 0) return PASFM_OK;
   cudaEvent_t t = ctx->begin(st);
@@ -577,7 +641,7 @@ int pasfm_destroy(pasfm_ctx* ctx) {
   if (!ctx) return PASFM_OK;
   cudaSetDevice(ctx->device);
   for (Buf* b : {&ctx->xw, &ctx->part, &ctx->n0, &ctx->gres, &ctx->vgrad, &ctx->gpart, &ctx->G, &ctx->grad6,
-                 &ctx->lpart, &ctx->lscalar, &ctx->taps, &ctx->vparts})
+                 &ctx->lpart, &ctx->lscalar, &ctx->taps, &ctx->vparts, &ctx->gw, &ctx->tpart})
     if (b->p) cudaFree(b->p);
   for (auto& r : ctx->recs) {
     cudaEventDestroy(r.a);
@@ -611,6 +675,10 @@ int pasfm_workspace_size(const pasfm_geom* geom, size_t* bytes) {
   b += size_t(G.n_rows) * G.g.n_samples * 4;                                // residual (step)
   b += size_t(G.nvox) * 4;                                                  // volume gradient (step)
   b += size_t(G.nvox) * 4 * kMaxParts;                                      // per-part adjoint sums
+  {
+    const dim3 tg = tgv_grid(G.g.nx, G.g.ny, G.g.nz);
+    b += size_t(G.nvox) * 12 + size_t(tg.x) * tg.y * tg.z * 8;               // TGV grad_w, energy partials
+  }
   b += size_t(G.n_rows) * 24 + size_t(F) * 48;                              // G, grad6
   b += (size_t(G.n_rows + 7) / 8 + (F + Ff - 1) / std::max(Ff, 1) + 2) * 8;  // loss partials
   *bytes = b;
@@ -633,6 +701,11 @@ int pasfm_reserve(pasfm_ctx* ctx, const pasfm_geom* geom) {
   TRY(ctx->ensure(ctx->vparts, size_t(G.nvox) * 4 * kMaxParts));
   TRY(ctx->ensure(ctx->G, size_t(G.n_rows) * 24));
   TRY(ctx->ensure(ctx->grad6, size_t(F) * 48));
+  {
+    const dim3 tg = tgv_grid(G.g.nx, G.g.ny, G.g.nz);
+    TRY(ctx->ensure(ctx->gw, size_t(G.nvox) * 12));
+    TRY(ctx->ensure(ctx->tpart, size_t(tg.x) * tg.y * tg.z * 8));
+  }
   TRY(ctx->ensure(ctx->lpart, (size_t(G.n_rows + 7) / 8 + (F + Ff - 1) / std::max(Ff, 1) + 2) * 8));
   TRY(ctx->ensure(ctx->lscalar, 8));
   return PASFM_OK;
@@ -742,11 +815,40 @@ int pasfm_loss(pasfm_ctx* ctx, const pasfm_geom* geom, const float* sig, const v
 
 int pasfm_step(pasfm_ctx* ctx, const pasfm_geom* geom, void* p0, double* pose, const double* elem,
                const void* meas, const uint8_t* mask, pasfm_adam* state, double* loss_out, void* stream) {
+  return pasfm_step_tgv(ctx, geom, p0, pose, elem, meas, mask, state, nullptr, loss_out, nullptr, stream);
+}
+
+int pasfm_tgv_grad(pasfm_ctx* ctx, const pasfm_geom* geom, const void* p0, const float* w, double alpha1,
+                   double alpha0, double eps, float* grad_u, int accumulate, float* grad_w, double* energy_out,
+                   void* stream) {
+  Geo G;
+  Plan pl;
+  TRY(prepare(ctx, geom, &G, &pl));
+  if (!(alpha1 >= 0) || !(alpha0 >= 0) || !(eps > 0) || !std::isfinite(alpha1) || !std::isfinite(alpha0) ||
+      !std::isfinite(eps))
+    return fail(PASFM_EINVAL, "TGV weights must be finite, alpha >= 0 and eps > 0");
+  if (G.nvox == 0) return PASFM_OK;
+  if (!p0 || !w || !grad_u || !grad_w) return fail(PASFM_EINVAL, "NULL array argument");
+  if (G.nvox > (int64_t(1) << 31) / 3) return fail(PASFM_EUNSUPPORTED, "volume too large for the TGV kernel");
+  return run_tgv(ctx, G, p0, w, alpha1, alpha0, eps, grad_u, accumulate, grad_w, energy_out,
+                 static_cast<cudaStream_t>(stream));
+}
+
+int pasfm_step_tgv(pasfm_ctx* ctx, const pasfm_geom* geom, void* p0, double* pose, const double* elem,
+                   const void* meas, const uint8_t* mask, pasfm_adam* state, const pasfm_tgv* tgv,
+                   double* loss_out, double* tgv_out, void* stream) {
   Geo G;
   Plan pl;
   TRY(prepare(ctx, geom, &G, &pl));
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (!state) return fail(PASFM_EINVAL, "state is NULL");
+  if (tgv) {
+    if (state->flags & PASFM_ADAM_FREEZE_VOLUME) return fail(PASFM_EINVAL, "a TGV step needs volume updates");
+    if (!tgv->w || !tgv->m_w || !tgv->v_w) return fail(PASFM_EINVAL, "TGV array is NULL");
+    if (!(tgv->alpha1 >= 0) || !(tgv->alpha0 >= 0) || !(tgv->eps > 0) || !std::isfinite(tgv->lr_w))
+      return fail(PASFM_EINVAL, "TGV weights must be finite, alpha >= 0 and eps > 0");
+    if (G.nvox > (int64_t(1) << 31) / 3) return fail(PASFM_EUNSUPPORTED, "volume too large for the TGV kernel");
+  }
   if (G.nvox == 0 || G.n_rows == 0 || G.g.n_samples == 0)
     return fail(PASFM_EINVAL, "pasfm_step needs a non-empty volume, array and record");
   if (!p0 || !pose || !elem || !meas) return fail(PASFM_EINVAL, "NULL array argument");
@@ -778,6 +880,20 @@ int pasfm_step(pasfm_ctx* ctx, const pasfm_geom* geom, void* p0, double* pose, c
                    static_cast<double*>(ctx->G.p), st));
   const double bc1 = 1.0 - std::pow(state->beta1, double(k));
   const double bc2 = 1.0 - std::pow(state->beta2, double(k));
+  if (tgv) {
+    // regulariser: its volume gradient joins the data gradient, then w takes its own Adam step
+    TRY(ctx->ensure(ctx->gw, size_t(G.nvox) * 12));
+    float* gw = static_cast<float*>(ctx->gw.p);
+    TRY(run_tgv(ctx, G, p0, tgv->w, tgv->alpha1, tgv->alpha0, tgv->eps, static_cast<float*>(ctx->vgrad.p), 1, gw,
+                tgv_out, st));
+    cudaEvent_t t = ctx->begin(st);
+    adam_vol_kernel<<<static_cast<unsigned>((3 * G.nvox + 255) / 256), 256, 0, st>>>(
+        tgv->w, PASFM_F32, gw, tgv->m_w, tgv->v_w, 3 * G.nvox, static_cast<float>(state->beta1),
+        static_cast<float>(state->beta2), static_cast<float>(tgv->lr_w / bc1), static_cast<float>(1.0 / std::sqrt(bc2)),
+        static_cast<float>(state->eps), 0);
+    ctx->end("adam_w", t, st);
+    TRY(check_launch("adam_w"));
+  }
   if (upd_pose) {
     TRY(run_grad6(ctx, G, xw, static_cast<double*>(ctx->G.p), static_cast<double*>(ctx->grad6.p), st));
     cudaEvent_t t = ctx->begin(st);

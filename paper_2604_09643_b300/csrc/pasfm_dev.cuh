@@ -72,6 +72,20 @@ struct FwdParams {
   unsigned* status;
 };
 
+struct TgvParams {
+  const void* u;        // volume [nz][ny][nx] of dtype_u
+  int dtype_u;
+  const float* w;       // auxiliary field [3][nz][ny][nx]
+  float* grad_u;        // [nz][ny][nx], overwritten or accumulated into
+  int accumulate;
+  float* grad_w;        // [3][nz][ny][nx], overwritten
+  double* energy_part;  // one per CTA
+  int nx, ny, nz;
+  float inv_dx, inv_dy, inv_dz, alpha1, alpha0, eps2;
+  int use_tma;
+  unsigned* status;
+};
+
 struct RedParams {
   const float* part;    // [Fc][E][ncubes][W]
   const int* n0tab;     // [Fc][E][ncubes]
@@ -175,6 +189,16 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, u
       "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
       " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(smem_addr(dst)),
       "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_addr(bar)), "r"(x), "r"(y), "r"(z)
+      : "memory");
+}
+
+// 4-D tiled TMA load.
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y, int z,
+                                            int c) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4, %5, %6}], [%2];" ::"r"(smem_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_addr(bar)), "r"(x), "r"(y), "r"(z), "r"(c)
       : "memory");
 }
 

@@ -153,6 +153,9 @@ class C2FConfig:
     # width per level, the data's width scaled by the level's spacing (at most SIGMA_MAX_SAMPLES sample pitches)
     sigma_schedule: tuple | None = None
     decimate_time: bool = True     # Gaussian kernel: coarse levels on a time grid coarser by their spacing ratio
+    # TGV regulariser of Stages 1 and 5 (alpha1, alpha0, eps, lr_w), or None; its auxiliary
+    # field starts at zero on every level
+    tgv: tuple | None = None
 
 
 SIGMA_MAX_SAMPLES = 3.75  # widest Gaussian the compiled kernels take, in sample pitches (8 sigma / h <= 30)
@@ -320,6 +323,7 @@ def reconstruct(ctx: binding.Context, geom_fine, elem, meas, poses_init, cfg: C2
                 ctx.step(geom, p0, poses, elem_d, meas_l, vadam, mask=mask, loss_out=loss)
         adam = binding.AdamState(geom, dev, lr_vol=cfg.lr_vol * decay, lr_rot=cfg.lr_rot * decay,
                                  lr_trans=cfg.lr_trans * decay, nonneg=cfg.nonneg, fix_frame0=cfg.fix_frame0)
+        reg = binding.TgvState(geom, dev, *cfg.tgv) if cfg.tgv is not None else None
         phase_len = max(1, -(-n_steps // len(widths)))
         for k in range(n_steps):
             if gauss and k > 0 and k % phase_len == 0:
@@ -335,7 +339,7 @@ def reconstruct(ctx: binding.Context, geom_fine, elem, meas, poses_init, cfg: C2
                     adam = binding.AdamState(geom, dev, lr_vol=cfg.lr_vol * decay, lr_rot=cfg.lr_rot * decay,
                                              lr_trans=cfg.lr_trans * decay, nonneg=cfg.nonneg,
                                              fix_frame0=cfg.fix_frame0)
-            ctx.step(geom, p0, poses, elem_d, meas_l, adam, mask=mask, loss_out=loss)
+            ctx.step(geom, p0, poses, elem_d, meas_l, adam, mask=mask, loss_out=loss, tgv=reg)
             if cfg.refine_every and (k + 1) % cfg.refine_every == 0:
                 mask, poses = rigid_consensus(ctx, geom, p0, poses, elem_d, meas_l, mask, cfg, rng)
         n_search = 0
