@@ -21,6 +21,25 @@ def nc(sim, meas) -> float:
     return float(-(s * m).sum() / den) if den > 0 else 0.0
 
 
+def nc_grad(sim, meas):
+    """d nc(sim, meas) / d sim.  With s~ and m~ the centred traces and
+    rho = <s~, m~> / (|s~| |m~|), the centring drops out of the derivative (the
+    centred traces sum to zero) and
+        d nc / d sim_n = -(m~_n / |m~| - rho s~_n / |s~|) / |s~|.
+    Zero for a trace with zero variance (where nc is defined as 0).  Pinned by
+    central differences of nc and by the invariances of nc: the gradient sums to
+    zero (offsets) and is orthogonal to sim (positive scaling)."""
+    s = np.asarray(sim, dtype=np.float64)
+    m = np.asarray(meas, dtype=np.float64)
+    s = s - s.mean()
+    m = m - m.mean()
+    ns, nm = np.sqrt((s * s).sum()), np.sqrt((m * m).sum())
+    if ns == 0 or nm == 0:
+        return np.zeros_like(s)
+    rho = (s * m).sum() / (ns * nm)
+    return -(m / nm - rho * s / ns) / ns
+
+
 def nc_scores(sim, meas, mask=None):
     """sim [K][E][Nt], meas [E][Nt] -> [K] mean NC over kept elements."""
     sim = np.asarray(sim)

@@ -85,6 +85,7 @@ _SIGS = {
     "pasfm_resample": ([_VP, _G, _VP, _G, _VP, _VP], _I),
     "pasfm_lowpass": ([_VP, ctypes.c_int64, _I, ctypes.c_double, _I, _VP, _VP, _VP], _I),
     "pasfm_nc_scores": ([_VP, _I, _I, _I, _VP, _VP, _I, _VP, _VP, _VP], _I),
+    "pasfm_nc_grad": ([_VP, ctypes.c_int64, _I, _VP, _VP, _I, _VP, ctypes.c_double, _VP, _VP, _VP], _I),
     "pasfm_pose_grad_noalloc": ([_G, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP], _I),
     "pasfm_status": ([_VP, _VP, ctypes.POINTER(ctypes.c_uint32)], _I),
     "pasfm_timing_enable": ([_VP, _I], _I),
@@ -371,6 +372,19 @@ class Context:
                                    _ptr(sig, torch.float32, "sig"), _ptr(out, torch.float32, "out"),
                                    _stream(stream, self.device)))
         return out
+
+    def nc_grad(self, sim, meas, mask=None, scale=1.0, out=None, stream=None):
+        """Gradient of the summed NC loss (Eq. 3) w.r.t. sim [..., Nt] (rows paired with
+        meas rows; mask per row or None) and the per-row NC values."""
+        T = int(sim.shape[-1])
+        rows = sim.numel() // T if sim.numel() else 0
+        out = torch.empty_like(sim) if out is None else out
+        nc = torch.zeros(sim.shape[:-1], dtype=torch.float64, device=self.device)
+        _check(lib().pasfm_nc_grad(self.handle, int(rows), T, _ptr(sim, torch.float32, "sim"), _ptr(meas, _VOL, "meas"),
+                                   _DTYPE_CODE[meas.dtype], _ptr(mask, torch.uint8, "mask", allow_none=True),
+                                   float(scale), _ptr(out, torch.float32, "out"), _ptr(nc, torch.float64, "nc"),
+                                   _stream(stream, self.device)))
+        return out, nc
 
     def nc_scores(self, sim, meas, mask=None, out=None, stream=None):
         """NC-loss scores of candidate trace sets sim [K][E][Nt] against meas [E][Nt]."""

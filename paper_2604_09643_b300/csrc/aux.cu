@@ -491,4 +491,55 @@ __global__ void __launch_bounds__(256) nc_scores_kernel(const float* __restrict_
   }
 }
 
+// Gradient of the NC loss (Eq. 3) summed over the kept traces: one warp per
+// trace; centred sums in two passes (means, then centred moments: FP32 runs of at
+// most ceil(Nt / 32) terms per lane, carried to FP64), then
+//   g_n = -scale (m~_n / |m~| - rho s~_n / |s~|) / |s~|,  rho = <s~, m~> / (|s~| |m~|).
+// g may alias sim: each lane reads s_n before writing g_n at the same n.
+__global__ void __launch_bounds__(256) nc_grad_kernel(const float* sim, const void* meas, int dtype,
+                                                      const uint8_t* __restrict__ mask, int64_t n_rows, int Nt,
+                                                      float scale, float* g, double* __restrict__ nc_out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t row = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (row >= n_rows) return;
+  const int64_t base = row * Nt;
+  const bool keep = !mask || mask[row];
+  auto warp_sum = [](double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+  };
+  double s_mean = 0.0, m_mean = 0.0, ns = 0.0, nm = 0.0, rho = 0.0;
+  if (keep) {
+    float a = 0.f, b = 0.f;
+    for (int n = lane; n < Nt; n += 32) {
+      a += sim[base + n];
+      b += load_elem(meas, base + n, dtype);
+    }
+    s_mean = warp_sum(a) / Nt;
+    m_mean = warp_sum(b) / Nt;
+    const float sm = static_cast<float>(s_mean), mm = static_cast<float>(m_mean);
+    float ss = 0.f, qq = 0.f, sq = 0.f;
+    for (int n = lane; n < Nt; n += 32) {
+      const float x = sim[base + n] - sm, y = load_elem(meas, base + n, dtype) - mm;
+      ss = fmaf(x, x, ss);
+      qq = fmaf(y, y, qq);
+      sq = fmaf(x, y, sq);
+    }
+    ns = sqrt(warp_sum(ss));
+    nm = sqrt(warp_sum(qq));
+    const double c = warp_sum(sq);
+    rho = (ns > 0.0 && nm > 0.0) ? c / (ns * nm) : 0.0;
+  }
+  const bool live = keep && ns > 0.0 && nm > 0.0;
+  const float sm = static_cast<float>(s_mean), mm = static_cast<float>(m_mean);
+  const float cm = live ? static_cast<float>(-scale / (nm * ns)) : 0.f;
+  const float cs = live ? static_cast<float>(scale * rho / (ns * ns)) : 0.f;
+  for (int n = lane; n < Nt; n += 32) {
+    const float x = sim[base + n] - sm, y = load_elem(meas, base + n, dtype) - mm;
+    g[base + n] = fmaf(cm, y, cs * x);
+  }
+  if (lane == 0 && nc_out) nc_out[row] = live ? -rho : 0.0;
+}
+
 }  // namespace pasfm

@@ -1018,6 +1018,24 @@ int pasfm_nc_scores(pasfm_ctx* ctx, int n_cand, int n_elem, int n_samples, const
   return check_launch("nc_scores");
 }
 
+int pasfm_nc_grad(pasfm_ctx* ctx, int64_t n_rows, int n_samples, const float* sim, const void* meas, int dtype_meas,
+                  const uint8_t* mask, double scale, float* g_out, double* nc_out, void* stream) {
+  if (!ctx) return fail(PASFM_EINVAL, "ctx is NULL");
+  if (n_rows < 0 || n_samples < 0 || !std::isfinite(scale)) return fail(PASFM_EINVAL, "bad size or scale");
+  if (dtype_meas != PASFM_F32 && dtype_meas != PASFM_BF16 && dtype_meas != PASFM_F16)
+    return fail(PASFM_EINVAL, "unknown dtype %d", dtype_meas);
+  if (n_rows == 0 || n_samples == 0) return PASFM_OK;
+  if (!sim || !meas || !g_out) return fail(PASFM_EINVAL, "NULL array argument");
+  if ((n_rows + 7) / 8 > INT32_MAX) return fail(PASFM_EUNSUPPORTED, "too many traces");
+  TRY(set_device(ctx));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaEvent_t t = ctx->begin(st);
+  nc_grad_kernel<<<static_cast<unsigned>((n_rows + 7) / 8), 256, 0, st>>>(
+      sim, meas, dtype_meas, mask, n_rows, n_samples, static_cast<float>(scale), g_out, nc_out);
+  ctx->end("nc_grad", t, st);
+  return check_launch("nc_grad");
+}
+
 int pasfm_status(pasfm_ctx* ctx, void* stream, uint32_t* bits) {
   if (!ctx) return fail(PASFM_EINVAL, "ctx is NULL");
   TRY(set_device(ctx));

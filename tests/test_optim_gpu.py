@@ -124,3 +124,25 @@ def test_gaussian_kernel_annealing_recovers_poses(cuda_device):
     assert [h["time_decimation"] for h in hist] == [2, 1]
     assert hist[-1]["kernel_sigma_mm"] == 0.08
     assert hist[-1]["mean_element_error_mm"] < 0.01
+
+
+def test_nc_grad_matches_oracle(cuda_device):
+    from oracle import nc as ncmod
+    rng = np.random.default_rng(12)
+    R, T = 40, 777
+    meas = rng.standard_normal((R, T)).astype(np.float32)
+    sim = (0.6 * meas + 0.8 * rng.standard_normal((R, T)) + 0.2).astype(np.float32)
+    sim[3] = 1.5  # zero variance: gradient 0, NC 0
+    mask = (rng.uniform(size=R) > 0.25).astype(np.uint8)
+    with binding.Context(0) as ctx:
+        d = lambda a: torch.tensor(a, device="cuda")
+        g, nc = ctx.nc_grad(d(sim), d(meas), d(mask), scale=2.0)
+        alias = d(sim)
+        ctx.nc_grad(alias, d(meas), d(mask), scale=2.0, out=alias)
+    g, nc = g.cpu().numpy(), nc.cpu().numpy()
+    ref = np.stack([2.0 * ncmod.nc_grad(sim[r], meas[r]) * mask[r] for r in range(R)])
+    ref_nc = np.array([ncmod.nc(sim[r], meas[r]) * mask[r] for r in range(R)])
+    assert rel_l2(g, ref) < 1e-5
+    assert np.abs(nc - ref_nc).max() < 1e-6
+    assert not g[3].any() and nc[3] == 0.0
+    assert np.array_equal(alias.cpu().numpy(), g)

@@ -208,6 +208,24 @@ def test_nc_loss_invariances():
 
 
 
+def test_nc_gradient_pins():
+    from oracle import nc as ncmod
+    rng = np.random.default_rng(41)
+    a = rng.standard_normal(300) + 0.3
+    b = 0.5 * a + rng.standard_normal(300)
+    g = ncmod.nc_grad(a, b)
+    assert abs(g.sum()) < 1e-13 * np.abs(g).sum()          # offsets of sim do not change nc
+    assert abs(np.dot(g, a)) < 1e-13 * np.abs(g * a).sum()  # nor does positive scaling
+    h = 1e-6
+    for n in rng.integers(0, 300, size=8):
+        ap, am = a.copy(), a.copy()
+        ap[n] += h
+        am[n] -= h
+        fd = (ncmod.nc(ap, b) - ncmod.nc(am, b)) / (2 * h)
+        assert abs(fd - g[n]) < 1e-7 * np.abs(g).max()
+    assert not ncmod.nc_grad(np.ones(10), a[:10]).any()
+
+
 # ---- TGV regulariser (Stages 1 and 5, Eq. 2)
 
 def test_tgv_matches_sparse_matrix_formulation():
