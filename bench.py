@@ -76,13 +76,19 @@ def peaks():
                 source="measured" if p else "fallback")
 
 
-HOT_SOURCES = ("kernels.cuh", "pasfm_dev.cuh", "kernels_s.cu", "aux.cu", "tgv.cu")
+# sources that define each measured kernel (traffic counters are valid only for these bytes)
+KERNEL_SOURCES = {
+    "fwd_cube": ("kernels.cuh", "pasfm_dev.cuh", "kernels_s.cu"),
+    "bwd_cube": ("kernels.cuh", "pasfm_dev.cuh", "kernels_s.cu"),
+    "fwd_reduce": ("aux.cu", "pasfm_dev.cuh"),
+    "tgv": ("tgv.cu", "pasfm_dev.cuh"),
+}
 
 
-def kernel_src_hash():
-    """Hash of the sources that define the measured kernels (bwd_cube, fwd_cube, fwd_reduce)."""
+def kernel_src_hash(kernel="bwd_cube"):
+    """Hash of the sources that define `kernel` (a KERNEL_SOURCES key, '_gauss' suffix ignored)."""
     h = hashlib.sha256()
-    for fn in HOT_SOURCES:
+    for fn in KERNEL_SOURCES[kernel.replace("_gauss", "")]:
         with open(os.path.join(ROOT, "paper_2604_09643_b300", "csrc", fn), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -96,7 +102,7 @@ def traffic_for(kernel):
     except (OSError, ValueError):
         return None
     e = t.get(kernel)
-    if not e or e.get("src_sha") != kernel_src_hash():
+    if not e or e.get("src_sha") != kernel_src_hash(kernel):
         return None
     return e.get("bytes_per_launch")
 

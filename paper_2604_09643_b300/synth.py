@@ -276,6 +276,58 @@ def mixed_precision_scan(n_frames=400, seed_offset=0) -> Scan:
                      seed_offset=seed_offset)
 
 
+def hemisphere_array(n_total=1024, radius=60.0, keep_half=True) -> np.ndarray:
+    """Elements spread evenly (Fibonacci spiral) over the hemisphere of `radius` mm
+    facing its centre from above (z > 0), centre at the origin of the array frame.
+    With keep_half only the elements with azimuth in [0, pi) are kept: the
+    512-element half of a 1024-element bowl."""
+    k = np.arange(n_total) + 0.5
+    z = 1.0 - k / n_total                     # cos(polar angle) uniform in (0, 1): even area on the hemisphere
+    phi = np.mod(math.pi * (3.0 - math.sqrt(5.0)) * k, 2 * math.pi)
+    r = np.sqrt(1.0 - z * z)
+    pts = radius * np.stack([r * np.cos(phi), r * np.sin(phi), z], axis=1)
+    if keep_half:
+        pts = pts[phi < math.pi]
+    return pts
+
+
+def cap_array(n_elem=33, radius=60.0, half_angle_deg=40.0, seed=0) -> np.ndarray:
+    """A sparse array of n_elem elements spread over a spherical cap of `radius` mm
+    and the given half-angle about +z, facing its centre (the origin)."""
+    rng = np.random.default_rng(SEED_TRAJ + 70 + seed)
+    cmin = math.cos(math.radians(half_angle_deg))
+    z = rng.uniform(cmin, 1.0, size=n_elem)
+    phi = rng.uniform(0, 2 * math.pi, size=n_elem)
+    r = np.sqrt(1.0 - z * z)
+    return radius * np.stack([r * np.cos(phi), r * np.sin(phi), z], axis=1)
+
+
+def two_view_scan(n=128, spacing=0.1, n_tubes=40, elem=None, view_b_deg=90.0, prior_rot_deg=2.0,
+                  prior_trans_mm=1.0, n_samples=768, seed_offset=0) -> Scan:
+    """Two views of a vessel-tree volume at the centre of a hemispherical bowl:
+    view A at the known pose (identity), view B the same probe turned by view_b_deg
+    about the bowl axis plus a small random offset.  poses_init holds the prior for
+    view B (truth perturbed by prior_rot_deg / prior_trans_mm; view A exact).  The
+    record starts when the nearest voxel's pulse can first arrive."""
+    elem = hemisphere_array() if elem is None else np.asarray(elem, dtype=np.float64)
+    geom = make_geom((n, n, n), spacing, len(elem), 2, n_samples)
+    rng = np.random.default_rng(SEED_PHANTOM + 80 + seed_offset)
+    p0 = vessel_tree_phantom(geom, n_tubes, rng)
+    trng = np.random.default_rng(SEED_TRAJ + 80 + seed_offset)
+    poses = np.zeros((2, 3, 4))
+    poses[0, :, :3] = np.eye(3)
+    poses[1, :, :3] = axis_angle_matrix(random_unit(trng), math.radians(trng.uniform(0.5, 1.5))) @ \
+        axis_angle_matrix([0.0, 0.0, 1.0], math.radians(view_b_deg))
+    poses[1, :, 3] = random_unit(trng) * trng.uniform(0.2, 0.6)
+    half_diag = 0.5 * math.sqrt(3.0) * n * spacing
+    d_min = float(np.linalg.norm(elem, axis=1).min()) - half_diag - 1.0
+    geom["t0_us"] = max(0.0, d_min) / geom["c_mm_per_us"]
+    nrng = np.random.default_rng(SEED_NOISE + 80 + seed_offset)
+    init = poses.copy()
+    init[1:] = perturb_poses(poses[1:], nrng, prior_rot_deg, prior_trans_mm, keep_first=False)
+    return Scan(geom, p0, elem, poses, name=f"two_view_{n}^3_{len(elem)}elem", poses_init=init)
+
+
 def random_like_signals(geom, rng, dtype=np.float32) -> np.ndarray:
     """Standard-normal array shaped like the signals [F][E][Nt]."""
     return rng.standard_normal((geom["n_frames"], geom["n_elem"],
