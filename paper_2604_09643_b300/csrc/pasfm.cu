@@ -528,30 +528,40 @@ int run_backward(pasfm_ctx* ctx, const Geo& G, const Plan& pl, int mode, const v
 int run_tgv(pasfm_ctx* ctx, const Geo& G, const void* p0, const float* w, double alpha1, double alpha0, double eps,
             float* grad_u, int accumulate, float* grad_w, double* energy_out, cudaStream_t st) {
   const pasfm_geom& g = G.g;
-  const dim3 grid = tgv_grid(g.nx, g.ny, g.nz);
-  const size_t nblk = size_t(grid.x) * grid.y * grid.z;
-  TRY(ctx->ensure(ctx->tpart, nblk * 8));
-  CUtensorMap umap, wmap;
+  const int tiles = tgv_tiles(g.nx, g.ny, g.nz);
+  const size_t smem = tgv_smem_bytes();
+  CUDA_TRY(cudaFuncSetAttribute(tgv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tgv_kernel, tgv_threads(), smem) != cudaSuccess) {
+    cudaGetLastError();
+    per_sm = 1;
+  }
+  const int grid = std::max(1, std::min(tiles, std::max(1, per_sm) * std::max(1, ctx->sms)));
+  TRY(ctx->ensure(ctx->tpart, size_t(grid) * 8));
+  CUtensorMap umap, wmap, gmap;
   std::memset(&umap, 0, sizeof umap);
   std::memset(&wmap, 0, sizeof wmap);
+  std::memset(&gmap, 0, sizeof gmap);
   int use_tma = 0;
   auto enc = encode_fn();
-  if (enc && g.dtype_vol == PASFM_F32 && g.nx % 4 == 0 && aligned16(p0) && aligned16(w)) {
-    unsigned b3[3], b4[4];
-    tgv_boxes(b3, b4);
+  if (enc && g.dtype_vol == PASFM_F32 && g.nx % 4 == 0 && aligned16(p0) && aligned16(w) && aligned16(grad_u)) {
+    unsigned b3[3], b4[4], bg[3];
+    tgv_boxes(b3, b4, bg);
     cuuint64_t d3[3] = {cuuint64_t(g.nx), cuuint64_t(g.ny), cuuint64_t(g.nz)};
     cuuint64_t s3[2] = {cuuint64_t(g.nx) * 4, cuuint64_t(g.nx) * g.ny * 4};
     cuuint32_t bx3[3] = {b3[0], b3[1], b3[2]};
+    cuuint32_t bxg[3] = {bg[0], bg[1], bg[2]};
     cuuint64_t d4[4] = {cuuint64_t(g.nx), cuuint64_t(g.ny), cuuint64_t(g.nz), 3};
     cuuint64_t s4[3] = {cuuint64_t(g.nx) * 4, cuuint64_t(g.nx) * g.ny * 4, cuuint64_t(G.nvox) * 4};
     cuuint32_t bx4[4] = {b4[0], b4[1], b4[2], b4[3]};
     cuuint32_t es[4] = {1, 1, 1, 1};
-    if (enc(&umap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(p0), d3, s3, bx3, es,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS &&
-        enc(&wmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float*>(w), d4, s4, bx4, es,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS)
+    auto mk = [&](CUtensorMap* m, int rank, void* base, cuuint64_t* dims, cuuint64_t* strides, cuuint32_t* box) {
+      return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, rank, base, dims, strides, box, es,
+                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    };
+    if (mk(&umap, 3, const_cast<void*>(p0), d3, s3, bx3) && mk(&wmap, 4, const_cast<float*>(w), d4, s4, bx4) &&
+        mk(&gmap, 3, grad_u, d3, s3, bxg))
       use_tma = 1;
   }
   TgvParams P{};
@@ -573,15 +583,13 @@ int run_tgv(pasfm_ctx* ctx, const Geo& G, const void* p0, const float* w, double
   P.eps2 = static_cast<float>(eps * eps);
   P.use_tma = use_tma;
   P.status = ctx->status;
-  const size_t smem = tgv_smem_bytes();
-  CUDA_TRY(cudaFuncSetAttribute(tgv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
   cudaEvent_t t = ctx->begin(st);
-  tgv_kernel<<<grid, tgv_threads(), smem, st>>>(umap, wmap, P);
+  tgv_kernel<<<grid, tgv_threads(), smem, st>>>(umap, wmap, gmap, P);
   ctx->end("tgv", t, st);
   TRY(check_launch("tgv"));
   if (energy_out) {
     t = ctx->begin(st);
-    sum_kernel<<<1, 256, 0, st>>>(P.energy_part, static_cast<int>(nblk), energy_out);
+    sum_kernel<<<1, 256, 0, st>>>(P.energy_part, grid, energy_out);
     ctx->end("tgv_sum", t, st);
     TRY(check_launch("tgv_sum"));
   }
@@ -675,10 +683,7 @@ int pasfm_workspace_size(const pasfm_geom* geom, size_t* bytes) {
   b += size_t(G.n_rows) * G.g.n_samples * 4;                                // residual (step)
   b += size_t(G.nvox) * 4;                                                  // volume gradient (step)
   b += size_t(G.nvox) * 4 * kMaxParts;                                      // per-part adjoint sums
-  {
-    const dim3 tg = tgv_grid(G.g.nx, G.g.ny, G.g.nz);
-    b += size_t(G.nvox) * 12 + size_t(tg.x) * tg.y * tg.z * 8;               // TGV grad_w, energy partials
-  }
+  b += size_t(G.nvox) * 12 + size_t(tgv_tiles(G.g.nx, G.g.ny, G.g.nz)) * 8;  // TGV grad_w, energy partials
   b += size_t(G.n_rows) * 24 + size_t(F) * 48;                              // G, grad6
   b += (size_t(G.n_rows + 7) / 8 + (F + Ff - 1) / std::max(Ff, 1) + 2) * 8;  // loss partials
   *bytes = b;
@@ -701,11 +706,8 @@ int pasfm_reserve(pasfm_ctx* ctx, const pasfm_geom* geom) {
   TRY(ctx->ensure(ctx->vparts, size_t(G.nvox) * 4 * kMaxParts));
   TRY(ctx->ensure(ctx->G, size_t(G.n_rows) * 24));
   TRY(ctx->ensure(ctx->grad6, size_t(F) * 48));
-  {
-    const dim3 tg = tgv_grid(G.g.nx, G.g.ny, G.g.nz);
-    TRY(ctx->ensure(ctx->gw, size_t(G.nvox) * 12));
-    TRY(ctx->ensure(ctx->tpart, size_t(tg.x) * tg.y * tg.z * 8));
-  }
+  TRY(ctx->ensure(ctx->gw, size_t(G.nvox) * 12));
+  TRY(ctx->ensure(ctx->tpart, size_t(tgv_tiles(G.g.nx, G.g.ny, G.g.nz)) * 8));
   TRY(ctx->ensure(ctx->lpart, (size_t(G.n_rows + 7) / 8 + (F + Ff - 1) / std::max(Ff, 1) + 2) * 8));
   TRY(ctx->ensure(ctx->lscalar, 8));
   return PASFM_OK;

@@ -302,23 +302,24 @@ def cap_array(n_elem=33, radius=60.0, half_angle_deg=40.0, seed=0) -> np.ndarray
     return radius * np.stack([r * np.cos(phi), r * np.sin(phi), z], axis=1)
 
 
-def two_view_scan(n=128, spacing=0.1, n_tubes=40, elem=None, view_b_deg=90.0, prior_rot_deg=2.0,
-                  prior_trans_mm=1.0, n_samples=768, seed_offset=0) -> Scan:
-    """Two views of a vessel-tree volume at the centre of a hemispherical bowl:
-    view A at the known pose (identity), view B the same probe turned by view_b_deg
-    about the bowl axis plus a small random offset.  poses_init holds the prior for
-    view B (truth perturbed by prior_rot_deg / prior_trans_mm; view A exact).  The
+def two_view_scan(n=128, spacing=0.1, n_tubes=40, elem=None, view_b_deg=90.0, prior_rot_deg=0.5,
+                  prior_trans_mm=0.5, n_samples=768, n_views=2, seed_offset=0) -> Scan:
+    """Views of a vessel-tree volume at the centre of a hemispherical bowl: view 0
+    at the known pose (identity), view k the same probe turned by k * view_b_deg
+    about the bowl axis plus a small random tilt and offset.  poses_init holds the
+    priors (truth perturbed by prior_rot_deg / prior_trans_mm; view 0 exact).  The
     record starts when the nearest voxel's pulse can first arrive."""
     elem = hemisphere_array() if elem is None else np.asarray(elem, dtype=np.float64)
-    geom = make_geom((n, n, n), spacing, len(elem), 2, n_samples)
+    geom = make_geom((n, n, n), spacing, len(elem), n_views, n_samples)
     rng = np.random.default_rng(SEED_PHANTOM + 80 + seed_offset)
     p0 = vessel_tree_phantom(geom, n_tubes, rng)
     trng = np.random.default_rng(SEED_TRAJ + 80 + seed_offset)
-    poses = np.zeros((2, 3, 4))
+    poses = np.zeros((n_views, 3, 4))
     poses[0, :, :3] = np.eye(3)
-    poses[1, :, :3] = axis_angle_matrix(random_unit(trng), math.radians(trng.uniform(0.5, 1.5))) @ \
-        axis_angle_matrix([0.0, 0.0, 1.0], math.radians(view_b_deg))
-    poses[1, :, 3] = random_unit(trng) * trng.uniform(0.2, 0.6)
+    for k in range(1, n_views):
+        poses[k, :, :3] = axis_angle_matrix(random_unit(trng), math.radians(trng.uniform(0.5, 1.5))) @ \
+            axis_angle_matrix([0.0, 0.0, 1.0], math.radians(k * view_b_deg))
+        poses[k, :, 3] = random_unit(trng) * trng.uniform(0.2, 0.6)
     half_diag = 0.5 * math.sqrt(3.0) * n * spacing
     d_min = float(np.linalg.norm(elem, axis=1).min()) - half_diag - 1.0
     geom["t0_us"] = max(0.0, d_min) / geom["c_mm_per_us"]
