@@ -550,23 +550,27 @@ def run_two_view(args):
     """The PA-SFM pipeline (Stages 1-5) on two views of a 128^3 vessel volume at the
     centre of a 512-element half of a 60 mm hemispherical bowl (view B turned 90 deg,
     prior off by 0.5 deg / 0.5 mm per axis), or with --array cap33 on three views of
-    a 33-element spherical-cap array."""
+    a 33-element spherical-cap array over a 32^3 grid at 0.4 mm."""
     import torch
 
     from paper_2604_09643_b300 import binding, pipeline, synth
 
     torch.cuda.set_device(0)
     if args.array == "cap33":
-        scan = synth.two_view_scan(n=128, spacing=0.1, elem=synth.cap_array(33), n_views=3, view_b_deg=30.0)
-        name = "pipeline_128^3_0.1mm_cap33_60mm_3views"
+        # 33 elements see too little for a fine reference map; the views are located on a 0.4 mm grid
+        scan = synth.two_view_scan(n=32, spacing=0.4, elem=synth.cap_array(33), n_views=3, view_b_deg=30.0)
+        name = "pipeline_32^3_0.4mm_cap33_60mm_3views"
+        cfg = pipeline.PipelineConfig(stage1_steps=1500, search_radius_mm=2.0, inlier_tol_mm=0.5, edge_tol_mm=0.5,
+                                      top_k=8)
     else:
         scan = synth.two_view_scan(n=128, spacing=0.1)
         name = "pipeline_128^3_0.1mm_bowl512_60mm_2views"
+        cfg = pipeline.PipelineConfig(stage1_steps=900, stage5_steps=900)
     with binding.Context(0) as ctx:
         l0 = ctx.launch_count()
         with ClockSampler(0) as clk:
             t0 = time.perf_counter()
-            res, _, _ = pipeline.run(ctx, scan, pipeline.PipelineConfig())
+            res, _, _ = pipeline.run(ctx, scan, cfg)
             wall = time.perf_counter() - t0
         launches = ctx.launch_count() - l0
         rc, bits = ctx.status()

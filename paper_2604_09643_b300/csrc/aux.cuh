@@ -47,12 +47,13 @@ using BwdLaunch = cudaError_t (*)(int C, int mode, const CUtensorMap& map, const
 
 // Launchers of the hot kernels for pulse profile K and slot count S; null when
 // (K, S) is not compiled (sphere: S = 2..16, Gaussian: S = 2..32).
-// TGV regulariser (tgv.cu): persistent kernel, its shared-memory size, tile count,
+// TGV regulariser (tgv.cu): kernel, its shared-memory size, tile count and grid,
 // block size and TMA boxes (u region, w region, volume-gradient tile).
 __global__ void tgv_kernel(const __grid_constant__ CUtensorMap umap, const __grid_constant__ CUtensorMap wmap,
                            const __grid_constant__ CUtensorMap gmap, const TgvParams P);
 size_t tgv_smem_bytes();
 int tgv_tiles(int nx, int ny, int nz);
+dim3 tgv_grid(int nx, int ny, int nz);
 int tgv_threads();
 void tgv_boxes(unsigned* box3, unsigned* box4, unsigned* boxg);
 

@@ -529,15 +529,10 @@ int run_tgv(pasfm_ctx* ctx, const Geo& G, const void* p0, const float* w, double
             float* grad_u, int accumulate, float* grad_w, double* energy_out, cudaStream_t st) {
   const pasfm_geom& g = G.g;
   const int tiles = tgv_tiles(g.nx, g.ny, g.nz);
+  const dim3 grid = tgv_grid(g.nx, g.ny, g.nz);
   const size_t smem = tgv_smem_bytes();
   CUDA_TRY(cudaFuncSetAttribute(tgv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
-  int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tgv_kernel, tgv_threads(), smem) != cudaSuccess) {
-    cudaGetLastError();
-    per_sm = 1;
-  }
-  const int grid = std::max(1, std::min(tiles, std::max(1, per_sm) * std::max(1, ctx->sms)));
-  TRY(ctx->ensure(ctx->tpart, size_t(grid) * 8));
+  TRY(ctx->ensure(ctx->tpart, size_t(tiles) * 8));
   CUtensorMap umap, wmap, gmap;
   std::memset(&umap, 0, sizeof umap);
   std::memset(&wmap, 0, sizeof wmap);
@@ -589,7 +584,7 @@ int run_tgv(pasfm_ctx* ctx, const Geo& G, const void* p0, const float* w, double
   TRY(check_launch("tgv"));
   if (energy_out) {
     t = ctx->begin(st);
-    sum_kernel<<<1, 256, 0, st>>>(P.energy_part, grid, energy_out);
+    sum_kernel<<<1, 256, 0, st>>>(P.energy_part, tiles, energy_out);
     ctx->end("tgv_sum", t, st);
     TRY(check_launch("tgv_sum"));
   }

@@ -9,17 +9,16 @@
 // are dJ/du = sum_a D_a^T q_a and dJ/dw_b = -q_b + sum_a D_a^T P_ab, where
 // (D_a^T y)[j] = ([j_a >= 1] y[j - e_a] - [j_a <= n_a - 2] y[j]) / d_a.
 //
-// Persistent CTAs (two per SM) walk 32 x 4 x 4 tiles, one voxel per thread.
-// For each tile, u and w with a one-voxel halo below and above (x widened to a
-// 4-voxel boundary) and the tile's slice of the accumulated volume gradient are
-// staged in shared memory by TMA (zero fill outside the grid) into one of two
-// buffers: the next tile's copies are in flight while the current tile is
-// computed, so HBM latency overlaps the arithmetic.  (Plain loads replace TMA
-// when rows are not 16-byte aligned or p0 is 16-bit.)  q and P are formed once
-// for the tile plus its lower halo, so each output reads its neighbours' q and P
-// from shared memory: u and w come from HBM once per tile (halos from L2) and
-// the gradients are written once.  The energy is reduced per CTA in FP64 and
-// summed in a fixed order.
+// One CTA per 32 x 4 x 4 tile, one voxel per thread, four CTAs per SM.  The
+// tile's u and w with a one-voxel halo below and above (x widened to a 4-voxel
+// boundary) and its slice of the accumulated volume gradient are staged in
+// shared memory by TMA (zero fill outside the grid; plain loads when rows are
+// not 16-byte aligned or p0 is 16-bit), so no thread waits on a dependent global
+// load.  q and P are formed once for the tile plus its lower halo, so each output
+// reads its neighbours' q and P from shared memory: u and w come from HBM once
+// per tile (halos from L2) and the gradients are written once.  The norms use one
+// rsqrt each (phi = f rsqrt(f), alpha / phi = alpha rsqrt(f)).  The energy is
+// reduced per CTA in FP64 and summed in a fixed order.
 #include "aux.cuh"
 
 namespace pasfm {
@@ -40,10 +39,10 @@ struct TgvBuf {
 };
 
 struct TgvSmem {
-  TgvBuf buf[2];
+  TgvBuf buf;
   float qp[9][QN];  // q_x, q_y, q_z, P_xx, P_yy, P_zz, P_xy, P_xz, P_yz
   double red[TN / 32];
-  uint64_t bar[2];
+  uint64_t bar;
 };
 
 __device__ __forceinline__ int ridx(int x, int y, int z) { return (z * RY + y) * RX + x; }
@@ -51,38 +50,37 @@ __device__ __forceinline__ int qidx(int x, int y, int z) { return (z * QY + y) *
 
 }  // namespace
 
-__global__ void __launch_bounds__(TN, 2)
+__global__ void __launch_bounds__(TN, 4)
     tgv_kernel(const __grid_constant__ CUtensorMap umap, const __grid_constant__ CUtensorMap wmap,
                const __grid_constant__ CUtensorMap gmap, const TgvParams P) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   TgvSmem& S = *reinterpret_cast<TgvSmem*>(smem_raw);
   const int tid = threadIdx.x;
-  const int ntx = (P.nx + TX - 1) / TX, nty = (P.ny + TY - 1) / TY, ntz = (P.nz + TZ - 1) / TZ;
-  const int n_tiles = ntx * nty * ntz;
   const int64_t nvox = static_cast<int64_t>(P.nx) * P.ny * P.nz;
   const float inv_d[3] = {P.inv_dx, P.inv_dy, P.inv_dz};
   const int nn[3] = {P.nx, P.ny, P.nz};
-  const uint32_t tx_bytes = static_cast<uint32_t>(4 * RN * 4 + (P.accumulate ? TN * 4 : 0));
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * TZ;
+  TgvBuf& B = S.buf;
 
-  auto origin = [&](int tile, int& x0, int& y0, int& z0) {
-    x0 = (tile % ntx) * TX;
-    y0 = ((tile / ntx) % nty) * TY;
-    z0 = (tile / (ntx * nty)) * TZ;
-  };
-  // stage tile `tile` into buffer b (TMA: issued by thread 0; plain loads: all threads)
-  auto stage = [&](int tile, int b) {
-    int x0, y0, z0;
-    origin(tile, x0, y0, z0);
-    TgvBuf& B = S.buf[b];
-    if (P.use_tma) {
-      if (tid == 0) {
-        mbar_arrive_expect_tx(&S.bar[b], tx_bytes);
-        tma_load_3d(B.u, &umap, &S.bar[b], x0 - 4, y0 - 1, z0 - 1);
-        tma_load_4d(B.w[0], &wmap, &S.bar[b], x0 - 4, y0 - 1, z0 - 1, 0);
-        if (P.accumulate) tma_load_3d(B.gu, &gmap, &S.bar[b], x0, y0, z0);
-      }
-      return;
+  // stage u, w (region) and the tile's accumulated volume gradient
+  bool ok = true;
+  if (P.use_tma) {
+    if (tid == 0) {
+      mbar_init(&S.bar, 1);
+      fence_mbar_init();
     }
+    __syncthreads();
+    if (tid == 0) {
+      mbar_arrive_expect_tx(&S.bar, static_cast<uint32_t>(4 * RN * 4 + (P.accumulate ? TN * 4 : 0)));
+      tma_load_3d(B.u, &umap, &S.bar, x0 - 4, y0 - 1, z0 - 1);
+      tma_load_4d(B.w[0], &wmap, &S.bar, x0 - 4, y0 - 1, z0 - 1, 0);
+      if (P.accumulate) tma_load_3d(B.gu, &gmap, &S.bar, x0, y0, z0);
+    }
+    // one thread polls the barrier; the others sleep in the block barrier below rather than
+    // spend issue slots that the co-resident tiles' arithmetic needs (the barrier orders the
+    // copies' completion, observed by thread 0, before every thread's reads)
+    if (tid == 0) ok = mbar_wait_bounded(&S.bar, 0, P.status);
+  } else {
     for (int k = tid; k < RN; k += blockDim.x) {
       const int rx = k % RX, ry = (k / RX) % RY, rz = k / (RX * RY);
       const int gx = x0 - 4 + rx, gy = y0 - 1 + ry, gz = z0 - 1 + rz;
@@ -92,43 +90,21 @@ __global__ void __launch_bounds__(TN, 2)
 #pragma unroll
       for (int c = 0; c < 3; ++c) B.w[c][k] = in ? P.w[c * nvox + g] : 0.f;
     }
-    {
-      const int gx = x0 + tid % TX, gy = y0 + (tid / TX) % TY, gz = z0 + tid / (TX * TY);
-      const bool in = gx < P.nx && gy < P.ny && gz < P.nz;
-      B.gu[tid] = (in && P.accumulate) ? P.grad_u[(static_cast<int64_t>(gz) * P.ny + gy) * P.nx + gx] : 0.f;
-    }
-  };
-
-  if (tid == 0) {
-    mbar_init(&S.bar[0], 1);
-    mbar_init(&S.bar[1], 1);
-    fence_mbar_init();
+    const int gx = x0 + tid % TX, gy = y0 + (tid / TX) % TY, gz = z0 + tid / (TX * TY);
+    const bool in = gx < P.nx && gy < P.ny && gz < P.nz;
+    B.gu[tid] = (in && P.accumulate) ? P.grad_u[(static_cast<int64_t>(gz) * P.ny + gy) * P.nx + gx] : 0.f;
   }
-  __syncthreads();
-  if (blockIdx.x < n_tiles) stage(blockIdx.x, 0);
+  if (__syncthreads_or(!ok)) {
+    if (tid == 0 && P.use_tma) mbar_wait_bounded(&S.bar, 0, P.status);  // let the copies land before exit
+    return;
+  }
 
   float e_loc = 0.f;
-  int it = 0;
-  for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++it) {
-    const int b = it & 1;
-    // the next tile's copies go into the other buffer, last read before the previous iteration's end barrier
-    if (tile + static_cast<int>(gridDim.x) < n_tiles) stage(tile + gridDim.x, b ^ 1);
-    bool ok = true;
-    if (P.use_tma) ok = mbar_wait_bounded(&S.bar[b], (it >> 1) & 1, P.status);
-    if (__syncthreads_or(!ok)) {
-      if (tid == 0 && P.use_tma) {  // let the copies in flight land before the CTA exits
-        mbar_wait_bounded(&S.bar[b], (it >> 1) & 1, P.status);
-        if (tile + static_cast<int>(gridDim.x) < n_tiles) mbar_wait_bounded(&S.bar[b ^ 1], ((it + 1) >> 1) & 1, P.status);
-      }
-      return;
-    }
-    const TgvBuf& B = S.buf[b];
-    int x0, y0, z0;
-    origin(tile, x0, y0, z0);
-
+  {
     // q and P at tile offsets (-1..TX-1, -1..TY-1, -1..TZ-1); the energy over the tile
     for (int k = tid; k < QN; k += blockDim.x) {
-      const int qx = k % QX, qy = (k / QX) % QY, qz = k / (QX * QY);
+      const int qz = k / (QX * QY), rem = k - qz * (QX * QY);
+      const int qy = rem / QX, qx = rem - qy * QX;
       const int g[3] = {x0 - 1 + qx, y0 - 1 + qy, z0 - 1 + qz};
       const bool in = g[0] >= 0 && g[0] < P.nx && g[1] >= 0 && g[1] < P.ny && g[2] >= 0 && g[2] < P.nz;
       float v[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
@@ -144,14 +120,15 @@ __global__ void __launch_bounds__(TN, 2)
           for (int c = 0; c < 3; ++c) dw[a][c] = fwd ? (B.w[c][r + step[a]] - B.w[c][r]) * inv_d[a] : 0.f;
         }
         const float rx_ = du[0] - B.w[0][r], ry_ = du[1] - B.w[1][r], rz_ = du[2] - B.w[2][r];
-        const float phi1 = sqrtf(fmaf(rx_, rx_, fmaf(ry_, ry_, fmaf(rz_, rz_, P.eps2))));
+        const float f1 = fmaf(rx_, rx_, fmaf(ry_, ry_, fmaf(rz_, rz_, P.eps2)));
+        const float r1 = rsqrtf(f1), phi1 = f1 * r1;
         const float exx = dw[0][0], eyy = dw[1][1], ezz = dw[2][2];
         const float exy = 0.5f * (dw[0][1] + dw[1][0]), exz = 0.5f * (dw[0][2] + dw[2][0]),
                     eyz = 0.5f * (dw[1][2] + dw[2][1]);
         const float f2 = fmaf(exx, exx, fmaf(eyy, eyy, fmaf(ezz, ezz, P.eps2))) +
                          2.f * fmaf(exy, exy, fmaf(exz, exz, eyz * eyz));
-        const float phi2 = sqrtf(f2);
-        const float c1 = P.alpha1 / phi1, c0 = P.alpha0 / phi2;
+        const float r2 = rsqrtf(f2), phi2 = f2 * r2;
+        const float c1 = P.alpha1 * r1, c0 = P.alpha0 * r2;
         v[0] = c1 * rx_;
         v[1] = c1 * ry_;
         v[2] = c1 * rz_;
@@ -192,10 +169,9 @@ __global__ void __launch_bounds__(TN, 2)
         P.grad_w[cb * nvox + g] = gw;
       }
     }
-    __syncthreads();  // qp and this buffer are rewritten by the next iterations
   }
 
-  // this CTA's energy in FP64, fixed order
+  // the tile's energy in FP64, fixed order
   double e = e_loc;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
@@ -204,7 +180,7 @@ __global__ void __launch_bounds__(TN, 2)
   if (tid == 0) {
     double t = 0.0;
     for (int k = 0; k < TN / 32; ++k) t += S.red[k];
-    P.energy_part[blockIdx.x] = t;
+    P.energy_part[(static_cast<int64_t>(blockIdx.z) * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = t;
   }
 }
 
@@ -213,6 +189,8 @@ size_t tgv_smem_bytes() { return sizeof(TgvSmem); }
 int tgv_tiles(int nx, int ny, int nz) {
   return ((nx + TX - 1) / TX) * ((ny + TY - 1) / TY) * ((nz + TZ - 1) / TZ);
 }
+
+dim3 tgv_grid(int nx, int ny, int nz) { return dim3((nx + TX - 1) / TX, (ny + TY - 1) / TY, (nz + TZ - 1) / TZ); }
 
 int tgv_threads() { return TN; }
 
