@@ -260,15 +260,20 @@ int pasfm_nc_scores(pasfm_ctx* ctx, int n_cand, int n_elem, int n_samples, const
                     int dtype_meas, const uint8_t* mask, double* scores_out, void* stream);
 
 /* Stages 2 and 4 support -- gradient of the NC loss of Eq. 3 summed over traces:
- * g_out[r][n] = scale * d(sum_r mask[r] NC(sim_r, meas_r)) / d sim[r][n], with
- * NC = -<s~, m~> / (|s~| |m~|) on the centred traces s~, m~, and nc_out[r] = NC
- * (0 for masked traces and traces of zero variance, whose gradient is 0).  Fed
- * to pasfm_pose_grad as its residual, g gives the element-position and rigid
- * gradients of the NC loss.  sim, g_out: float [n_rows][n_samples] (g_out may
- * alias sim); meas: [n_rows][n_samples] of dtype_meas; mask: uint8 [n_rows] or
- * NULL; nc_out: double [n_rows] or NULL.  Device memory. */
+ * g_out[r][n] = scale * d(sum_r mask[r] NC(sim_r, meas_{r / meas_repeat})) / d sim[r][n],
+ * with NC = -<s~, m~> / (|s~| |m~|) on the centred traces s~, m~, and nc_out[r] = NC
+ * (0 for masked traces and traces of zero variance, whose gradient is 0).  Each
+ * measured trace serves meas_repeat consecutive simulated ones (candidates of one
+ * element).  Fed to pasfm_pose_grad as its residual, g gives the element-position
+ * and rigid gradients of the NC loss.  sim, g_out: float [n_rows][n_samples]
+ * (g_out may alias sim); meas: [n_rows / meas_repeat][n_samples] of dtype_meas;
+ * mask: uint8 [n_rows] or NULL; nc_out: double [n_rows] or NULL.  Device memory. */
 int pasfm_nc_grad(pasfm_ctx* ctx, int64_t n_rows, int n_samples, const float* sim, const void* meas, int dtype_meas,
-                  const uint8_t* mask, double scale, float* g_out, double* nc_out, void* stream);
+                  int meas_repeat, const uint8_t* mask, double scale, float* g_out, double* nc_out, void* stream);
+
+/* A8 support -- x *= alpha over n floats (rescaling a volume estimate when the
+ * Gaussian width or the grid spacing changes).  Device memory. */
+int pasfm_scale(pasfm_ctx* ctx, int64_t n, double alpha, float* x, void* stream);
 
 /* Allocation-free pose gradient.  No counterpart in the paper: this is a
  * library service for callers that must not allocate device memory while they

@@ -85,7 +85,8 @@ _SIGS = {
     "pasfm_resample": ([_VP, _G, _VP, _G, _VP, _VP], _I),
     "pasfm_lowpass": ([_VP, ctypes.c_int64, _I, ctypes.c_double, _I, _VP, _VP, _VP], _I),
     "pasfm_nc_scores": ([_VP, _I, _I, _I, _VP, _VP, _I, _VP, _VP, _VP], _I),
-    "pasfm_nc_grad": ([_VP, ctypes.c_int64, _I, _VP, _VP, _I, _VP, ctypes.c_double, _VP, _VP, _VP], _I),
+    "pasfm_nc_grad": ([_VP, ctypes.c_int64, _I, _VP, _VP, _I, _I, _VP, ctypes.c_double, _VP, _VP, _VP], _I),
+    "pasfm_scale": ([_VP, ctypes.c_int64, ctypes.c_double, _VP, _VP], _I),
     "pasfm_pose_grad_noalloc": ([_G, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP], _I),
     "pasfm_status": ([_VP, _VP, ctypes.POINTER(ctypes.c_uint32)], _I),
     "pasfm_timing_enable": ([_VP, _I], _I),
@@ -373,18 +374,27 @@ class Context:
                                    _stream(stream, self.device)))
         return out
 
-    def nc_grad(self, sim, meas, mask=None, scale=1.0, out=None, stream=None):
-        """Gradient of the summed NC loss (Eq. 3) w.r.t. sim [..., Nt] (rows paired with
-        meas rows; mask per row or None) and the per-row NC values."""
+    def nc_grad(self, sim, meas, mask=None, scale=1.0, out=None, stream=None, meas_repeat=1):
+        """Gradient of the summed NC loss (Eq. 3) w.r.t. sim [..., Nt] and the per-row NC
+        values; sim row r is paired with meas row r // meas_repeat; mask per sim row or None."""
         T = int(sim.shape[-1])
         rows = sim.numel() // T if sim.numel() else 0
+        if meas.numel() // max(T, 1) * int(meas_repeat) != rows:
+            raise ValueError("meas must hold one trace per meas_repeat rows of sim")
         out = torch.empty_like(sim) if out is None else out
         nc = torch.zeros(sim.shape[:-1], dtype=torch.float64, device=self.device)
         _check(lib().pasfm_nc_grad(self.handle, int(rows), T, _ptr(sim, torch.float32, "sim"), _ptr(meas, _VOL, "meas"),
-                                   _DTYPE_CODE[meas.dtype], _ptr(mask, torch.uint8, "mask", allow_none=True),
-                                   float(scale), _ptr(out, torch.float32, "out"), _ptr(nc, torch.float64, "nc"),
+                                   _DTYPE_CODE[meas.dtype], int(meas_repeat),
+                                   _ptr(mask, torch.uint8, "mask", allow_none=True), float(scale),
+                                   _ptr(out, torch.float32, "out"), _ptr(nc, torch.float64, "nc"),
                                    _stream(stream, self.device)))
         return out, nc
+
+    def scale(self, x, alpha, stream=None):
+        """x *= alpha in place (float32 device tensor)."""
+        _check(lib().pasfm_scale(self.handle, int(x.numel()), float(alpha), _ptr(x, torch.float32, "x"),
+                                 _stream(stream, self.device)))
+        return x
 
     def nc_scores(self, sim, meas, mask=None, out=None, stream=None):
         """NC-loss scores of candidate trace sets sim [K][E][Nt] against meas [E][Nt]."""

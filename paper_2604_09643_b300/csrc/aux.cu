@@ -408,6 +408,12 @@ namespace pasfm {
 // dst[n] = sum_k w_k src[n + k], |k| <= r, w_k ~ exp(-k^2 / (2 sigma^2)) summing
 // to 1, samples outside the record taken as zero.  One block per trace; the
 // trace is staged in shared memory, so dst may alias src.
+__global__ void __launch_bounds__(256) scale_kernel(float* __restrict__ x, int64_t n, float alpha) {
+  for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    x[i] *= alpha;
+}
+
 __global__ void __launch_bounds__(256) sum_parts_kernel(const float* __restrict__ parts, int n_parts, int64_t nvox,
                                                         float* __restrict__ vol, int accumulate) {
   for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < nvox;
@@ -498,11 +504,14 @@ __global__ void __launch_bounds__(256) nc_scores_kernel(const float* __restrict_
 // g may alias sim: each lane reads s_n before writing g_n at the same n.
 __global__ void __launch_bounds__(256) nc_grad_kernel(const float* sim, const void* meas, int dtype,
                                                       const uint8_t* __restrict__ mask, int64_t n_rows, int Nt,
-                                                      float scale, float* g, double* __restrict__ nc_out) {
+                                                      int meas_repeat, float scale, float* g,
+                                                      double* __restrict__ nc_out) {
   const int lane = threadIdx.x & 31;
   const int64_t row = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (row >= n_rows) return;
   const int64_t base = row * Nt;
+  const int64_t mrow = row / meas_repeat;  // measured trace paired with this simulated one
+  const int64_t mbase = mrow * Nt;
   const bool keep = !mask || mask[row];
   auto warp_sum = [](double v) {
 #pragma unroll
@@ -514,14 +523,14 @@ __global__ void __launch_bounds__(256) nc_grad_kernel(const float* sim, const vo
     float a = 0.f, b = 0.f;
     for (int n = lane; n < Nt; n += 32) {
       a += sim[base + n];
-      b += load_elem(meas, base + n, dtype);
+      b += load_elem(meas, mbase + n, dtype);
     }
     s_mean = warp_sum(a) / Nt;
     m_mean = warp_sum(b) / Nt;
     const float sm = static_cast<float>(s_mean), mm = static_cast<float>(m_mean);
     float ss = 0.f, qq = 0.f, sq = 0.f;
     for (int n = lane; n < Nt; n += 32) {
-      const float x = sim[base + n] - sm, y = load_elem(meas, base + n, dtype) - mm;
+      const float x = sim[base + n] - sm, y = load_elem(meas, mbase + n, dtype) - mm;
       ss = fmaf(x, x, ss);
       qq = fmaf(y, y, qq);
       sq = fmaf(x, y, sq);
@@ -536,7 +545,7 @@ __global__ void __launch_bounds__(256) nc_grad_kernel(const float* sim, const vo
   const float cm = live ? static_cast<float>(-scale / (nm * ns)) : 0.f;
   const float cs = live ? static_cast<float>(scale * rho / (ns * ns)) : 0.f;
   for (int n = lane; n < Nt; n += 32) {
-    const float x = sim[base + n] - sm, y = load_elem(meas, base + n, dtype) - mm;
+    const float x = sim[base + n] - sm, y = load_elem(meas, mbase + n, dtype) - mm;
     g[base + n] = fmaf(cm, y, cs * x);
   }
   if (lane == 0 && nc_out) nc_out[row] = live ? -rho : 0.0;

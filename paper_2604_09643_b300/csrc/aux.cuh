@@ -36,7 +36,8 @@ __global__ void resample_kernel(const float* src, int sx, int sy, int sz, double
 __global__ void lowpass_kernel(const float* src, float* dst, int Nt, int r, int decim, int Nout, const float* w);
 
 __global__ void nc_grad_kernel(const float* sim, const void* meas, int dtype, const uint8_t* mask, int64_t n_rows,
-                               int Nt, float scale, float* g, double* nc_out);
+                               int Nt, int meas_repeat, float scale, float* g, double* nc_out);
+__global__ void scale_kernel(float* x, int64_t n, float alpha);
 __global__ void nc_scores_kernel(const float* sim, const void* meas, int dtype, const uint8_t* mask, int E, int Nt,
                                  double* out);
 

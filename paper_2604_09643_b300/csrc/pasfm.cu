@@ -1016,9 +1016,10 @@ int pasfm_nc_scores(pasfm_ctx* ctx, int n_cand, int n_elem, int n_samples, const
 }
 
 int pasfm_nc_grad(pasfm_ctx* ctx, int64_t n_rows, int n_samples, const float* sim, const void* meas, int dtype_meas,
-                  const uint8_t* mask, double scale, float* g_out, double* nc_out, void* stream) {
+                  int meas_repeat, const uint8_t* mask, double scale, float* g_out, double* nc_out, void* stream) {
   if (!ctx) return fail(PASFM_EINVAL, "ctx is NULL");
   if (n_rows < 0 || n_samples < 0 || !std::isfinite(scale)) return fail(PASFM_EINVAL, "bad size or scale");
+  if (meas_repeat < 1) return fail(PASFM_EINVAL, "meas_repeat must be >= 1");
   if (dtype_meas != PASFM_F32 && dtype_meas != PASFM_BF16 && dtype_meas != PASFM_F16)
     return fail(PASFM_EINVAL, "unknown dtype %d", dtype_meas);
   if (n_rows == 0 || n_samples == 0) return PASFM_OK;
@@ -1028,9 +1029,23 @@ int pasfm_nc_grad(pasfm_ctx* ctx, int64_t n_rows, int n_samples, const float* si
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   cudaEvent_t t = ctx->begin(st);
   nc_grad_kernel<<<static_cast<unsigned>((n_rows + 7) / 8), 256, 0, st>>>(
-      sim, meas, dtype_meas, mask, n_rows, n_samples, static_cast<float>(scale), g_out, nc_out);
+      sim, meas, dtype_meas, mask, n_rows, n_samples, meas_repeat, static_cast<float>(scale), g_out, nc_out);
   ctx->end("nc_grad", t, st);
   return check_launch("nc_grad");
+}
+
+int pasfm_scale(pasfm_ctx* ctx, int64_t n, double alpha, float* x, void* stream) {
+  if (!ctx) return fail(PASFM_EINVAL, "ctx is NULL");
+  if (n < 0 || !std::isfinite(alpha)) return fail(PASFM_EINVAL, "bad size or factor");
+  if (n == 0) return PASFM_OK;
+  if (!x) return fail(PASFM_EINVAL, "NULL array argument");
+  TRY(set_device(ctx));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaEvent_t t = ctx->begin(st);
+  scale_kernel<<<static_cast<unsigned>(std::min<int64_t>((n + 255) / 256, 148 * 32)), 256, 0, st>>>(
+      x, n, static_cast<float>(alpha));
+  ctx->end("scale", t, st);
+  return check_launch("scale");
 }
 
 int pasfm_status(pasfm_ctx* ctx, void* stream, uint32_t* bits) {

@@ -292,7 +292,8 @@ def reconstruct(ctx: binding.Context, geom_fine, elem, meas, poses_init, cfg: C2
         else:
             p0 = ctx.resample(prev_geom, p0, geom)
             if gauss:
-                p0 *= gauss_amplitude_factor(prev_geom["sigma_mm"], prev_geom["dx"], geom["sigma_mm"], geom["dx"])
+                ctx.scale(p0, gauss_amplitude_factor(prev_geom["sigma_mm"], prev_geom["dx"], geom["sigma_mm"],
+                                                     geom["dx"]))
         if gauss:
             # a Gaussian pulse of width s low-passed by a Gaussian of width t is one of width sqrt(s^2 + t^2)
             sigma = (cfg.lowpass[li] if cfg.lowpass is not None
@@ -330,7 +331,7 @@ def reconstruct(ctx: binding.Context, geom_fine, elem, meas, poses_init, cfg: C2
                 # next, narrower width: keep the represented field, band-limit the data to match
                 w_new = widths[min(k // phase_len, len(widths) - 1)]
                 if w_new != geom["sigma_mm"]:
-                    p0 *= gauss_amplitude_factor(geom["sigma_mm"], geom["dx"], w_new, geom["dx"])
+                    ctx.scale(p0, gauss_amplitude_factor(geom["sigma_mm"], geom["dx"], w_new, geom["dx"]))
                     geom = dict(geom, sigma_mm=w_new)
                     lp = (gauss_lowpass_samples(w_new, geom_fine["sigma_mm"], h, decim)
                           if cfg.lowpass is None else cfg.lowpass[li])

@@ -97,9 +97,10 @@ def stage1_reference(ctx, geom, elem_d, meas_a, pose_a, cfg, p0=None):
     return p0
 
 
-def _nc_rows(ctx, geom, p0, points, meas_rows, sigma):
-    """NC loss of elements placed at `points` against `meas_rows` (already band-limited
-    by `sigma`) and its gradient in the element positions."""
+def _nc_rows(ctx, geom, p0, points, meas_rows, sigma, repeat):
+    """NC loss of elements placed at `points` against the measured traces `meas_rows`
+    (already band-limited by `sigma`; each serves `repeat` consecutive points) and its
+    gradient in the element positions."""
     dev = ctx.device
     g1 = _points_geom(geom, len(points))
     pts = _T(points, dev)
@@ -107,7 +108,7 @@ def _nc_rows(ctx, geom, p0, points, meas_rows, sigma):
     sim = ctx.forward(g1, p0, pts, ident)
     if sigma > 0:
         sim = ctx.lowpass(sim, sigma)
-    g, nc = ctx.nc_grad(sim, meas_rows)
+    g, nc = ctx.nc_grad(sim, meas_rows, meas_repeat=repeat)
     if sigma > 0:
         g = ctx.lowpass(g, sigma)  # the Gaussian low-pass is self-adjoint
     _, G = ctx.pose_grad(g1, p0, pts, ident, g, want_elem=True)
@@ -131,11 +132,10 @@ def stage2_localise(ctx, geom, p0, elem, pose_b0, meas_b, cfg):
     for j0 in range(0, E, cfg.element_batch):
         js = np.arange(j0, min(E, j0 + cfg.element_batch))
         pts = (prior[js, None, :] + offs[None, :, :]).reshape(-1, 3)
-        rows = meas_s0[js].repeat_interleave(K, dim=0).contiguous()
         sim = ctx.forward(_points_geom(geom, len(pts)), p0, _T(pts, dev), ident)
         if s0 > 0:
             sim = ctx.lowpass(sim, s0)
-        _, nc = ctx.nc_grad(sim, rows)
+        _, nc = ctx.nc_grad(sim, meas_s0[j0:j0 + len(js)], meas_repeat=K)
         nc = nc.reshape(len(js), K).cpu().numpy()
         best = np.argsort(nc, axis=1, kind="stable")[:, :cfg.top_k]
         top[js] = pts.reshape(len(js), K, 3)[np.arange(len(js))[:, None], best]
@@ -149,18 +149,16 @@ def stage2_localise(ctx, geom, p0, elem, pose_b0, meas_b, cfg):
     k = 0
     for si, sig in enumerate(cfg.smoothing):
         meas_s = ctx.lowpass(meas_b, sig) if sig > 0 else meas_b
-        rows = meas_s.repeat_interleave(cfg.top_k, dim=0).contiguous()
         n_steps = min(phase, cfg.refine_steps - si * phase)
         for _ in range(max(0, n_steps)):
-            nc, gx = _nc_rows(ctx, geom, p0, X, rows, sig)
+            nc, gx = _nc_rows(ctx, geom, p0, X, meas_s, sig, cfg.top_k)
             gx = gx.cpu().numpy()
             k += 1
             m = b1 * m + (1 - b1) * gx
             v = b2 * v + (1 - b2) * gx * gx
             X -= cfg.refine_lr_mm * (m / (1 - b1 ** k)) / (np.sqrt(v / (1 - b2 ** k)) + 1e-12)
     # final scores at the unsmoothed level, best prior per element
-    rows = meas_b.repeat_interleave(cfg.top_k, dim=0).contiguous()
-    nc, _ = _nc_rows(ctx, geom, p0, X, rows, 0.0)
+    nc, _ = _nc_rows(ctx, geom, p0, X, meas_b, 0.0, cfg.top_k)
     nc = nc.cpu().numpy().reshape(E, cfg.top_k)
     pick = np.argmin(nc, axis=1)
     Xe = X.reshape(E, cfg.top_k, 3)[np.arange(E), pick]

@@ -146,3 +146,20 @@ def test_nc_grad_matches_oracle(cuda_device):
     assert np.abs(nc - ref_nc).max() < 1e-6
     assert not g[3].any() and nc[3] == 0.0
     assert np.array_equal(alias.cpu().numpy(), g)
+
+
+def test_nc_grad_pairs_each_measured_trace_with_repeated_candidates(cuda_device):
+    from oracle import nc as ncmod
+    rng = np.random.default_rng(13)
+    E, K, T = 5, 7, 300
+    meas = rng.standard_normal((E, T)).astype(np.float32)
+    sim = (0.5 * np.repeat(meas, K, axis=0) + rng.standard_normal((E * K, T))).astype(np.float32)
+    with binding.Context(0) as ctx:
+        d = lambda a: torch.tensor(a, device="cuda")
+        g, nc = ctx.nc_grad(d(sim), d(meas), meas_repeat=K)
+        x = d(sim[0].copy())
+        ctx.scale(x, -2.5)
+    ref = np.stack([ncmod.nc_grad(sim[r], meas[r // K]) for r in range(E * K)])
+    assert rel_l2(g.cpu().numpy(), ref) < 1e-5
+    assert np.abs(nc.cpu().numpy() - [ncmod.nc(sim[r], meas[r // K]) for r in range(E * K)]).max() < 1e-6
+    assert np.array_equal(x.cpu().numpy(), (sim[0] * np.float32(-2.5)).astype(np.float32))
