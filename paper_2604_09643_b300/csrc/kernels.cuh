@@ -428,7 +428,12 @@ __global__ void __launch_bounds__(C* C, (C == 16 ? 2 : 8))
           const float Ec = exp2f(P.gs.c1 * (bc * bc));
           float up = exp2f(fmaf(bc, P.gs.c2, P.gs.c3));
           float dn = exp2f(fmaf(-bc, P.gs.c2, P.gs.c3));
+          // With u_s = E_s dg_s and beta_s = bc + (s - kc) h, the boundary-motion sum
+          // S2 = sum_s beta_s u_s over the boundaries inside the support is
+          // bc sum_s u_s + h sum_s (s - kc) u_s; boundary S-1 (possibly past the edge,
+          // where it does not move with d) is added on its own.
           float E = Ec, gp = gw[kc - 1];
+          float U = 0.f, T = 0.f, last = 0.f;  // sum u, sum (s - kc) u over boundaries < S-1
           S1 = 0.f;
 #pragma unroll
           for (int s = kc; s < S; ++s) {
@@ -439,12 +444,19 @@ __global__ void __launch_bounds__(C* C, (C == 16 ? 2 : 8))
             const float gs = gw[s];
             const float dg = gs - gp;
             gp = gs;
-            const float Es = (s == S - 1) ? fmaxf(E, P.gs.e_clamp) : E;
-            S1 = fmaf(Es, dg, S1);
-            if (POSE) {
-              const float beta = fmaf(static_cast<float>(s - 1), P.h, m.beta1);
-              const float D = (s == S - 1) ? (beta < P.supf ? beta * Es : 0.f) : beta * Es;
-              S2 = fmaf(D, dg, S2);
+            if (s == S - 1) {
+              const float Es = fmaxf(E, P.gs.e_clamp);
+              S1 = fmaf(Es, dg, S1);
+              if (POSE) {
+                const float beta = fmaf(static_cast<float>(s - 1), P.h, m.beta1);
+                last = beta < P.supf ? beta * Es * dg : 0.f;
+              }
+            } else if (POSE) {
+              const float u = E * dg;
+              U += u;
+              if (s != kc) T = fmaf(static_cast<float>(s - kc), u, T);
+            } else {
+              S1 = fmaf(E, dg, S1);
             }
           }
           const float g_last = gp;
@@ -457,8 +469,17 @@ __global__ void __launch_bounds__(C* C, (C == 16 ? 2 : 8))
             const float gs = gw[s - 1];
             const float dg = gn - gs;
             gn = gs;
-            S1 = fmaf(E, dg, S1);
-            if (POSE) S2 = fmaf(fmaf(static_cast<float>(s - 1), P.h, m.beta1) * E, dg, S2);
+            if (POSE) {
+              const float u = E * dg;
+              U += u;
+              T = fmaf(static_cast<float>(s - kc), u, T);
+            } else {
+              S1 = fmaf(E, dg, S1);
+            }
+          }
+          if (POSE) {
+            S1 += U;
+            S2 = fmaf(bc, U, fmaf(P.h, T, last));
           }
           S1 = fmaf(P.gs.e_clamp, gn - g_last, S1);
           lam = P.lam;
