@@ -185,7 +185,12 @@ __global__ void __launch_bounds__(256, 2)
   // 5. pair loop: every voxel of the cube against this lane's element
   const unsigned max_idx = static_cast<unsigned>(P.W - S);
   const int idx_bias = kMagicBits + nb_rel;
-  unsigned seen = 0;  // largest raw index (a negative one wraps to a huge value)
+  // Clamp detection.  A voxel's distance to the element is convex along a row, and the
+  // first slot index grows with the distance, so a row's largest index is at one of its
+  // two ends: those are the only pairs checked.  (The window covers the cube's
+  // distance range with half a sample to spare, so no index is clamped unless the
+  // geometry is degenerate; the clamp itself is applied to every pair.)
+  unsigned seen = 0;  // largest raw index at the row ends (a negative one wraps to a huge value)
   for (int lz = 0; lz < C; ++lz) {
     const float qz = (lz - 0.5f * (C - 1)) * dzf;
     const float Cz = qz * (qz + R.m2uz);
@@ -201,7 +206,7 @@ __global__ void __launch_bounds__(256, 2)
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           const PairMath m = pair_math(Pix[i4 + u] + Crow, R.dc2, R.dcf, R.phim, P.inv_hf, P.h, P.cb1, idx_bias);
-          seen = max(seen, m.idx);
+          if (i4 + u == 0 || i4 + u == C - 1) seen = max(seen, m.idx);
           float* slot = col + min(m.idx, max_idx) * kWarp;
           const float s = pv[u] * m.rs;
           if constexpr (K == PASFM_KERNEL_GAUSS) {
@@ -399,7 +404,7 @@ __global__ void __launch_bounds__(C* C, (C == 16 ? 2 : 8))
   // refs[buf] ahead of its producer writes.  A timed-out wait makes every
   // thread skip the compute, and the barrier (an OR vote) ends the CTA.
   const unsigned max_idx = static_cast<unsigned>(WP - S);
-  unsigned seen = 0;  // largest raw window index (a negative one wraps to a huge value)
+  unsigned seen = 0;  // largest raw window index at the row ends (see fwd_cube_kernel)
   for (int b = 0; b < nb; ++b) {
     const int buf = b & 1;
     const bool ok = mbar_wait_bounded(&bar[buf], (b >> 1) & 1, P.status);
@@ -416,7 +421,7 @@ __global__ void __launch_bounds__(C* C, (C == 16 ? 2 : 8))
       for (int k = 0; k < C; ++k) {
         const float A = fmaf(qx[k], qx[k] + ra.x, Crow);
         const PairMath m = pair_math(A, ra.w, rb.x, rb.y, P.inv_hf, P.h, P.cb1, idx_bias);
-        seen = max(seen, m.idx);
+        if (k == 0 || k == C - 1) seen = max(seen, m.idx);
         const float* gw = wv + min(m.idx, max_idx);
         // S1 = sum_k g_k (b_k - b_{k+1}) by parts; S2 = the boundary-motion term of dW/dd
         float S1, S2 = 0.f, lam;
