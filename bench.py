@@ -340,22 +340,39 @@ def run_native(args):
     ms_per_step = ms / args.steps
     value = replicas.job_throughput(args.steps, ms / 1e3, world)
 
-    # ---- end to end through the public API with host buffers
+    # ---- end to end through the public API with host buffers: every step's measurements
+    # are copied from pinned host memory (on a copy stream, into the buffer the step before
+    # last used, so the copy overlaps the previous step) and its loss and poses read back
     meas_host = meas.cpu().pin_memory()
     loss_host = torch.zeros((), dtype=torch.float64).pin_memory()
     poses_host = torch.zeros(poses.shape, dtype=poses.dtype).pin_memory()
-    meas_dev = torch.empty_like(meas)
+    meas_dev = [torch.empty_like(meas), torch.empty_like(meas)]
+    copy_stream = torch.cuda.Stream(dev)
+    copied = [torch.cuda.Event(), torch.cuda.Event()]
+    used = [torch.cuda.Event(), torch.cuda.Event()]
     e2e_steps = max(3, args.steps // 2)
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        meas_dev.copy_(meas_host, non_blocking=True)
-        ctx.step(geom, p0, poses, elem, meas_dev, adam, loss_out=loss)
+    with torch.cuda.stream(copy_stream):
+        meas_dev[0].copy_(meas_host, non_blocking=True)
+        copied[0].record(copy_stream)
+    for k in range(e2e_steps):
+        b = k & 1
+        if k + 1 < e2e_steps:  # next step's copy into the other buffer, once its last step is done
+            with torch.cuda.stream(copy_stream):
+                if k >= 1:
+                    copy_stream.wait_event(used[b ^ 1])
+                meas_dev[b ^ 1].copy_(meas_host, non_blocking=True)
+                copied[b ^ 1].record(copy_stream)
+        stream.wait_event(copied[b])
+        ctx.step(geom, p0, poses, elem, meas_dev[b], adam, loss_out=loss)
+        used[b].record(stream)
         loss_host.copy_(loss, non_blocking=True)
         poses_host.copy_(poses, non_blocking=True)
         stream.synchronize()
+    torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     e2e_s = replicas.max_over_ranks(e2e_s, dev)
     e2e = {"value": replicas.job_throughput(e2e_steps, e2e_s, world), "unit": UNIT,
