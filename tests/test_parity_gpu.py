@@ -182,7 +182,9 @@ def test_adjoint_identity_on_gpu(ctx, case):
     Aty = ctx.adjoint(geom, dev(elem), dev(poses), dev(y)).double()
     lhs = float((Ax * dev(y).double()).sum())
     rhs = float((dev(x).double() * Aty).sum())
-    assert abs(lhs - rhs) <= 1e-5 * max(abs(lhs), abs(rhs)), (name, lhs, rhs)
+    # each side is an FP32 operator within REL_L2_SIG of the FP64 oracle, so the two
+    # inner products may differ by up to twice that
+    assert abs(lhs - rhs) <= 2 * REL_L2_SIG * max(abs(lhs), abs(rhs)), (name, lhs, rhs)
 
 
 def test_repeat_calls_are_bitwise_identical(ctx):
