@@ -86,11 +86,14 @@ KERNEL_SOURCES = {
 
 
 def kernel_src_hash(kernel="bwd_cube"):
-    """Hash of the sources that define `kernel` (a KERNEL_SOURCES key, '_gauss' suffix ignored)."""
+    """Hash of the sources that define `kernel` (a KERNEL_SOURCES key, '_gauss' suffix ignored)
+    and of the build script that holds their compiler flags."""
     h = hashlib.sha256()
     for fn in KERNEL_SOURCES[kernel.replace("_gauss", "")]:
         with open(os.path.join(ROOT, "paper_2604_09643_b300", "csrc", fn), "rb") as fh:
             h.update(fh.read())
+    with open(os.path.join(ROOT, "paper_2604_09643_b300", "build.py"), "rb") as fh:
+        h.update(fh.read())
     return h.hexdigest()[:16]
 
 

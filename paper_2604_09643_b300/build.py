@@ -40,7 +40,7 @@ def _flags():
 
 
 def _sources():
-    return glob.glob(os.path.join(CSRC, "*")) + [os.path.join(ROOT, "include", "pasfm.h")]
+    return glob.glob(os.path.join(CSRC, "*")) + [os.path.join(ROOT, "include", "pasfm.h"), os.path.abspath(__file__)]
 
 
 def _stale() -> bool:
@@ -65,11 +65,14 @@ def build(force: bool = False, jobs: int | None = None, verbose: bool = False) -
         return LIB
     os.makedirs(OBJ, exist_ok=True)
     os.makedirs(os.path.dirname(LIB), exist_ok=True)
+    # The hot kernels flush FP32 subnormals to zero: none of their quantities comes near
+    # 1e-38, and without it rsqrtf, __fdividef and exp2f each carry extra instructions to
+    # handle subnormal operands (measured: 10-17% of the forward and backward time).
     work = [(os.path.join(CSRC, "kernels_s.cu"), os.path.join(OBJ, f"kernels_k{k}_s{s}.o"),
-             [f"-DPASFM_K={k}", f"-DPASFM_S={s}"]) for k, s in KS_VALUES]
+             [f"-DPASFM_K={k}", f"-DPASFM_S={s}", "-ftz=true"]) for k, s in KS_VALUES]
     work += [(os.path.join(CSRC, "aux.cu"), os.path.join(OBJ, "aux.o"), []),
              (os.path.join(CSRC, "launchers.cu"), os.path.join(OBJ, "launchers.o"), []),
-             (os.path.join(CSRC, "tgv.cu"), os.path.join(OBJ, "tgv.o"), []),
+             (os.path.join(CSRC, "tgv.cu"), os.path.join(OBJ, "tgv.o"), ["-ftz=true"]),
              (os.path.join(CSRC, "pasfm.cu"), os.path.join(OBJ, "pasfm.o"), []),
              (os.path.join(CSRC, "noalloc.cu"), os.path.join(OBJ, "noalloc.o"), [])]
     jobs = jobs or max(1, min(len(work), os.cpu_count() or 1))
