@@ -488,7 +488,35 @@ __global__ void __launch_bounds__(C* C, (C == 16 ? 2 : 8))
           }
           S1 = fmaf(P.gs.e_clamp, gn - g_last, S1);
           lam = P.lam;
-        } else {
+        } else if constexpr (S >= 3) {
+          // Sphere, b_s = beta_s^2 on the interior boundaries s = 1..n (n = S - 2,
+          // beta_s = beta1 + (s - 1) h), b_{S-1} = min(beta_{S-1}, a0)^2, b_0 = b_S = a0^2.
+          // Summation by parts turns the interior sums into three fixed combinations of
+          // the window values, M_p = sum_s (s - 1)^p dg_s (p = 0, 1, 2):
+          //   S1 = a0^2 (g_0 - g_{S-1}) + beta1^2 M0 + 2 h beta1 M1 + h^2 M2 + b_{S-1} dg_{S-1},
+          //   S2 = -(beta1 M0 + h M1) - D dg_{S-1},  D = beta_{S-1} inside the support, else 0,
+          // which costs about a third fewer instructions than a boundary-by-boundary sum.
+          float g[S];
+#pragma unroll
+          for (int s = 0; s < S; ++s) g[s] = gw[s];
+          constexpr int n = S - 2;
+          const float M0 = g[n] - g[0];
+          float M1 = static_cast<float>(n - 1) * g[n], M2 = static_cast<float>((n - 1) * (n - 1)) * g[n];
+#pragma unroll
+          for (int s = 1; s <= n - 1; ++s) {
+            M1 -= g[s];
+            M2 = fmaf(-static_cast<float>(2 * s - 1), g[s], M2);
+          }
+          const float dgl = g[S - 1] - g[n];
+          const float b1 = m.beta1;
+          const float bl = fmaf(static_cast<float>(S - 2), P.h, b1);  // beta_{S-1}
+          const float tl = fminf(bl, P.supf);
+          const float X = fmaf(P.h, M1, b1 * M0);  // sum of beta_s dg_s over the interior
+          if (POSE) S2 = -fmaf(bl < P.supf ? bl : 0.f, dgl, X);
+          const float Y = fmaf(P.h, M1, X);        // beta1 M0 + 2 h M1
+          S1 = fmaf(b1, Y, fmaf(P.h * P.h, M2, fmaf(fmaf(tl, tl, -P.sup2), dgl, -P.sup2 * M0)));
+          lam = 2.f;
+        } else {  // S = 2: boundary 1 is the clamped one
           float g[S];
 #pragma unroll
           for (int s = 0; s < S; ++s) g[s] = gw[s];

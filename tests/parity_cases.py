@@ -83,3 +83,11 @@ def gaussian(case, sigma):
         geom, p0, elem, poses = case(*a, **kw)
         return dict(geom, kernel="gauss", sigma_mm=float(sigma)), p0, elem, poses
     return make
+
+
+def sphere(case, a0):
+    """The same inputs with a uniform-sphere voxel of radius ``a0`` (mm)."""
+    def make(*a, **kw):
+        geom, p0, elem, poses = case(*a, **kw)
+        return dict(geom, a0_mm=float(a0)), p0, elem, poses
+    return make
