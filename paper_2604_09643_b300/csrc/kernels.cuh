@@ -7,9 +7,11 @@
 //                       column of a shared-memory time window laid out
 //                       [slot][32 lanes], so any per-lane offset is
 //                       bank-conflict free and no atomics are needed.  The
-//                       window (the cube's distance range for that element) is
-//                       flushed as a per-cube partial trace; fwd_reduce_kernel
-//                       sums the partials in a fixed order.
+//                       window (the cube's distance range for that element)
+//                       holds the running sum of the slot weights, so a pair
+//                       writes S - 1 slots (its weights sum to zero; S >= 3); the
+//                       flush differences it into a per-cube partial trace and
+//                       fwd_reduce_kernel sums the partials in a fixed order.
 //   bwd_cube_kernel  -- adjoint v = A^T g and/or pose gradient.  Voxel-
 //                       stationary: a thread owns a row of C voxels along x; the
 //                       CTA walks all (frame, element) traces in batches of 32
@@ -209,31 +211,39 @@ __global__ void __launch_bounds__(256, 2)
           if (i4 + u == 0 || i4 + u == C - 1) seen = max(seen, m.idx);
           float* slot = col + min(m.idx, max_idx) * kWarp;
           const float s = pv[u] * m.rs;
-          if constexpr (K == PASFM_KERNEL_GAUSS) {
+          // The pair's slot weights b_k - b_{k+1} (k = 0..S-1) sum to b_0 - b_S = 0, so
+          // for S >= 3 the window holds their running sum: slot k gets b_0 - b_{k+1} for
+          // k = 0..S-2 and slot S-1 gets nothing.  That is S - 1 read-modify-writes
+          // instead of S through shared memory, which bounds this loop; the flush takes
+          // the first difference.  Sphere: b_0 = a0^2, b_k = beta_k^2 inside, the last
+          // boundary clamped.  Gaussian: b = -E, b_0 = -E(edge).  At S = 2 (a pulse
+          // narrower than a sample) every pair is a +-w dipole on two slots; the running
+          // sum would then hold two separately accumulated sums per sample whose
+          // difference cancels in homogeneous regions, so the weights go in directly.
+          if constexpr (S == 2) {
+            float w;
+            if constexpr (K == PASFM_KERNEL_GAUSS) {
+              float E[S];
+              gauss_boundaries<S>(m.beta1, P.h, P.gs, E);
+              w = E[1] - P.gs.e_clamp;
+            } else {
+              const float bc = fminf(m.beta1, P.supf);
+              w = fmaf(-bc, bc, P.sup2);
+            }
+            slot[0] = fmaf(s, w, slot[0]);
+            slot[kWarp] = fmaf(-s, w, slot[kWarp]);
+          } else if constexpr (K == PASFM_KERNEL_GAUSS) {
             float E[S];
             gauss_boundaries<S>(m.beta1, P.h, P.gs, E);
-            float eprev = P.gs.e_clamp;
 #pragma unroll
-            for (int k = 0; k < S; ++k) {
-              const float ek = (k == S - 1) ? P.gs.e_clamp : E[k + 1];
-              slot[k * kWarp] = fmaf(s, ek - eprev, slot[k * kWarp]);
-              eprev = ek;
-            }
+            for (int k = 0; k <= S - 2; ++k) slot[k * kWarp] = fmaf(s, E[k + 1] - P.gs.e_clamp, slot[k * kWarp]);
           } else {
             float beta = m.beta1;
-            float bprev = P.sup2;
 #pragma unroll
-            for (int k = 0; k < S; ++k) {
-              float bk;
-              if (k == S - 1) {
-                bk = P.sup2;
-              } else {
-                if (k > 0) beta += P.h;
-                const float bc = (k == S - 2) ? fminf(beta, P.supf) : beta;
-                bk = bc * bc;
-              }
-              slot[k * kWarp] = fmaf(s, bprev - bk, slot[k * kWarp]);
-              bprev = bk;
+            for (int k = 0; k <= S - 2; ++k) {
+              if (k > 0) beta += P.h;
+              const float bc = (k == S - 2) ? fminf(beta, P.supf) : beta;
+              slot[k * kWarp] = fmaf(s, fmaf(-bc, bc, P.sup2), slot[k * kWarp]);
             }
           }
         }
@@ -242,17 +252,26 @@ __global__ void __launch_bounds__(256, 2)
   }
   if (seen > max_idx) atomicOr(P.status, PASFM_STATUS_INDEX_CLAMPED);
 
-  // 6. flush the window as this cube's partial trace (scaled by 1 / (4 h), or sigma^2 / (2 h))
+  // 6. flush the window (its first difference for S >= 3) as this cube's partial trace
+  //    (scaled by 1 / (4 h), or sigma^2 / (2 h))
   __syncwarp();
   if (valid) {
     const int64_t row = static_cast<int64_t>(fl) * P.E + j;
     float* dst = P.part + (row * ncubes + c) * P.W;
+    float prev = 0.f;
     for (int k = 0; k < P.W; k += 4) {
+      const float c0 = col[(k + 0) * kWarp], c1 = col[(k + 1) * kWarp], c2 = col[(k + 2) * kWarp],
+                  c3 = col[(k + 3) * kWarp];
       float4 v;
-      v.x = col[(k + 0) * kWarp] * P.p0_scale;
-      v.y = col[(k + 1) * kWarp] * P.p0_scale;
-      v.z = col[(k + 2) * kWarp] * P.p0_scale;
-      v.w = col[(k + 3) * kWarp] * P.p0_scale;
+      if constexpr (S >= 3) {
+        v.x = (c0 - prev) * P.p0_scale;
+        v.y = (c1 - c0) * P.p0_scale;
+        v.z = (c2 - c1) * P.p0_scale;
+        v.w = (c3 - c2) * P.p0_scale;
+        prev = c3;
+      } else {
+        v = make_float4(c0 * P.p0_scale, c1 * P.p0_scale, c2 * P.p0_scale, c3 * P.p0_scale);
+      }
       *reinterpret_cast<float4*>(dst + k) = v;
     }
     P.n0tab[row * ncubes + c] = R.Nc + nb_rel;
