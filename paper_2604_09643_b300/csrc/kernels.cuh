@@ -400,6 +400,7 @@ __global__ void __launch_bounds__(C* C, (C == 16 ? 2 : 8))
       }
     }
     if (P.use_tma) {
+      __syncwarp();  // the warp's reference writes happen before lane 0's (releasing) arrival
       if (lane == 0) mbar_arrive_expect_tx(&bar[buf], static_cast<uint32_t>(cnt * WP * 4));
       __syncwarp();
       if (it < ib + nl) tma_load_2d(wdst, &gmap, &bar[buf], x0, row);
