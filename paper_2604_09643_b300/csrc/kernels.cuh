@@ -455,10 +455,13 @@ __global__ void __launch_bounds__(C* C, (C == 16 ? 2 : 8))
           float dn = exp2f(fmaf(-bc, P.gs.c2, P.gs.c3));
           // With u_s = E_s dg_s and beta_s = bc + (s - kc) h, the boundary-motion sum
           // S2 = sum_s beta_s u_s over the boundaries inside the support is
-          // bc sum_s u_s + h sum_s (s - kc) u_s; boundary S-1 (possibly past the edge,
-          // where it does not move with d) is added on its own.
+          // bc U + h T with U = sum_s u_s and T = sum_s (s - kc) u_s; boundary S-1
+          // (possibly past the edge, where it does not move with d) is added on its own.
+          // Each sweep keeps the running sum P_j of u over its first j boundaries and the
+          // sum Q of those running sums: sum_{j=0..J} j u_j = J P_J - (P_0 + ... + P_{J-1}),
+          // two operations per boundary instead of three.
           float E = Ec, gp = gw[kc - 1];
-          float U = 0.f, T = 0.f, last = 0.f;  // sum u, sum (s - kc) u over boundaries < S-1
+          float Pu = 0.f, Qu = 0.f, Pd = 0.f, Qd = 0.f, last = 0.f;
           S1 = 0.f;
 #pragma unroll
           for (int s = kc; s < S; ++s) {
@@ -477,9 +480,8 @@ __global__ void __launch_bounds__(C* C, (C == 16 ? 2 : 8))
                 last = beta < P.supf ? beta * Es * dg : 0.f;
               }
             } else if (POSE) {
-              const float u = E * dg;
-              U += u;
-              if (s != kc) T = fmaf(static_cast<float>(s - kc), u, T);
+              Pu = fmaf(E, dg, Pu);
+              if (s < S - 2) Qu += Pu;
             } else {
               S1 = fmaf(E, dg, S1);
             }
@@ -495,14 +497,16 @@ __global__ void __launch_bounds__(C* C, (C == 16 ? 2 : 8))
             const float dg = gn - gs;
             gn = gs;
             if (POSE) {
-              const float u = E * dg;
-              U += u;
-              T = fmaf(static_cast<float>(s - kc), u, T);
+              Pd = fmaf(E, dg, Pd);
+              if (s >= 2) Qd += Pd;
             } else {
               S1 = fmaf(E, dg, S1);
             }
           }
           if (POSE) {
+            // upward sweep: j = s - kc in 0..S-2-kc; downward: j = kc - s in 1..kc-1, weight -j
+            const float U = Pu + Pd;
+            const float T = fmaf(static_cast<float>(S - 2 - kc), Pu, -Qu) - fmaf(static_cast<float>(kc - 1), Pd, -Qd);
             S1 += U;
             S2 = fmaf(bc, U, fmaf(P.h, T, last));
           }
