@@ -62,7 +62,10 @@ __device__ __forceinline__ void block_loss(double lsum, double* out, int warp, i
   }
 }
 
-// One warp per trace: sum the per-cube partial windows in cube order.
+// One warp per trace: sum the per-cube partial windows in cube order.  LANES =
+// ceil(W / 32) words per lane and cube, so that only the window's own words are
+// loaded and kRedUnroll cubes' loads are in flight at once.
+template <int LANES>
 __global__ void __launch_bounds__(256) fwd_reduce_kernel(const RedParams P) {
   extern __shared__ float racc[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -96,14 +99,15 @@ __global__ void __launch_bounds__(256) fwd_reduce_kernel(const RedParams P) {
       __syncwarp();
       for (int cc = 0; cc < P.ncubes; cc += kRedUnroll) {
         int o[kRedUnroll];
-        float v[kRedUnroll][kRedLanes];
+        float v[kRedUnroll][LANES];
 #pragma unroll
         for (int u = 0; u < kRedUnroll; ++u) {
-          const bool okc = cc + u < P.ncubes;
-          o[u] = okc ? n0[cc + u] - cs : INT_MIN / 2;
+          const int ou = cc + u < P.ncubes ? n0[cc + u] - cs : INT_MIN / 2;
+          const bool okc = ou < len && ou + P.W > 0;  // the cube's window meets this chunk
+          o[u] = okc ? ou : INT_MIN / 2;
           const float* src = part + static_cast<int64_t>(cc + u) * P.W;
 #pragma unroll
-          for (int m = 0; m < kRedLanes; ++m) {
+          for (int m = 0; m < LANES; ++m) {
             const int k = lane + 32 * m;
             v[u][m] = (okc && k < P.W) ? src[k] : 0.f;
           }
@@ -111,7 +115,7 @@ __global__ void __launch_bounds__(256) fwd_reduce_kernel(const RedParams P) {
 #pragma unroll
         for (int u = 0; u < kRedUnroll; ++u) {
 #pragma unroll
-          for (int m = 0; m < kRedLanes; ++m) {
+          for (int m = 0; m < LANES; ++m) {
             const int k = lane + 32 * m;
             const int pos = o[u] + k;
             if (k < P.W && pos >= 0 && pos < len) acc[pos] += v[u][m];
@@ -124,6 +128,34 @@ __global__ void __launch_bounds__(256) fwd_reduce_kernel(const RedParams P) {
     }
   }
   if (P.loss_part) block_loss(em.lsum, P.loss_part + P.loss_offset + blockIdx.x, warp, lane);
+}
+
+size_t fwd_reduce_smem() { return size_t(8) * kRedChunk * 4; }
+
+namespace {
+template <int LANES>
+cudaError_t reduce_launch_l(const RedParams& P, int blocks, cudaStream_t st) {
+  const size_t smem = fwd_reduce_smem();
+  cudaError_t e = cudaFuncSetAttribute(fwd_reduce_kernel<LANES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(smem));
+  if (e != cudaSuccess) return e;
+  fwd_reduce_kernel<LANES><<<blocks, 256, smem, st>>>(P);
+  return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t fwd_reduce_launch(const RedParams& P, int blocks, cudaStream_t st) {
+  switch ((P.W + 31) / 32) {
+    case 1: return reduce_launch_l<1>(P, blocks, st);
+    case 2: return reduce_launch_l<2>(P, blocks, st);
+    case 3: return reduce_launch_l<3>(P, blocks, st);
+    case 4: return reduce_launch_l<4>(P, blocks, st);
+    case 5: return reduce_launch_l<5>(P, blocks, st);
+    case 6: return reduce_launch_l<6>(P, blocks, st);
+    case 7: return reduce_launch_l<7>(P, blocks, st);
+    case 8: return reduce_launch_l<8>(P, blocks, st);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 // Standalone loss head: one warp per trace.

@@ -385,9 +385,6 @@ int run_forward(pasfm_ctx* ctx, const Geo& G, const Plan& pl, const void* p0, co
   const int threads = 32 * pl.fwd_warps;
   const size_t smem = size_t(pl.C == 16 ? fwd_win_offset<16>() : fwd_win_offset<8>()) +
                       size_t(pl.fwd_warps) * pl.W * 32 * 4;
-  const size_t rsmem = size_t(8) * kRedChunk * 4;
-  CUDA_TRY(cudaFuncSetAttribute(fwd_reduce_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                static_cast<int>(rsmem)));
   int loss_off = 0;
   for (int fb = 0; fb < F; fb += Fc) {
     const int fc = std::min(Fc, F - fb);
@@ -419,9 +416,9 @@ int run_forward(pasfm_ctx* ctx, const Geo& G, const Plan& pl, const void* p0, co
     R.loss_offset = loss_off;
     const int rblocks = (R.n_rows + 7) / 8;
     t = ctx->begin(st);
-    fwd_reduce_kernel<<<rblocks, 256, rsmem, st>>>(R);
+    const cudaError_t re = fwd_reduce_launch(R, rblocks, st);
     ctx->end("fwd_reduce", t, st);
-    TRY(check_launch("fwd_reduce"));
+    if (re != cudaSuccess) return fail(PASFM_ECUDA, "fwd_reduce launch: %s", cudaGetErrorString(re));
     loss_off += rblocks;
   }
   if (g_out) {
