@@ -12,6 +12,7 @@
 //                       writes S - 1 slots (its weights sum to zero; S >= 3); the
 //                       flush differences it into a per-cube partial trace and
 //                       fwd_reduce_kernel sums the partials in a fixed order.
+//                       Voxels go in pairs along a row, in packed FP32.
 //   bwd_cube_kernel  -- adjoint v = A^T g and/or pose gradient.  Voxel-
 //                       stationary: a thread owns a row of C voxels along x; the
 //                       CTA walks all (frame, element) traces in batches of 32
@@ -19,6 +20,7 @@
 //                       double buffer.  The adjoint is an atomic-free gather; the
 //                       pose gradient is reduced per element with warp shuffles
 //                       and a fixed-order block reduction, then carried to FP64.
+//                       The row's voxels go in pairs, in packed FP32.
 //
 // Sample slots: a voxel-element pair touches at most S = floor(2 a0 / h) + 2
 // consecutive samples.  With psi = (d - a0 - tau0) / h + 1/2 and first slot
@@ -63,6 +65,40 @@ __device__ __forceinline__ PairMath pair_math(float A, float dc2, float dcf, flo
   return m;
 }
 
+// Two pairs at once (the same element against two neighbouring voxels of a row):
+// Blackwell's packed FP32 instructions do two FMAs, adds or multiplies per lane in
+// one issue slot, with the rounding of the scalar instruction.  The hot loops are
+// bound by instruction issue, so every operation the two pairs share in form runs
+// packed; the reciprocal square root, the reciprocal and the integer index stay
+// scalar.
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 min2(float2 a, float b) { return make_float2(fminf(a.x, b), fminf(a.y, b)); }
+
+struct PairMath2 {
+  float2 rs;
+  unsigned idx0, idx1;
+  float2 beta1;
+};
+
+__device__ __forceinline__ PairMath2 pair_math2(float2 A, float dc2, float dcf, float phim, float inv_h, float h,
+                                                float cb1, int idx_bias) {
+  PairMath2 m;
+  const float2 D2 = add2(f2(dc2), A);
+  m.rs = make_float2(rsqrtf(D2.x), rsqrtf(D2.y));
+  const float2 den = fma2(D2, m.rs, f2(dcf));
+  const float2 del = mul2(A, make_float2(__fdividef(1.f, den.x), __fdividef(1.f, den.y)));
+  const float2 psi = fma2(del, f2(inv_h), f2(phim));
+  const float2 t = add2(psi, f2(kMagic));
+  m.idx0 = static_cast<unsigned>(__float_as_int(t.x) - idx_bias);
+  m.idx1 = static_cast<unsigned>(__float_as_int(t.y) - idx_bias);
+  m.beta1 = fma2(fma2(psi, f2(-1.f), add2(t, f2(-kMagic))), f2(h), f2(cb1));
+  return m;
+}
+
 // ------------------------------------------------------------------------
 // Gaussian boundary values
 // ------------------------------------------------------------------------
@@ -98,6 +134,29 @@ __device__ __forceinline__ void gauss_boundaries(float beta1, float h, const Gau
     dn *= G.q;
   }
   E[S - 1] = fmaxf(E[S - 1], G.e_clamp);
+}
+
+// gauss_boundaries for two pairs, packed
+template <int S>
+__device__ __forceinline__ void gauss_boundaries2(float2 beta1, float h, const GaussConst& G, float2 (&E)[S]) {
+  constexpr int kc = gauss_centre<S>();
+  const float2 bc = fma2(f2(static_cast<float>(kc - 1)), f2(h), beta1);
+  const float2 eb = mul2(f2(G.c1), mul2(bc, bc));
+  E[kc] = make_float2(exp2f(eb.x), exp2f(eb.y));
+  const float2 ua = fma2(bc, f2(G.c2), f2(G.c3)), da = fma2(neg2(bc), f2(G.c2), f2(G.c3));
+  float2 up = make_float2(exp2f(ua.x), exp2f(ua.y));
+  float2 dn = make_float2(exp2f(da.x), exp2f(da.y));
+#pragma unroll
+  for (int k = kc + 1; k < S; ++k) {
+    E[k] = mul2(E[k - 1], up);
+    up = mul2(up, f2(G.q));
+  }
+#pragma unroll
+  for (int k = kc - 1; k >= 1; --k) {
+    E[k] = mul2(E[k + 1], dn);
+    dn = mul2(dn, f2(G.q));
+  }
+  E[S - 1] = make_float2(fmaxf(E[S - 1].x, G.e_clamp), fmaxf(E[S - 1].y, G.e_clamp));
 }
 
 // ------------------------------------------------------------------------
@@ -168,6 +227,9 @@ __global__ void __launch_bounds__(256, 2)
     const float qx = (ix - 0.5f * (C - 1)) * dxf;
     Pix[ix] = qx * (qx + R.m2ux);
   }
+  float2 Pix2[C / 2];
+#pragma unroll
+  for (int i = 0; i < C / 2; ++i) Pix2[i] = make_float2(Pix[2 * i], Pix[2 * i + 1]);
 
   // 4. wait for the tile; flag rows that hold any nonzero voxel
   bool ok = true;
@@ -201,51 +263,71 @@ __global__ void __launch_bounds__(256, 2)
       const float qy = (ly - 0.5f * (C - 1)) * dyf;
       const float Crow = fmaf(qy, qy + R.m2uy, Cz);
       const float* prow = tile + (lz * C + ly) * C;
+      // The pair's slot weights b_k - b_{k+1} (k = 0..S-1) sum to b_0 - b_S = 0, so for
+      // S >= 3 the window holds their running sum, negated: slot k gets b_{k+1} - b_0 for
+      // k = 0..S-2 and slot S-1 gets nothing.  That is S - 1 read-modify-writes instead
+      // of S through shared memory, which bounds this loop; the flush takes the first
+      // difference.  Sphere: b_0 = a0^2, b_k = beta_k^2 inside, the last boundary
+      // clamped.  Gaussian: b = -E, b_0 = -E(edge).  Voxels go in pairs along the row
+      // (packed arithmetic); their read-modify-writes stay in voxel order, since the two
+      // windows may overlap.
+      if constexpr (S >= 3) {
 #pragma unroll
-      for (int i4 = 0; i4 < C; i4 += 4) {
-        const float4 pv4 = *reinterpret_cast<const float4*>(prow + i4);
-        const float pv[4] = {pv4.x, pv4.y, pv4.z, pv4.w};
+        for (int i4 = 0; i4 < C; i4 += 4) {
+          const float4 pv4 = *reinterpret_cast<const float4*>(prow + i4);
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const PairMath m = pair_math(Pix[i4 + u] + Crow, R.dc2, R.dcf, R.phim, P.inv_hf, P.h, P.cb1, idx_bias);
-          if (i4 + u == 0 || i4 + u == C - 1) seen = max(seen, m.idx);
-          float* slot = col + min(m.idx, max_idx) * kWarp;
-          const float s = pv[u] * m.rs;
-          // The pair's slot weights b_k - b_{k+1} (k = 0..S-1) sum to b_0 - b_S = 0, so
-          // for S >= 3 the window holds their running sum: slot k gets b_0 - b_{k+1} for
-          // k = 0..S-2 and slot S-1 gets nothing.  That is S - 1 read-modify-writes
-          // instead of S through shared memory, which bounds this loop; the flush takes
-          // the first difference.  Sphere: b_0 = a0^2, b_k = beta_k^2 inside, the last
-          // boundary clamped.  Gaussian: b = -E, b_0 = -E(edge).  At S = 2 (a pulse
-          // narrower than a sample) every pair is a +-w dipole on two slots; the running
-          // sum would then hold two separately accumulated sums per sample whose
-          // difference cancels in homogeneous regions, so the weights go in directly.
-          if constexpr (S == 2) {
-            float w;
+          for (int u = 0; u < 4; u += 2) {
+            const int i = i4 + u;
+            const float2 pv = u == 0 ? make_float2(pv4.x, pv4.y) : make_float2(pv4.z, pv4.w);
+            const PairMath2 m = pair_math2(add2(Pix2[i / 2], f2(Crow)), R.dc2, R.dcf, R.phim, P.inv_hf, P.h, P.cb1,
+                                           idx_bias);
+            if (i == 0) seen = max(seen, m.idx0);
+            if (i + 1 == C - 1) seen = max(seen, m.idx1);
+            float* sa = col + min(m.idx0, max_idx) * kWarp;
+            float* sb = col + min(m.idx1, max_idx) * kWarp;
+            const float2 s = mul2(pv, m.rs);
+            float2 c[S - 1];  // b_{k+1} - b_0
             if constexpr (K == PASFM_KERNEL_GAUSS) {
-              float E[S];
-              gauss_boundaries<S>(m.beta1, P.h, P.gs, E);
-              w = E[1] - P.gs.e_clamp;
+              float2 E[S];
+              gauss_boundaries2<S>(m.beta1, P.h, P.gs, E);
+#pragma unroll
+              for (int k = 0; k <= S - 2; ++k) c[k] = fma2(E[k + 1], f2(-1.f), f2(P.gs.e_clamp));
             } else {
-              const float bc = fminf(m.beta1, P.supf);
-              w = fmaf(-bc, bc, P.sup2);
+              float2 beta = m.beta1;
+#pragma unroll
+              for (int k = 0; k <= S - 2; ++k) {
+                if (k > 0) beta = add2(beta, f2(P.h));
+                const float2 bc = (k == S - 2) ? min2(beta, P.supf) : beta;
+                c[k] = fma2(bc, bc, f2(-P.sup2));
+              }
             }
-            slot[0] = fmaf(s, w, slot[0]);
-            slot[kWarp] = fmaf(-s, w, slot[kWarp]);
-          } else if constexpr (K == PASFM_KERNEL_GAUSS) {
+#pragma unroll
+            for (int k = 0; k <= S - 2; ++k) sa[k * kWarp] = fmaf(s.x, c[k].x, sa[k * kWarp]);
+#pragma unroll
+            for (int k = 0; k <= S - 2; ++k) sb[k * kWarp] = fmaf(s.y, c[k].y, sb[k * kWarp]);
+          }
+        }
+      } else {
+        // S = 2 (a pulse narrower than a sample): every pair is a +-w dipole on two
+        // slots.  A running sum would hold two separately accumulated sums per sample
+        // whose difference cancels in homogeneous regions, so the weights go in directly.
+#pragma unroll
+        for (int i = 0; i < C; ++i) {
+          const PairMath m = pair_math(Pix[i] + Crow, R.dc2, R.dcf, R.phim, P.inv_hf, P.h, P.cb1, idx_bias);
+          if (i == 0 || i == C - 1) seen = max(seen, m.idx);
+          float* slot = col + min(m.idx, max_idx) * kWarp;
+          const float s = prow[i] * m.rs;
+          float w;
+          if constexpr (K == PASFM_KERNEL_GAUSS) {
             float E[S];
             gauss_boundaries<S>(m.beta1, P.h, P.gs, E);
-#pragma unroll
-            for (int k = 0; k <= S - 2; ++k) slot[k * kWarp] = fmaf(s, E[k + 1] - P.gs.e_clamp, slot[k * kWarp]);
+            w = E[1] - P.gs.e_clamp;
           } else {
-            float beta = m.beta1;
-#pragma unroll
-            for (int k = 0; k <= S - 2; ++k) {
-              if (k > 0) beta += P.h;
-              const float bc = (k == S - 2) ? fminf(beta, P.supf) : beta;
-              slot[k * kWarp] = fmaf(s, fmaf(-bc, bc, P.sup2), slot[k * kWarp]);
-            }
+            const float bc = fminf(m.beta1, P.supf);
+            w = fmaf(-bc, bc, P.sup2);
           }
+          slot[0] = fmaf(s, w, slot[0]);
+          slot[kWarp] = fmaf(-s, w, slot[kWarp]);
         }
       }
     }
@@ -263,11 +345,11 @@ __global__ void __launch_bounds__(256, 2)
       const float c0 = col[(k + 0) * kWarp], c1 = col[(k + 1) * kWarp], c2 = col[(k + 2) * kWarp],
                   c3 = col[(k + 3) * kWarp];
       float4 v;
-      if constexpr (S >= 3) {
-        v.x = (c0 - prev) * P.p0_scale;
-        v.y = (c1 - c0) * P.p0_scale;
-        v.z = (c2 - c1) * P.p0_scale;
-        v.w = (c3 - c2) * P.p0_scale;
+      if constexpr (S >= 3) {  // minus the running sum: T_k = W_{k-1} - W_k
+        v.x = (prev - c0) * P.p0_scale;
+        v.y = (c0 - c1) * P.p0_scale;
+        v.z = (c1 - c2) * P.p0_scale;
+        v.w = (c2 - c3) * P.p0_scale;
         prev = c3;
       } else {
         v = make_float4(c0 * P.p0_scale, c1 * P.p0_scale, c2 * P.p0_scale, c3 * P.p0_scale);
@@ -281,6 +363,120 @@ __global__ void __launch_bounds__(256, 2)
 // ------------------------------------------------------------------------
 // backward (adjoint gather + pose-gradient reduction)
 // ------------------------------------------------------------------------
+
+// The backward's slot sums for two voxels of a row against one trace window (ga, gb:
+// each voxel's first slot), packed.  S1 = sum_s g_s (b_s - b_{s+1}) is the adjoint's;
+// lam S2 is minus the boundary-motion term of dW/dd (lam turns the boundary offsets
+// into derivatives of b and carries the sign, so that no operand needs negating).
+template <int S, int K, bool POSE>
+__device__ __forceinline__ void slot_sums2(const float* ga, const float* gb, float2 beta1, const BwdParams& P,
+                                           float2& S1, float2& S2, float& lam) {
+  if constexpr (K == PASFM_KERNEL_GAUSS) {
+    constexpr int kc = gauss_centre<S>();
+    const float2 bc = fma2(f2(static_cast<float>(kc - 1)), f2(P.h), beta1);
+    const float2 eb = mul2(f2(P.gs.c1), mul2(bc, bc));
+    const float2 Ec = make_float2(exp2f(eb.x), exp2f(eb.y));
+    const float2 ua = fma2(bc, f2(P.gs.c2), f2(P.gs.c3)), da = fma2(bc, f2(-P.gs.c2), f2(P.gs.c3));
+    float2 up = make_float2(exp2f(ua.x), exp2f(ua.y));
+    float2 dn = make_float2(exp2f(da.x), exp2f(da.y));
+    float2 E = Ec, gp = make_float2(ga[kc - 1], gb[kc - 1]);
+    float2 Pu = f2(0.f), Qu = f2(0.f), Pd = f2(0.f), Qd = f2(0.f), last = f2(0.f);
+    S1 = f2(0.f);
+#pragma unroll
+    for (int s = kc; s < S; ++s) {
+      if (s > kc) {
+        E = mul2(E, up);
+        up = mul2(up, f2(P.gs.q));
+      }
+      const float2 gs = make_float2(ga[s], gb[s]);
+      const float2 dg = fma2(gp, f2(-1.f), gs);
+      gp = gs;
+      if (s == S - 1) {
+        const float2 Es = make_float2(fmaxf(E.x, P.gs.e_clamp), fmaxf(E.y, P.gs.e_clamp));
+        S1 = fma2(Es, dg, S1);
+        if (POSE) {
+          const float2 beta = fma2(f2(static_cast<float>(s - 1)), f2(P.h), beta1);
+          const float2 bed = mul2(mul2(beta, Es), dg);
+          last = make_float2(beta.x < P.supf ? bed.x : 0.f, beta.y < P.supf ? bed.y : 0.f);
+        }
+      } else if (POSE) {
+        Pu = fma2(E, dg, Pu);
+        if (s < S - 2) Qu = add2(Qu, Pu);
+      } else {
+        S1 = fma2(E, dg, S1);
+      }
+    }
+    const float2 g_last = gp;
+    E = Ec;
+    float2 gn = make_float2(ga[kc - 1], gb[kc - 1]);
+#pragma unroll
+    for (int s = kc - 1; s >= 1; --s) {
+      E = mul2(E, dn);
+      dn = mul2(dn, f2(P.gs.q));
+      const float2 gs = make_float2(ga[s - 1], gb[s - 1]);
+      const float2 dg = fma2(gs, f2(-1.f), gn);
+      gn = gs;
+      if (POSE) {
+        Pd = fma2(E, dg, Pd);
+        if (s >= 2) Qd = add2(Qd, Pd);
+      } else {
+        S1 = fma2(E, dg, S1);
+      }
+    }
+    if (POSE) {
+      const float2 U = add2(Pu, Pd);
+      // T = (Ju Pu - Qu) - (Jd Pd - Qd)
+      const float2 T = fma2(f2(static_cast<float>(S - 2 - kc)), Pu,
+                            fma2(f2(-static_cast<float>(kc - 1)), Pd, fma2(Qu, f2(-1.f), Qd)));
+      S1 = add2(S1, U);
+      S2 = fma2(bc, U, fma2(f2(P.h), T, last));
+    }
+    S1 = fma2(f2(P.gs.e_clamp), fma2(g_last, f2(-1.f), gn), S1);
+    lam = -P.lam;  // S2 carries its own sign
+  } else if constexpr (S >= 3) {
+    float2 g[S];
+#pragma unroll
+    for (int s = 0; s < S; ++s) g[s] = make_float2(ga[s], gb[s]);
+    constexpr int n = S - 2;
+    const float2 M0 = fma2(g[0], f2(-1.f), g[n]);
+    float2 M1 = g[n], M2 = g[n];
+    if constexpr (n != 2) {
+      M1 = mul2(f2(static_cast<float>(n - 1)), g[n]);
+      M2 = mul2(f2(static_cast<float>((n - 1) * (n - 1))), g[n]);
+    }
+#pragma unroll
+    for (int s = 1; s <= n - 1; ++s) {
+      M1 = fma2(g[s], f2(-1.f), M1);
+      M2 = fma2(f2(-static_cast<float>(2 * s - 1)), g[s], M2);
+    }
+    const float2 dgl = fma2(g[n], f2(-1.f), g[S - 1]);
+    const float2 bl = fma2(f2(static_cast<float>(S - 2)), f2(P.h), beta1);
+    const float2 tl = min2(bl, P.supf);
+    const float2 X = fma2(f2(P.h), M1, mul2(beta1, M0));
+    if (POSE) {
+      const float2 D = make_float2(bl.x < P.supf ? bl.x : 0.f, bl.y < P.supf ? bl.y : 0.f);
+      S2 = fma2(D, dgl, X);  // minus the boundary-motion sum; lam carries the sign
+    }
+    const float2 Y = fma2(f2(P.h), M1, X);
+    S1 = fma2(beta1, Y, fma2(f2(P.h * P.h), M2, fma2(fma2(tl, tl, f2(-P.sup2)), dgl, mul2(f2(-P.sup2), M0))));
+    lam = 2.f;
+  } else {  // S = 2, per voxel
+    const float* gv[2] = {ga, gb};
+    const float b1[2] = {beta1.x, beta1.y};
+    float s1[2], s2[2];
+#pragma unroll
+    for (int v = 0; v < 2; ++v) {
+      const float g0 = gv[v][0], g1 = gv[v][1];
+      const float bc = fminf(b1[v], P.supf);
+      s1[v] = fmaf(bc * bc, g1 - g0, P.sup2 * (g0 - g1));
+      s2[v] = POSE ? (b1[v] < P.supf ? b1[v] : 0.f) * (g1 - g0) : 0.f;  // minus the sum
+    }
+    S1 = make_float2(s1[0], s1[1]);
+    S2 = make_float2(s2[0], s2[1]);
+    lam = 2.f;
+  }
+}
+
 constexpr int kBatch = 32;  // traces staged per batch
 
 template <int C>
@@ -333,25 +529,26 @@ __global__ void __launch_bounds__(C* C, (C == 16 ? 2 : 8))
   const float dxf = static_cast<float>(P.dx);
   const float qy = (ty - 0.5f * (C - 1)) * static_cast<float>(P.dy);
   const float qz = (tz - 0.5f * (C - 1)) * static_cast<float>(P.dz);
-  float qx[C];
+  float2 qx2[C / 2];
 #pragma unroll
-  for (int k = 0; k < C; ++k) qx[k] = (k - 0.5f * (C - 1)) * dxf;
+  for (int k = 0; k < C / 2; ++k) qx2[k] = make_float2((2 * k - 0.5f * (C - 1)) * dxf, (2 * k + 1 - 0.5f * (C - 1)) * dxf);
 
-  float p0s[POSE ? C : 1];
+  float2 p0s2[POSE ? C / 2 : 1];  // p0 along this thread's row, voxels (2k, 2k + 1)
   if (POSE) {
 #pragma unroll
     for (int k = 0; k < C; ++k) {
       const int ix = cx * C + k;
-      p0s[k] = (row_in && ix < P.nx)
-                   ? load_elem(P.p0, (static_cast<int64_t>(iz) * P.ny + iy) * P.nx + ix, P.dtype_vol) * P.scale
-                   : 0.f;
+      const float v = (row_in && ix < P.nx)
+                          ? load_elem(P.p0, (static_cast<int64_t>(iz) * P.ny + iy) * P.nx + ix, P.dtype_vol) * P.scale
+                          : 0.f;
+      if (k % 2) p0s2[k / 2].y = v; else p0s2[k / 2].x = v;
     }
   }
   // adjoint: per-batch partial sums (<= 32 traces x S terms) folded once per batch
-  float acc[ADJ ? C : 1], bacc[ADJ ? C : 1];
+  float2 acc[ADJ ? C / 2 : 1], bacc[ADJ ? C / 2 : 1];
   if (ADJ) {
 #pragma unroll
-    for (int k = 0; k < C; ++k) acc[k] = bacc[k] = 0.f;
+    for (int k = 0; k < C / 2; ++k) acc[k] = bacc[k] = f2(0.f);
   }
 
   const double hc = 0.5 * (C - 1);
@@ -436,137 +633,26 @@ __global__ void __launch_bounds__(C* C, (C == 16 ? 2 : 8))
       const int idx_bias = kMagicBits - __float_as_int(rb.z);
       const float* wv = wb + e * WP;
       const float Crow = fmaf(qy, qy + ra.y, qz * (qz + ra.z));
-      float R0 = 0.f, R1 = 0.f;
+      float2 R0v = f2(0.f), R1v = f2(0.f);
 #pragma unroll
-      for (int k = 0; k < C; ++k) {
-        const float A = fmaf(qx[k], qx[k] + ra.x, Crow);
-        const PairMath m = pair_math(A, ra.w, rb.x, rb.y, P.inv_hf, P.h, P.cb1, idx_bias);
-        if (k == 0 || k == C - 1) seen = max(seen, m.idx);
-        const float* gw = wv + min(m.idx, max_idx);
-        // S1 = sum_k g_k (b_k - b_{k+1}) by parts; S2 = the boundary-motion term of dW/dd
-        float S1, S2 = 0.f, lam;
-        if constexpr (K == PASFM_KERNEL_GAUSS) {
-          // b_s = -E_s (sign folded into P.scale < 0); visited outward from the centre
-          // boundary as in gauss_boundaries, without an array of values
-          constexpr int kc = gauss_centre<S>();
-          const float bc = fmaf(static_cast<float>(kc - 1), P.h, m.beta1);
-          const float Ec = exp2f(P.gs.c1 * (bc * bc));
-          float up = exp2f(fmaf(bc, P.gs.c2, P.gs.c3));
-          float dn = exp2f(fmaf(-bc, P.gs.c2, P.gs.c3));
-          // With u_s = E_s dg_s and beta_s = bc + (s - kc) h, the boundary-motion sum
-          // S2 = sum_s beta_s u_s over the boundaries inside the support is
-          // bc U + h T with U = sum_s u_s and T = sum_s (s - kc) u_s; boundary S-1
-          // (possibly past the edge, where it does not move with d) is added on its own.
-          // Each sweep keeps the running sum P_j of u over its first j boundaries and the
-          // sum Q of those running sums: sum_{j=0..J} j u_j = J P_J - (P_0 + ... + P_{J-1}),
-          // two operations per boundary instead of three.
-          float E = Ec, gp = gw[kc - 1];
-          float Pu = 0.f, Qu = 0.f, Pd = 0.f, Qd = 0.f, last = 0.f;
-          S1 = 0.f;
-#pragma unroll
-          for (int s = kc; s < S; ++s) {
-            if (s > kc) {
-              E *= up;
-              up *= P.gs.q;
-            }
-            const float gs = gw[s];
-            const float dg = gs - gp;
-            gp = gs;
-            if (s == S - 1) {
-              const float Es = fmaxf(E, P.gs.e_clamp);
-              S1 = fmaf(Es, dg, S1);
-              if (POSE) {
-                const float beta = fmaf(static_cast<float>(s - 1), P.h, m.beta1);
-                last = beta < P.supf ? beta * Es * dg : 0.f;
-              }
-            } else if (POSE) {
-              Pu = fmaf(E, dg, Pu);
-              if (s < S - 2) Qu += Pu;
-            } else {
-              S1 = fmaf(E, dg, S1);
-            }
-          }
-          const float g_last = gp;
-          E = Ec;
-          float gn = gw[kc - 1];
-#pragma unroll
-          for (int s = kc - 1; s >= 1; --s) {
-            E *= dn;
-            dn *= P.gs.q;
-            const float gs = gw[s - 1];
-            const float dg = gn - gs;
-            gn = gs;
-            if (POSE) {
-              Pd = fmaf(E, dg, Pd);
-              if (s >= 2) Qd += Pd;
-            } else {
-              S1 = fmaf(E, dg, S1);
-            }
-          }
-          if (POSE) {
-            // upward sweep: j = s - kc in 0..S-2-kc; downward: j = kc - s in 1..kc-1, weight -j
-            const float U = Pu + Pd;
-            const float T = fmaf(static_cast<float>(S - 2 - kc), Pu, -Qu) - fmaf(static_cast<float>(kc - 1), Pd, -Qd);
-            S1 += U;
-            S2 = fmaf(bc, U, fmaf(P.h, T, last));
-          }
-          S1 = fmaf(P.gs.e_clamp, gn - g_last, S1);
-          lam = P.lam;
-        } else if constexpr (S >= 3) {
-          // Sphere, b_s = beta_s^2 on the interior boundaries s = 1..n (n = S - 2,
-          // beta_s = beta1 + (s - 1) h), b_{S-1} = min(beta_{S-1}, a0)^2, b_0 = b_S = a0^2.
-          // Summation by parts turns the interior sums into three fixed combinations of
-          // the window values, M_p = sum_s (s - 1)^p dg_s (p = 0, 1, 2):
-          //   S1 = a0^2 (g_0 - g_{S-1}) + beta1^2 M0 + 2 h beta1 M1 + h^2 M2 + b_{S-1} dg_{S-1},
-          //   S2 = -(beta1 M0 + h M1) - D dg_{S-1},  D = beta_{S-1} inside the support, else 0,
-          // which costs about a third fewer instructions than a boundary-by-boundary sum.
-          float g[S];
-#pragma unroll
-          for (int s = 0; s < S; ++s) g[s] = gw[s];
-          constexpr int n = S - 2;
-          const float M0 = g[n] - g[0];
-          float M1 = static_cast<float>(n - 1) * g[n], M2 = static_cast<float>((n - 1) * (n - 1)) * g[n];
-#pragma unroll
-          for (int s = 1; s <= n - 1; ++s) {
-            M1 -= g[s];
-            M2 = fmaf(-static_cast<float>(2 * s - 1), g[s], M2);
-          }
-          const float dgl = g[S - 1] - g[n];
-          const float b1 = m.beta1;
-          const float bl = fmaf(static_cast<float>(S - 2), P.h, b1);  // beta_{S-1}
-          const float tl = fminf(bl, P.supf);
-          const float X = fmaf(P.h, M1, b1 * M0);  // sum of beta_s dg_s over the interior
-          if (POSE) S2 = -fmaf(bl < P.supf ? bl : 0.f, dgl, X);
-          const float Y = fmaf(P.h, M1, X);        // beta1 M0 + 2 h M1
-          S1 = fmaf(b1, Y, fmaf(P.h * P.h, M2, fmaf(fmaf(tl, tl, -P.sup2), dgl, -P.sup2 * M0)));
-          lam = 2.f;
-        } else {  // S = 2: boundary 1 is the clamped one
-          float g[S];
-#pragma unroll
-          for (int s = 0; s < S; ++s) g[s] = gw[s];
-          float beta = m.beta1;
-          S1 = P.sup2 * (g[0] - g[S - 1]);
-#pragma unroll
-          for (int s = 1; s < S; ++s) {
-            if (s > 1) beta += P.h;
-            const float dg = g[s] - g[s - 1];
-            const float bc = (s == S - 1) ? fminf(beta, P.supf) : beta;
-            S1 = fmaf(bc * bc, dg, S1);
-            if (POSE) {
-              const float D = (s == S - 1) ? (beta < P.supf ? beta : 0.f) : beta;
-              S2 = fmaf(-D, dg, S2);
-            }
-          }
-          lam = 2.f;
-        }
-        const float t1 = m.rs * S1;
-        if (ADJ) bacc[k] += t1;
-        if (POSE) {
-          const float coef = p0s[k] * (m.rs * m.rs) * fmaf(lam, S2, -t1);
-          R0 += coef;
-          R1 = fmaf(coef, qx[k], R1);
+      for (int k2 = 0; k2 < C / 2; ++k2) {
+        const int k = 2 * k2;
+        const float2 A = fma2(qx2[k2], add2(qx2[k2], f2(ra.x)), f2(Crow));
+        const PairMath2 m = pair_math2(A, ra.w, rb.x, rb.y, P.inv_hf, P.h, P.cb1, idx_bias);
+        if (k == 0) seen = max(seen, m.idx0);
+        if (k + 1 == C - 1) seen = max(seen, m.idx1);
+        float2 S1, S2 = f2(0.f);
+        float lam;
+        slot_sums2<S, K, POSE>(wv + min(m.idx0, max_idx), wv + min(m.idx1, max_idx), m.beta1, P, S1, S2, lam);
+        const float2 t1 = mul2(m.rs, S1);
+        if (ADJ) bacc[k2] = add2(bacc[k2], t1);
+        if (POSE) {  // minus the coefficient: p0 (1/d^2) (t1 - dW/dd boundary term)
+          const float2 coef = mul2(mul2(p0s2[k2], mul2(m.rs, m.rs)), fma2(f2(lam), S2, t1));
+          R0v = add2(R0v, coef);
+          R1v = fma2(coef, qx2[k2], R1v);
         }
       }
+      const float R0 = -(R0v.x + R0v.y), R1 = -(R1v.x + R1v.y);
       if (POSE) {
         // reduce-scatter: lanes 0-7 end with sum(R0), 8-15 sum(R1), 16-23 sum(qy R0), 24-31 sum(qz R0)
         const float R2 = qy * R0, R3 = qz * R0;
@@ -584,9 +670,9 @@ __global__ void __launch_bounds__(C* C, (C == 16 ? 2 : 8))
     }
     if (ADJ) {  // fold the batch partial (<= 32 traces x S terms) into the voxel sum
 #pragma unroll
-      for (int k = 0; k < C; ++k) {
-        acc[k] += bacc[k];
-        bacc[k] = 0.f;
+      for (int k = 0; k < C / 2; ++k) {
+        acc[k] = add2(acc[k], bacc[k]);
+        bacc[k] = f2(0.f);
       }
     }
     if (__syncthreads_or(!ok)) {
@@ -630,7 +716,7 @@ __global__ void __launch_bounds__(C* C, (C == 16 ? 2 : 8))
     for (int k = 0; k < C; ++k) {
       const int ix = cx * C + k;
       if (ix < P.nx) {
-        const float v = acc[k] * P.scale;
+        const float v = (k % 2 ? acc[k / 2].y : acc[k / 2].x) * P.scale;
         out[ix] = add ? out[ix] + v : v;
       }
     }
