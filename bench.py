@@ -402,7 +402,10 @@ def run_native(args):
                     "unit": "TFLOP/s", "frac": achieved / pk["fp32_tflops"], "traffic": traffic_for(dom + ("_gauss" if gauss else "")) if captured else None,
                     "peak_source": f"FP32 148 SM x 128 lanes x 2 flops x {pk['sm_max_mhz']:.0f} MHz "
                                    f"({pk['source']} clock)",
-                    "flops_per_pair": fpp, "pairs_per_launch": pairs / launches_per_step}
+                    "flops_per_pair": fpp, "pairs_per_launch": pairs / launches_per_step,
+                    "note": "flops_per_pair is the frozen algorithmic count; the kernels' rewritten "
+                            "slot sums execute fewer FP32 operations, so frac can pass 1.0; the "
+                            "measured FMA-pipe occupancy (ncu) is in the profile summaries"}
     step_flops = pairs * (f_fwd(m) + f_adj(m) + f_pose(m))
     # achieved DRAM bandwidth of the kernels whose per-launch traffic ncu measured on these sources
     hbm = {}

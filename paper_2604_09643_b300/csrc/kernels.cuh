@@ -489,7 +489,8 @@ struct BwdLayout {
   __host__ __device__ static int refb_off(int WP) { return refa_off(WP) + 2 * kBatch * 16; }
   __host__ __device__ static int refu_off(int WP) { return refb_off(WP) + 2 * kBatch * 16; }
   __host__ __device__ static int red_off(int WP) { return refu_off(WP) + 2 * kBatch * 24; }
-  __host__ __device__ static int bar_off(int WP) { return red_off(WP) + 2 * NW * kBatch * 16; }
+  __host__ __device__ static int pix_off(int WP) { return red_off(WP) + 2 * NW * kBatch * 16; }
+  __host__ __device__ static int bar_off(int WP) { return pix_off(WP) + 2 * kBatch * C * 4; }
   __host__ __device__ static int total(int WP) { return bar_off(WP) + 16; }
 };
 
@@ -505,8 +506,12 @@ __device__ __forceinline__ void bwd_thread_row(int tid, int& ty, int& tz) {
   }
 }
 
+// Resident CTAs per SM: two 16^3 CTAs (128 registers a thread) for the sphere; three for
+// the Gaussian, whose longer dependent chains gain more from the extra warps than they
+// lose to the few spilled registers (measured 4% faster at S = 12; the sphere gains
+// nothing); eight 8^3 CTAs.
 template <int C, int S, int K, bool ADJ, bool POSE>
-__global__ void __launch_bounds__(C* C, (C == 16 ? 2 : 8))
+__global__ void __launch_bounds__(C* C, (C == 16 ? (K == PASFM_KERNEL_GAUSS ? 3 : 2) : 8))
     bwd_cube_kernel(const __grid_constant__ CUtensorMap gmap, const BwdParams P) {
   using L = BwdLayout<C>;
   extern __shared__ __align__(128) unsigned char smem[];
@@ -516,6 +521,7 @@ __global__ void __launch_bounds__(C* C, (C == 16 ? 2 : 8))
   float4* refb = reinterpret_cast<float4*>(smem + L::refb_off(WP));
   double* refu = reinterpret_cast<double*>(smem + L::refu_off(WP));
   float4* red = reinterpret_cast<float4*>(smem + L::red_off(WP));
+  float2* pix = reinterpret_cast<float2*>(smem + L::pix_off(WP));
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L::bar_off(WP));
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -529,11 +535,9 @@ __global__ void __launch_bounds__(C* C, (C == 16 ? 2 : 8))
   const float dxf = static_cast<float>(P.dx);
   const float qy = (ty - 0.5f * (C - 1)) * static_cast<float>(P.dy);
   const float qz = (tz - 0.5f * (C - 1)) * static_cast<float>(P.dz);
-  float2 qx2[C / 2];
-#pragma unroll
-  for (int k = 0; k < C / 2; ++k) qx2[k] = make_float2((2 * k - 0.5f * (C - 1)) * dxf, (2 * k + 1 - 0.5f * (C - 1)) * dxf);
 
-  float2 p0s2[POSE ? C / 2 : 1];  // p0 along this thread's row, voxels (2k, 2k + 1)
+  // p0 and p0 q_x along this thread's row, voxels (2k, 2k + 1)
+  float2 p0s2[POSE ? C / 2 : 1], p0qx2[POSE ? C / 2 : 1];
   if (POSE) {
 #pragma unroll
     for (int k = 0; k < C; ++k) {
@@ -541,7 +545,14 @@ __global__ void __launch_bounds__(C* C, (C == 16 ? 2 : 8))
       const float v = (row_in && ix < P.nx)
                           ? load_elem(P.p0, (static_cast<int64_t>(iz) * P.ny + iy) * P.nx + ix, P.dtype_vol) * P.scale
                           : 0.f;
-      if (k % 2) p0s2[k / 2].y = v; else p0s2[k / 2].x = v;
+      const float vq = v * ((k - 0.5f * (C - 1)) * dxf);
+      if (k % 2) {
+        p0s2[k / 2].y = v;
+        p0qx2[k / 2].y = vq;
+      } else {
+        p0s2[k / 2].x = v;
+        p0qx2[k / 2].x = vq;
+      }
     }
   }
   // adjoint: per-batch partial sums (<= 32 traces x S terms) folded once per batch
@@ -582,6 +593,14 @@ __global__ void __launch_bounds__(C* C, (C == 16 ? 2 : 8))
       x0 = n0 & ~3;
       const float mk = (POSE && P.mask) ? (P.mask[row] ? 1.f : 0.f) : 1.f;
       refa[buf * kBatch + lane] = make_float4(R.m2ux, R.m2uy, R.m2uz, R.dc2);
+      // the x part of A, q_x (q_x - 2 u_x), for the C voxels of a row: the same for every
+      // row of the cube, so formed once per trace
+      float2* pd = pix + (buf * kBatch + lane) * (C / 2);
+#pragma unroll
+      for (int k = 0; k < C / 2; ++k) {
+        const float qa = (2 * k - 0.5f * (C - 1)) * dxf, qb = (2 * k + 1 - 0.5f * (C - 1)) * dxf;
+        pd[k] = make_float2(qa * (qa + R.m2ux), qb * (qb + R.m2ux));
+      }
       refb[buf * kBatch + lane] = make_float4(R.dcf, R.phim, __int_as_float(R.Nc - x0), mk);
       if (POSE) {
         refu[(buf * kBatch + lane) * 3 + 0] = R.ux;
@@ -633,11 +652,12 @@ __global__ void __launch_bounds__(C* C, (C == 16 ? 2 : 8))
       const int idx_bias = kMagicBits - __float_as_int(rb.z);
       const float* wv = wb + e * WP;
       const float Crow = fmaf(qy, qy + ra.y, qz * (qz + ra.z));
+      const float2* pe = pix + (buf * kBatch + e) * (C / 2);
       float2 R0v = f2(0.f), R1v = f2(0.f);
 #pragma unroll
       for (int k2 = 0; k2 < C / 2; ++k2) {
         const int k = 2 * k2;
-        const float2 A = fma2(qx2[k2], add2(qx2[k2], f2(ra.x)), f2(Crow));
+        const float2 A = add2(pe[k2], f2(Crow));
         const PairMath2 m = pair_math2(A, ra.w, rb.x, rb.y, P.inv_hf, P.h, P.cb1, idx_bias);
         if (k == 0) seen = max(seen, m.idx0);
         if (k + 1 == C - 1) seen = max(seen, m.idx1);
@@ -647,9 +667,9 @@ __global__ void __launch_bounds__(C* C, (C == 16 ? 2 : 8))
         const float2 t1 = mul2(m.rs, S1);
         if (ADJ) bacc[k2] = add2(bacc[k2], t1);
         if (POSE) {  // minus the coefficient: p0 (1/d^2) (t1 - dW/dd boundary term)
-          const float2 coef = mul2(mul2(p0s2[k2], mul2(m.rs, m.rs)), fma2(f2(lam), S2, t1));
-          R0v = add2(R0v, coef);
-          R1v = fma2(coef, qx2[k2], R1v);
+          const float2 cf = mul2(mul2(m.rs, m.rs), fma2(f2(lam), S2, t1));
+          R0v = fma2(p0s2[k2], cf, R0v);
+          R1v = fma2(p0qx2[k2], cf, R1v);
         }
       }
       const float R0 = -(R0v.x + R0v.y), R1 = -(R1v.x + R1v.y);
