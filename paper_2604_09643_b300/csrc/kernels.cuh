@@ -490,7 +490,8 @@ struct BwdLayout {
   __host__ __device__ static int refu_off(int WP) { return refb_off(WP) + 2 * kBatch * 16; }
   __host__ __device__ static int red_off(int WP) { return refu_off(WP) + 2 * kBatch * 24; }
   __host__ __device__ static int pix_off(int WP) { return red_off(WP) + 2 * NW * kBatch * 16; }
-  __host__ __device__ static int bar_off(int WP) { return pix_off(WP) + 2 * kBatch * C * 4; }
+  __host__ __device__ static int acc_off(int WP) { return pix_off(WP) + 2 * kBatch * C * 4; }
+  __host__ __device__ static int bar_off(int WP) { return acc_off(WP) + NT * C * 4; }
   __host__ __device__ static int total(int WP) { return bar_off(WP) + 16; }
 };
 
@@ -506,12 +507,12 @@ __device__ __forceinline__ void bwd_thread_row(int tid, int& ty, int& tz) {
   }
 }
 
-// Resident CTAs per SM: two 16^3 CTAs (128 registers a thread) for the sphere; three for
-// the Gaussian, whose longer dependent chains gain more from the extra warps than they
-// lose to the few spilled registers (measured 4% faster at S = 12; the sphere gains
-// nothing); eight 8^3 CTAs.
+// Resident CTAs per SM: three 16^3 CTAs (80 registers a thread; the adjoint's voxel sums
+// live in shared memory), whose 24 warps hide the dependent chains better than two CTAs
+// at 128 registers, at the price of a few spilled registers (measured 2% faster on the
+// sphere, 4% on the Gaussian at S = 12); eight 8^3 CTAs.
 template <int C, int S, int K, bool ADJ, bool POSE>
-__global__ void __launch_bounds__(C* C, (C == 16 ? (K == PASFM_KERNEL_GAUSS ? 3 : 2) : 8))
+__global__ void __launch_bounds__(C* C, (C == 16 ? 3 : 8))
     bwd_cube_kernel(const __grid_constant__ CUtensorMap gmap, const BwdParams P) {
   using L = BwdLayout<C>;
   extern __shared__ __align__(128) unsigned char smem[];
@@ -522,6 +523,7 @@ __global__ void __launch_bounds__(C* C, (C == 16 ? (K == PASFM_KERNEL_GAUSS ? 3 
   double* refu = reinterpret_cast<double*>(smem + L::refu_off(WP));
   float4* red = reinterpret_cast<float4*>(smem + L::red_off(WP));
   float2* pix = reinterpret_cast<float2*>(smem + L::pix_off(WP));
+  float* accs = reinterpret_cast<float*>(smem + L::acc_off(WP));  // [voxel k][thread]
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L::bar_off(WP));
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -556,10 +558,12 @@ __global__ void __launch_bounds__(C* C, (C == 16 ? (K == PASFM_KERNEL_GAUSS ? 3 
     }
   }
   // adjoint: per-batch partial sums (<= 32 traces x S terms) folded once per batch
-  float2 acc[ADJ ? C / 2 : 1], bacc[ADJ ? C / 2 : 1];
+  float2 bacc[ADJ ? C / 2 : 1];
   if (ADJ) {
 #pragma unroll
-    for (int k = 0; k < C / 2; ++k) acc[k] = bacc[k] = f2(0.f);
+    for (int k = 0; k < C / 2; ++k) bacc[k] = f2(0.f);
+#pragma unroll
+    for (int k = 0; k < C; ++k) accs[k * L::NT + tid] = 0.f;
   }
 
   const double hc = 0.5 * (C - 1);
@@ -691,7 +695,8 @@ __global__ void __launch_bounds__(C* C, (C == 16 ? (K == PASFM_KERNEL_GAUSS ? 3 
     if (ADJ) {  // fold the batch partial (<= 32 traces x S terms) into the voxel sum
 #pragma unroll
       for (int k = 0; k < C / 2; ++k) {
-        acc[k] = add2(acc[k], bacc[k]);
+        accs[(2 * k) * L::NT + tid] += bacc[k].x;
+        accs[(2 * k + 1) * L::NT + tid] += bacc[k].y;
         bacc[k] = f2(0.f);
       }
     }
@@ -736,7 +741,7 @@ __global__ void __launch_bounds__(C* C, (C == 16 ? (K == PASFM_KERNEL_GAUSS ? 3 
     for (int k = 0; k < C; ++k) {
       const int ix = cx * C + k;
       if (ix < P.nx) {
-        const float v = (k % 2 ? acc[k / 2].y : acc[k / 2].x) * P.scale;
+        const float v = accs[k * L::NT + tid] * P.scale;
         out[ix] = add ? out[ix] + v : v;
       }
     }

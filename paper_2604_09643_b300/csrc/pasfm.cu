@@ -58,7 +58,7 @@ struct Rec {
 };
 
 constexpr size_t kDefaultPartialBudget = size_t(4) << 30;
-constexpr int kMaxParts = 4;  // backward CTAs per cube (item parts); bounds the per-part adjoint buffer
+constexpr int kMaxParts = 8;  // backward CTAs per cube (item parts); bounds the per-part adjoint buffer
 constexpr int kFwdWmax16 = 128;  // forward window cap for 16^3 cubes (8 warps x W x 128 B)
 constexpr int kFwdWmax8 = 200;   // forward window cap for 8^3 cubes
 
