@@ -386,8 +386,9 @@ def run_native(args):
     pk = peaks()
     dom = max(per_kernel, key=lambda k: per_kernel[k]["ms_total"])
     gauss = args.kernel == "gauss"
-    # the committed DRAM counters were taken on the full-scan workload; other workloads report none
-    captured = args.workload == "full_scan"
+    # the committed DRAM counters are per launch of the full-scan workload at its 64 frames;
+    # other workloads and cut-down profiling cases report none
+    captured = args.workload == "full_scan" and geom["n_frames"] == 64
     meas_mib = meas.numel() * meas.element_size() / 2**20
     resid_mib = meas.numel() * 4 / 2**20
     f_fwd, f_adj, f_pose = ((flops_fwd_gauss, flops_adj_gauss, flops_pose_gauss) if gauss
