@@ -444,6 +444,10 @@ def run_native(args):
         out["config"]["workload"] += f" (profiling case: {args.frames} frames, not a bench line)"
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "full_scan" and not gauss:
         out["cpu_baseline"] = cpu_baseline(scan, p_init, poses_init)
+    # measured FP32 FMA throughput of this GPU (after the timed region), scalar and packed:
+    # context for the derived roofline peak
+    out["fp32_probe_tflops"] = {"ffma": binding.fp32_probe(local, packed=False),
+                                "ffma2": binding.fp32_probe(local, packed=True)}
     if rank == 0:
         print(json.dumps(out))
     ctx.close()

@@ -275,6 +275,13 @@ int pasfm_nc_grad(pasfm_ctx* ctx, int64_t n_rows, int n_samples, const float* si
  * Gaussian width or the grid spacing changes).  Device memory. */
 int pasfm_scale(pasfm_ctx* ctx, int64_t n, double alpha, float* x, void* stream);
 
+/* Measurement aid, no counterpart in the paper -- FP32 FMA throughput of `device`
+ * in TFLOP/s (an FMA counts 2 flops): independent FMA chains on every SM, scalar
+ * (packed = 0) or Blackwell's packed two-wide FMA on float2 (packed = 1).  Allocates
+ * and frees 4 bytes of device memory, runs on the default stream and synchronises,
+ * about 10 ms; not for use while other work runs on the device.  tflops_out: host. */
+int pasfm_fp32_probe(int device, int packed, double* tflops_out);
+
 /* Allocation-free pose gradient.  No counterpart in the paper: this is a
  * library service for callers that must not allocate device memory while they
  * run -- code hosted inside an application that owns all device memory through

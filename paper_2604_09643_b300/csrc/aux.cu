@@ -446,6 +446,54 @@ __global__ void __launch_bounds__(256) scale_kernel(float* __restrict__ x, int64
     x[i] *= alpha;
 }
 
+// FP32 throughput probe: kProbeChains independent FMA chains per thread for `iters`
+// rounds (a multiple of 16; PACKED: two-wide packed FMAs on float2 chains).  The chains converge to
+// c / (1 - m); their sum is stored only if it equals an impossible value, so no chain
+// can be dropped and the kernel touches no memory.
+template <bool PACKED>
+__global__ void __launch_bounds__(256) fp32_probe_kernel(float* out, int iters, float m, float c) {
+  constexpr int kProbeChains = 8;
+  const float seed = 1e-3f * static_cast<float>(threadIdx.x);
+  float s = 0.f;
+  if constexpr (PACKED) {
+    float2 a[kProbeChains];
+#pragma unroll
+    for (int k = 0; k < kProbeChains; ++k) a[k] = make_float2(seed + k, seed - k);
+    const float2 m2 = make_float2(m, m), c2 = make_float2(c, c);
+#pragma unroll 16
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+      for (int k = 0; k < kProbeChains; ++k) a[k] = __ffma2_rn(a[k], m2, c2);
+    }
+#pragma unroll
+    for (int k = 0; k < kProbeChains; ++k) s += a[k].x + a[k].y;
+  } else {
+    float a[kProbeChains];
+#pragma unroll
+    for (int k = 0; k < kProbeChains; ++k) a[k] = seed + k;
+#pragma unroll 16
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+      for (int k = 0; k < kProbeChains; ++k) a[k] = fmaf(a[k], m, c);
+    }
+#pragma unroll
+    for (int k = 0; k < kProbeChains; ++k) s += a[k];
+  }
+  if (s == -1.2345e30f) out[0] = s;
+}
+
+double fp32_probe_flops(int blocks, int iters, bool packed) {
+  return double(blocks) * 256.0 * iters * 8 * 2 * (packed ? 2 : 1);
+}
+
+cudaError_t fp32_probe_launch(bool packed, int blocks, int iters, float* out, cudaStream_t st) {
+  if (packed)
+    fp32_probe_kernel<true><<<blocks, 256, 0, st>>>(out, iters, 0.9999f, 1e-4f);
+  else
+    fp32_probe_kernel<false><<<blocks, 256, 0, st>>>(out, iters, 0.9999f, 1e-4f);
+  return cudaGetLastError();
+}
+
 __global__ void __launch_bounds__(256) sum_parts_kernel(const float* __restrict__ parts, int n_parts, int64_t nvox,
                                                         float* __restrict__ vol, int accumulate) {
   for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < nvox;

@@ -1045,6 +1045,32 @@ int pasfm_scale(pasfm_ctx* ctx, int64_t n, double alpha, float* x, void* stream)
   return check_launch("scale");
 }
 
+int pasfm_fp32_probe(int device, int packed, double* tflops_out) {
+  if (!tflops_out) return fail(PASFM_EINVAL, "NULL output");
+  CUDA_TRY(cudaSetDevice(device));
+  int sms = 0;
+  CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
+  float* out = nullptr;
+  CUDA_TRY(cudaMalloc(&out, sizeof(float)));
+  const int blocks = sms * 8, iters = 1 << 14, reps = 5;
+  cudaEvent_t a = nullptr, b = nullptr;
+  cudaError_t e = cudaEventCreate(&a);
+  if (e == cudaSuccess) e = cudaEventCreate(&b);
+  if (e == cudaSuccess) e = fp32_probe_launch(packed != 0, blocks, iters, out, nullptr);  // warm-up
+  if (e == cudaSuccess) e = cudaEventRecord(a, nullptr);
+  for (int r = 0; e == cudaSuccess && r < reps; ++r) e = fp32_probe_launch(packed != 0, blocks, iters, out, nullptr);
+  if (e == cudaSuccess) e = cudaEventRecord(b, nullptr);
+  if (e == cudaSuccess) e = cudaEventSynchronize(b);
+  float ms = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+  if (a) cudaEventDestroy(a);
+  if (b) cudaEventDestroy(b);
+  cudaFree(out);
+  if (e != cudaSuccess) return fail(PASFM_ECUDA, "fp32 probe: %s", cudaGetErrorString(e));
+  *tflops_out = reps * fp32_probe_flops(blocks, iters, packed != 0) / (ms * 1e-3) / 1e12;
+  return PASFM_OK;
+}
+
 int pasfm_status(pasfm_ctx* ctx, void* stream, uint32_t* bits) {
   if (!ctx) return fail(PASFM_EINVAL, "ctx is NULL");
   TRY(set_device(ctx));

@@ -362,3 +362,11 @@ def test_full_scan_sampled(ctx):
     _band_check(gE[f], g6[f:f + 1], mid, half, [(xw[f], slice(0, E))])
     others = np.delete(np.arange(geom["n_frames"]), f)
     assert np.abs(g6[others]).max() == 0.0
+
+
+def test_fp32_probe_is_plausible(ctx):
+    """The FP32 FMA throughput probe returns a rate between a tenth and twice the unit-count
+    peak (148 SMs x 128 lanes x 2 flops x clock), for scalar and packed FMAs."""
+    for packed in (False, True):
+        tf = binding.fp32_probe(0, packed=packed)
+        assert 5.0 < tf < 200.0, (packed, tf)
