@@ -448,6 +448,21 @@ def run_native(args):
     # context for the derived roofline peak
     out["fp32_probe_tflops"] = {"ffma": binding.fp32_probe(local, packed=False),
                                 "ffma2": binding.fp32_probe(local, packed=True)}
+    # and the shared-memory read-modify-write rate of the forward's window pattern, the
+    # forward's own roofline: algorithmic shared bytes = read + write of its window slots
+    # (S - 1 per pair for S >= 3, 2 for S = 2; 4 bytes each way)
+    smem_tbs = binding.smem_probe(local)
+    out["smem_rmw_probe_tbs"] = smem_tbs
+    if "fwd_cube" in per_kernel:
+        h_mm = geom["c_mm_per_us"] / geom["fs_mhz"]
+        sup = 4 * geom["sigma_mm"] if gauss else geom["a0_mm"]
+        S = int(np.floor(2 * sup / h_mm)) + 2
+        bpp = 8 * (S - 1 if S >= 3 else 2)
+        launches_f = per_kernel["fwd_cube"]["launches"] / args.steps
+        tbs = pairs * bpp / launches_f / (per_kernel["fwd_cube"]["ms_avg"] * 1e-3) / 1e12
+        out["roofline_fwd"] = {"bound": "smem", "kernel": "fwd_cube", "achieved": tbs, "peak": smem_tbs,
+                               "unit": "TB/s", "frac": tbs / smem_tbs, "bytes_per_pair": bpp,
+                               "peak_source": "measured: pasfm_smem_probe"}
     if rank == 0:
         print(json.dumps(out))
     ctx.close()

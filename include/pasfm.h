@@ -282,6 +282,12 @@ int pasfm_scale(pasfm_ctx* ctx, int64_t n, double alpha, float* x, void* stream)
  * about 10 ms; not for use while other work runs on the device.  tflops_out: host. */
 int pasfm_fp32_probe(int device, int packed, double* tflops_out);
 
+/* Measurement aid, no counterpart in the paper -- shared-memory read-modify-write
+ * throughput of `device` in TB/s, for the access pattern of the forward's window
+ * (each thread adds into its own column of a [slot][thread] array: one conflict-free
+ * 128-byte wavefront per warp load or store).  Same conditions as pasfm_fp32_probe. */
+int pasfm_smem_probe(int device, double* tbs_out);
+
 /* Allocation-free pose gradient.  No counterpart in the paper: this is a
  * library service for callers that must not allocate device memory while they
  * run -- code hosted inside an application that owns all device memory through

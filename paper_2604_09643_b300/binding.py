@@ -88,6 +88,7 @@ _SIGS = {
     "pasfm_nc_grad": ([_VP, ctypes.c_int64, _I, _VP, _VP, _I, _I, _VP, ctypes.c_double, _VP, _VP, _VP], _I),
     "pasfm_scale": ([_VP, ctypes.c_int64, ctypes.c_double, _VP, _VP], _I),
     "pasfm_fp32_probe": ([_I, _I, ctypes.POINTER(ctypes.c_double)], _I),
+    "pasfm_smem_probe": ([_I, ctypes.POINTER(ctypes.c_double)], _I),
     "pasfm_pose_grad_noalloc": ([_G, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP], _I),
     "pasfm_status": ([_VP, _VP, ctypes.POINTER(ctypes.c_uint32)], _I),
     "pasfm_timing_enable": ([_VP, _I], _I),
@@ -248,6 +249,13 @@ def fp32_probe(device=0, packed=False):
     """Measured FP32 FMA throughput of the device in TFLOP/s (scalar or packed two-wide FMA)."""
     v = ctypes.c_double()
     _check(lib().pasfm_fp32_probe(int(device), int(bool(packed)), ctypes.byref(v)))
+    return v.value
+
+
+def smem_probe(device=0):
+    """Measured shared-memory read-modify-write throughput of the device in TB/s."""
+    v = ctypes.c_double()
+    _check(lib().pasfm_smem_probe(int(device), ctypes.byref(v)))
     return v.value
 
 

@@ -482,6 +482,47 @@ __global__ void __launch_bounds__(256) fp32_probe_kernel(float* out, int iters, 
   if (s == -1.2345e30f) out[0] = s;
 }
 
+// Shared-memory read-modify-write probe, the access pattern of the forward's window:
+// each thread owns a column of a [64 slots][256 threads] float array (a warp's access
+// is one conflict-free 128-byte wavefront) and adds to 4 slot streams per round, 16
+// rounds unrolled with compile-time slots, so every update is a load, an add and a
+// store with no address arithmetic.
+__global__ void __launch_bounds__(256) smem_probe_kernel(float* out, int iters, float v) {
+  extern __shared__ float sp_win[];
+  // volatile: every update is a real load and store (a private column could otherwise
+  // live in registers), as in the forward, whose lanes' columns are indexed at run time
+  volatile float* col = sp_win + threadIdx.x;
+#pragma unroll
+  for (int k = 0; k < 64; ++k) col[k * 256] = 0.f;
+  for (int i = 0; i < iters; i += 16) {
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int s = (16 * j + 5 * r) & 63;
+        col[s * 256] += v;
+      }
+    }
+  }
+  float sum = 0.f;
+#pragma unroll
+  for (int k = 0; k < 64; ++k) sum += col[k * 256];
+  if (sum == -1.2345e30f) out[0] = sum;
+}
+
+double smem_probe_bytes(int blocks, int iters) {
+  // per update: one 128-byte load and one 128-byte store wavefront per warp
+  return double(blocks) * (256 / 32) * iters * 4 * 2 * 128.0;
+}
+
+cudaError_t smem_probe_launch(int blocks, int iters, float* out, cudaStream_t st) {
+  const int smem = 64 * 256 * 4;
+  cudaError_t e = cudaFuncSetAttribute(smem_probe_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  smem_probe_kernel<<<blocks, 256, smem, st>>>(out, iters, 1e-3f);
+  return cudaGetLastError();
+}
+
 double fp32_probe_flops(int blocks, int iters, bool packed) {
   return double(blocks) * 256.0 * iters * 8 * 2 * (packed ? 2 : 1);
 }

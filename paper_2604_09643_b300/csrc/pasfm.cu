@@ -1071,6 +1071,32 @@ int pasfm_fp32_probe(int device, int packed, double* tflops_out) {
   return PASFM_OK;
 }
 
+int pasfm_smem_probe(int device, double* tbs_out) {
+  if (!tbs_out) return fail(PASFM_EINVAL, "NULL output");
+  CUDA_TRY(cudaSetDevice(device));
+  int sms = 0;
+  CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
+  float* out = nullptr;
+  CUDA_TRY(cudaMalloc(&out, sizeof(float)));
+  const int blocks = sms * 3, iters = 1 << 14, reps = 5;
+  cudaEvent_t a = nullptr, b = nullptr;
+  cudaError_t e = cudaEventCreate(&a);
+  if (e == cudaSuccess) e = cudaEventCreate(&b);
+  if (e == cudaSuccess) e = smem_probe_launch(blocks, iters, out, nullptr);  // warm-up
+  if (e == cudaSuccess) e = cudaEventRecord(a, nullptr);
+  for (int r = 0; e == cudaSuccess && r < reps; ++r) e = smem_probe_launch(blocks, iters, out, nullptr);
+  if (e == cudaSuccess) e = cudaEventRecord(b, nullptr);
+  if (e == cudaSuccess) e = cudaEventSynchronize(b);
+  float ms = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+  if (a) cudaEventDestroy(a);
+  if (b) cudaEventDestroy(b);
+  cudaFree(out);
+  if (e != cudaSuccess) return fail(PASFM_ECUDA, "shared-memory probe: %s", cudaGetErrorString(e));
+  *tbs_out = reps * smem_probe_bytes(blocks, iters) / (ms * 1e-3) / 1e12;
+  return PASFM_OK;
+}
+
 int pasfm_status(pasfm_ctx* ctx, void* stream, uint32_t* bits) {
   if (!ctx) return fail(PASFM_EINVAL, "ctx is NULL");
   TRY(set_device(ctx));

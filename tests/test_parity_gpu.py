@@ -370,3 +370,10 @@ def test_fp32_probe_is_plausible(ctx):
     for packed in (False, True):
         tf = binding.fp32_probe(0, packed=packed)
         assert 5.0 < tf < 200.0, (packed, tf)
+
+
+def test_smem_probe_is_plausible(ctx):
+    """The shared-memory read-modify-write probe returns a rate between 5 and 60 TB/s
+    (148 SMs x one 128-byte wavefront per clock is 38.5 TB/s at 2032 MHz)."""
+    tbs = binding.smem_probe(0)
+    assert 5.0 < tbs < 60.0, tbs
