@@ -75,7 +75,6 @@ __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
 __device__ __forceinline__ float2 min2(float2 a, float b) { return make_float2(fminf(a.x, b), fminf(a.y, b)); }
 
 struct PairMath2 {
@@ -143,7 +142,7 @@ __device__ __forceinline__ void gauss_boundaries2(float2 beta1, float h, const G
   const float2 bc = fma2(f2(static_cast<float>(kc - 1)), f2(h), beta1);
   const float2 eb = mul2(f2(G.c1), mul2(bc, bc));
   E[kc] = make_float2(exp2f(eb.x), exp2f(eb.y));
-  const float2 ua = fma2(bc, f2(G.c2), f2(G.c3)), da = fma2(neg2(bc), f2(G.c2), f2(G.c3));
+  const float2 ua = fma2(bc, f2(G.c2), f2(G.c3)), da = fma2(bc, f2(-G.c2), f2(G.c3));
   float2 up = make_float2(exp2f(ua.x), exp2f(ua.y));
   float2 dn = make_float2(exp2f(da.x), exp2f(da.y));
 #pragma unroll
