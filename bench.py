@@ -327,8 +327,8 @@ def run_native(args):
     launches = ctx.launch_count() - l0
     ms = ev0.elapsed_time(ev1)
     per_kernel = {}
-    for name in ("fwd_cube", "fwd_reduce", "bwd_cube", "pose_rows", "grad6", "adam_vol", "adam_pose",
-                 "elem_pos", "loss_sum"):
+    for name in ("fwd_cube", "fwd_reduce", "bwd_cube", "diff_rows", "sum_parts", "pose_rows", "grad6", "adam_vol",
+                 "adam_pose", "elem_pos", "loss_sum"):
         t, n = ctx.timing_read(name)
         if n:
             per_kernel[name] = {"ms_total": t, "launches": n, "ms_avg": t / n}

@@ -446,6 +446,20 @@ __global__ void __launch_bounds__(256) scale_kernel(float* __restrict__ x, int64
     x[i] *= alpha;
 }
 
+__global__ void __launch_bounds__(256) diff_rows_kernel(const void* __restrict__ g, int dtype, int64_t rows,
+                                                        int Nt, int Ntd, float* __restrict__ D) {
+  const int64_t total = rows * Ntd;
+  for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < total;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t r = i / Ntd;
+    const int n = static_cast<int>(i - r * Ntd);
+    const int64_t base = r * Nt;
+    const float cur = n < Nt ? load_elem(g, base + n, dtype) : 0.f;
+    const float prev = (n >= 1 && n - 1 < Nt) ? load_elem(g, base + n - 1, dtype) : 0.f;
+    D[i] = cur - prev;
+  }
+}
+
 // FP32 throughput probe: kProbeChains independent FMA chains per thread for `iters`
 // rounds (a multiple of 16; PACKED: two-wide packed FMAs on float2 chains).  The chains converge to
 // c / (1 - m); their sum is stored only if it equals an impossible value, so no chain

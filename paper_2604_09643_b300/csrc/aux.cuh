@@ -41,6 +41,9 @@ __global__ void lowpass_kernel(const float* src, float* dst, int Nt, int r, int 
 __global__ void nc_grad_kernel(const float* sim, const void* meas, int dtype, const uint8_t* mask, int64_t n_rows,
                                int Nt, int meas_repeat, float scale, float* g, double* nc_out);
 __global__ void scale_kernel(float* x, int64_t n, float alpha);
+// first difference of every trace: D[r][n] = g[r][n] - g[r][n-1], n in [0, Ntd), g = 0
+// outside [0, Nt)
+__global__ void diff_rows_kernel(const void* g, int dtype, int64_t rows, int Nt, int Ntd, float* D);
 // FP32 throughput probe (fp32_probe_kernel): flops per launch and the launch itself
 double fp32_probe_flops(int blocks, int iters, bool packed);
 cudaError_t fp32_probe_launch(bool packed, int blocks, int iters, float* out, cudaStream_t st);

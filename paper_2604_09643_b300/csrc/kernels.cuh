@@ -367,7 +367,10 @@ __global__ void __launch_bounds__(256, 2)
 // each voxel's first slot), packed.  S1 = sum_s g_s (b_s - b_{s+1}) is the adjoint's;
 // lam S2 is minus the boundary-motion term of dW/dd (lam turns the boundary offsets
 // into derivatives of b and carries the sign, so that no operand needs negating).
-template <int S, int K, bool POSE>
+// GWIN: the window may hold the traces themselves (P.diff == 0: the pose-gradient-only
+// kernel of the allocation-free entry point); otherwise the sphere's windows always hold
+// the first differences.
+template <int S, int K, bool POSE, bool GWIN>
 __device__ __forceinline__ void slot_sums2(const float* ga, const float* gb, float2 beta1, const BwdParams& P,
                                            float2& S1, float2& S2, float& lam) {
   if constexpr (K == PASFM_KERNEL_GAUSS) {
@@ -433,22 +436,39 @@ __device__ __forceinline__ void slot_sums2(const float* ga, const float* gb, flo
     S1 = fma2(f2(P.gs.e_clamp), fma2(g_last, f2(-1.f), gn), S1);
     lam = -P.lam;  // S2 carries its own sign
   } else if constexpr (S >= 3) {
-    float2 g[S];
-#pragma unroll
-    for (int s = 0; s < S; ++s) g[s] = make_float2(ga[s], gb[s]);
     constexpr int n = S - 2;
-    const float2 M0 = fma2(g[0], f2(-1.f), g[n]);
-    float2 M1 = g[n], M2 = g[n];
-    if constexpr (n != 2) {
-      M1 = mul2(f2(static_cast<float>(n - 1)), g[n]);
-      M2 = mul2(f2(static_cast<float>((n - 1) * (n - 1))), g[n]);
-    }
+    float2 M0, M1, M2, dgl;
+    if (!GWIN || P.diff) {  // the window holds d_s = g_s - g_(s-1): M_p = sum_s (s - 1)^p d_s directly
+      float2 d[S];
 #pragma unroll
-    for (int s = 1; s <= n - 1; ++s) {
-      M1 = fma2(g[s], f2(-1.f), M1);
-      M2 = fma2(f2(-static_cast<float>(2 * s - 1)), g[s], M2);
+      for (int s = 1; s < S; ++s) d[s] = make_float2(ga[s], gb[s]);
+      M0 = d[1];
+      M1 = M2 = f2(0.f);
+#pragma unroll
+      for (int s = 2; s <= n; ++s) {
+        M0 = add2(M0, d[s]);
+        M1 = s == 2 ? d[2] : fma2(f2(static_cast<float>(s - 1)), d[s], M1);
+        M2 = s == 2 ? d[2] : fma2(f2(static_cast<float>((s - 1) * (s - 1))), d[s], M2);
+      }
+      dgl = d[S - 1];
+    } else {
+      float2 g[S];
+#pragma unroll
+      for (int s = 0; s < S; ++s) g[s] = make_float2(ga[s], gb[s]);
+      M0 = fma2(g[0], f2(-1.f), g[n]);
+      M1 = g[n];
+      M2 = g[n];
+      if constexpr (n != 2) {
+        M1 = mul2(f2(static_cast<float>(n - 1)), g[n]);
+        M2 = mul2(f2(static_cast<float>((n - 1) * (n - 1))), g[n]);
+      }
+#pragma unroll
+      for (int s = 1; s <= n - 1; ++s) {
+        M1 = fma2(g[s], f2(-1.f), M1);
+        M2 = fma2(f2(-static_cast<float>(2 * s - 1)), g[s], M2);
+      }
+      dgl = fma2(g[n], f2(-1.f), g[S - 1]);
     }
-    const float2 dgl = fma2(g[n], f2(-1.f), g[S - 1]);
     const float2 bl = fma2(f2(static_cast<float>(S - 2)), f2(P.h), beta1);
     const float2 tl = min2(bl, P.supf);
     const float2 X = fma2(f2(P.h), M1, mul2(beta1, M0));
@@ -465,10 +485,10 @@ __device__ __forceinline__ void slot_sums2(const float* ga, const float* gb, flo
     float s1[2], s2[2];
 #pragma unroll
     for (int v = 0; v < 2; ++v) {
-      const float g0 = gv[v][0], g1 = gv[v][1];
+      const float d1 = (!GWIN || P.diff) ? gv[v][1] : gv[v][1] - gv[v][0];  // g_1 - g_0
       const float bc = fminf(b1[v], P.supf);
-      s1[v] = fmaf(bc * bc, g1 - g0, P.sup2 * (g0 - g1));
-      s2[v] = POSE ? (b1[v] < P.supf ? b1[v] : 0.f) * (g1 - g0) : 0.f;  // minus the sum
+      s1[v] = fmaf(bc, bc, -P.sup2) * d1;
+      s2[v] = POSE ? (b1[v] < P.supf ? b1[v] : 0.f) * d1 : 0.f;  // minus the sum
     }
     S1 = make_float2(s1[0], s1[1]);
     S2 = make_float2(s2[0], s2[1]);
@@ -666,7 +686,7 @@ __global__ void __launch_bounds__(C* C, (C == 16 ? 3 : 8))
         if (k + 1 == C - 1) seen = max(seen, m.idx1);
         float2 S1, S2 = f2(0.f);
         float lam;
-        slot_sums2<S, K, POSE>(wv + min(m.idx0, max_idx), wv + min(m.idx1, max_idx), m.beta1, P, S1, S2, lam);
+        slot_sums2<S, K, POSE, !ADJ>(wv + min(m.idx0, max_idx), wv + min(m.idx1, max_idx), m.beta1, P, S1, S2, lam);
         const float2 t1 = mul2(m.rs, S1);
         if (ADJ) bacc[k2] = add2(bacc[k2], t1);
         if (POSE) {  // minus the coefficient: p0 (1/d^2) (t1 - dW/dd boundary term)

@@ -59,6 +59,8 @@ struct Rec {
 
 constexpr size_t kDefaultPartialBudget = size_t(4) << 30;
 constexpr int kMaxParts = 8;  // backward CTAs per cube (item parts); bounds the per-part adjoint buffer
+// length of a difference trace: samples 0..Nt (the last is minus g[Nt-1]), padded to 4 floats
+inline int diff_len(int Nt) { return (Nt + 1 + 3) & ~3; }
 constexpr int kFwdWmax16 = 128;  // forward window cap for 16^3 cubes (8 warps x W x 128 B)
 constexpr int kFwdWmax8 = 200;   // forward window cap for 8^3 cubes
 
@@ -169,7 +171,7 @@ int frames_per_chunk(size_t per_frame, size_t budget, int F) {
 struct pasfm_ctx {
   int device = 0;
   unsigned* status = nullptr;
-  Buf xw, part, n0, gres, vgrad, gpart, G, grad6, lpart, lscalar, taps, vparts, gw, tpart;
+  Buf xw, part, n0, gres, vgrad, gpart, G, grad6, lpart, lscalar, taps, vparts, gw, tpart, gdiff;
   int sms = 0;  // streaming multiprocessors of the device
   size_t budget = kDefaultPartialBudget;
   bool timing = false;
@@ -431,12 +433,30 @@ int run_forward(pasfm_ctx* ctx, const Geo& G, const Plan& pl, const void* p0, co
   return PASFM_OK;
 }
 
-// Backward: mode 1 adjoint into vol, 2 pose gradient into G rows, 3 both.
+// Backward: mode 1 adjoint into vol, 2 pose gradient into G rows, 3 both.  For the sphere
+// the kernel reads the traces' first differences (its slot sums need only those), formed
+// here into the workspace.
 int run_backward(pasfm_ctx* ctx, const Geo& G, const Plan& pl, int mode, const void* p0, const double* xw,
-                 const void* gsig, int dtype_sig, const uint8_t* mask, float* vol, double* Gout,
+                 const void* gsig_in, int dtype_in, const uint8_t* mask, float* vol, double* Gout,
                  cudaStream_t st) {
   const pasfm_geom& g = G.g;
-  const int F = g.n_frames, E = g.n_elem, Nt = g.n_samples;
+  const int F = g.n_frames, E = g.n_elem;
+  const bool diff = pl.K == PASFM_KERNEL_SPHERE;
+  const void* gsig = gsig_in;
+  int dtype_sig = dtype_in, Nt = g.n_samples;
+  if (diff && G.n_rows > 0) {
+    const int Ntd = diff_len(g.n_samples);
+    TRY(ctx->ensure(ctx->gdiff, size_t(G.n_rows) * Ntd * 4));
+    const int64_t total = G.n_rows * int64_t(Ntd);
+    cudaEvent_t t = ctx->begin(st);
+    diff_rows_kernel<<<static_cast<unsigned>(std::min<int64_t>((total + 255) / 256, 148 * 32)), 256, 0, st>>>(
+        gsig_in, dtype_in, G.n_rows, g.n_samples, Ntd, static_cast<float*>(ctx->gdiff.p));
+    ctx->end("diff_rows", t, st);
+    TRY(check_launch("diff_rows"));
+    gsig = ctx->gdiff.p;
+    dtype_sig = PASFM_F32;
+    Nt = Ntd;
+  }
   const bool pose = mode & 2;
   const int Fc = pose ? frames_per_chunk(bwd_per_frame(G, pl), ctx->budget, F) : std::max(F, 1);
   if (pose) TRY(ctx->ensure(ctx->gpart, size_t(Fc) * E * pl.ncubes * 24));
@@ -481,6 +501,7 @@ int run_backward(pasfm_ctx* ctx, const Geo& G, const Plan& pl, int mode, const v
   P.dz = g.dz;
   set_bwd_profile(pl, &P);
   P.use_tma = use_tma;
+  P.diff = diff ? 1 : 0;
   P.status = ctx->status;
   const size_t smem = pl.C == 16 ? BwdLayout<16>::total(pl.WP) : BwdLayout<8>::total(pl.WP);
   const int per_sm = bwd_occupancy(pl.K, pl.S)(pl.C, mode, smem);
@@ -641,7 +662,7 @@ int pasfm_destroy(pasfm_ctx* ctx) {
   if (!ctx) return PASFM_OK;
   cudaSetDevice(ctx->device);
   for (Buf* b : {&ctx->xw, &ctx->part, &ctx->n0, &ctx->gres, &ctx->vgrad, &ctx->gpart, &ctx->G, &ctx->grad6,
-                 &ctx->lpart, &ctx->lscalar, &ctx->taps, &ctx->vparts, &ctx->gw, &ctx->tpart})
+                 &ctx->lpart, &ctx->lscalar, &ctx->taps, &ctx->vparts, &ctx->gw, &ctx->tpart, &ctx->gdiff})
     if (b->p) cudaFree(b->p);
   for (auto& r : ctx->recs) {
     cudaEventDestroy(r.a);
@@ -673,6 +694,7 @@ int pasfm_workspace_size(const pasfm_geom* geom, size_t* bytes) {
   b += size_t(Ff) * fwd_per_frame(G, pl);                                   // part + n0
   b += size_t(Fb) * bwd_per_frame(G, pl);                                   // gpart
   b += size_t(G.n_rows) * G.g.n_samples * 4;                                // residual (step)
+  if (G.g.kernel == PASFM_KERNEL_SPHERE) b += size_t(G.n_rows) * diff_len(G.g.n_samples) * 4;  // its difference
   b += size_t(G.nvox) * 4;                                                  // volume gradient (step)
   b += size_t(G.nvox) * 4 * kMaxParts;                                      // per-part adjoint sums
   b += size_t(G.nvox) * 12 + size_t(tgv_tiles(G.g.nx, G.g.ny, G.g.nz)) * 8;  // TGV grad_w, energy partials
@@ -694,6 +716,7 @@ int pasfm_reserve(pasfm_ctx* ctx, const pasfm_geom* geom) {
   TRY(ctx->ensure(ctx->n0, size_t(Ff) * G.g.n_elem * pl.ncubes * 4));
   TRY(ctx->ensure(ctx->gpart, size_t(Fb) * G.g.n_elem * pl.ncubes * 24));
   TRY(ctx->ensure(ctx->gres, size_t(G.n_rows) * G.g.n_samples * 4));
+  if (G.g.kernel == PASFM_KERNEL_SPHERE) TRY(ctx->ensure(ctx->gdiff, size_t(G.n_rows) * diff_len(G.g.n_samples) * 4));
   TRY(ctx->ensure(ctx->vgrad, size_t(G.nvox) * 4));
   TRY(ctx->ensure(ctx->vparts, size_t(G.nvox) * 4 * kMaxParts));
   TRY(ctx->ensure(ctx->G, size_t(G.n_rows) * 24));
@@ -855,6 +878,7 @@ int pasfm_step_tgv(pasfm_ctx* ctx, const pasfm_geom* geom, void* p0, double* pos
 
   TRY(ctx->ensure(ctx->xw, size_t(G.n_rows) * 24));
   TRY(ctx->ensure(ctx->gres, size_t(G.n_rows) * G.g.n_samples * 4));
+  if (G.g.kernel == PASFM_KERNEL_SPHERE) TRY(ctx->ensure(ctx->gdiff, size_t(G.n_rows) * diff_len(G.g.n_samples) * 4));
   TRY(ctx->ensure(ctx->vgrad, size_t(G.nvox) * 4));
   TRY(ctx->ensure(ctx->vparts, size_t(G.nvox) * 4 * kMaxParts));
   TRY(ctx->ensure(ctx->G, size_t(G.n_rows) * 24));

@@ -119,6 +119,7 @@ struct BwdParams {
   float lam;            // pose-coefficient weight of the boundary term: 2 (sphere), 1 / sigma^2 (Gaussian)
   GaussConst gs;
   int use_tma;
+  int diff;             // sphere: the staged trace is the difference g_n - g_(n-1)
   unsigned* status;
 };
 
