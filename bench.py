@@ -16,6 +16,7 @@ from __future__ import annotations
 
 import argparse
 import hashlib
+import re
 import json
 import os
 import statistics
@@ -85,15 +86,25 @@ KERNEL_SOURCES = {
 }
 
 
+def _code_only(text):
+    """Source text without comments and blank lines, so that editing a comment does not
+    invalidate counters taken on the same code."""
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    lines = (re.sub(r"(^|\s)(//|#(?!include|define|if|endif|else|elif|pragma|undef)).*$", "", ln).rstrip()
+             for ln in text.splitlines())
+    return "\n".join(ln for ln in lines if ln.strip())
+
+
 def kernel_src_hash(kernel="bwd_cube"):
-    """Hash of the sources that define `kernel` (a KERNEL_SOURCES key, '_gauss' suffix ignored)
-    and of the build script that holds their compiler flags."""
+    """Hash of the code (comments stripped) of the sources that define `kernel` (a
+    KERNEL_SOURCES key, '_gauss' suffix ignored) and of the build script that holds their
+    compiler flags."""
     h = hashlib.sha256()
     for fn in KERNEL_SOURCES[kernel.replace("_gauss", "")]:
-        with open(os.path.join(ROOT, "paper_2604_09643_b300", "csrc", fn), "rb") as fh:
-            h.update(fh.read())
-    with open(os.path.join(ROOT, "paper_2604_09643_b300", "build.py"), "rb") as fh:
-        h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2604_09643_b300", "csrc", fn), encoding="utf-8") as fh:
+            h.update(_code_only(fh.read()).encode())
+    with open(os.path.join(ROOT, "paper_2604_09643_b300", "build.py"), encoding="utf-8") as fh:
+        h.update(_code_only(fh.read()).encode())
     return h.hexdigest()[:16]
 
 

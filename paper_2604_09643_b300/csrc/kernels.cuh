@@ -16,7 +16,8 @@
 //   bwd_cube_kernel  -- adjoint v = A^T g and/or pose gradient.  Voxel-
 //                       stationary: a thread owns a row of C voxels along x; the
 //                       CTA walks all (frame, element) traces in batches of 32
-//                       whose sample windows are staged by 2-D TMA loads into a
+//                       whose sample windows (for the sphere, of the traces'
+//                       first differences) are staged by 2-D TMA loads into a
 //                       double buffer.  The adjoint is an atomic-free gather; the
 //                       pose gradient is reduced per element with warp shuffles
 //                       and a fixed-order block reduction, then carried to FP64.
