@@ -139,6 +139,7 @@ class C2FConfig:
     search_rounds: int = 0         # coarsest level: Stage 2 grid searches after its joint steps
     search_radius_mm: float = 0.8  # half-width of the cubic translation grid
     search_step_mm: float = 0.1
+    search_coarse_to_fine: bool = True  # shrinking 5-point grids instead of the full grid
     search_joint_steps: int = 150  # joint steps after each search round
     search_batch: int = 512        # candidates per forward call
     refine_every: int = 0          # 0 disables the rigid-consensus pass
@@ -235,29 +236,51 @@ def rigid_consensus(ctx, geom, p0, poses, elem, meas, mask, cfg: C2FConfig, rng)
     return torch.from_numpy(new_mask).to(poses.device), poses
 
 
+def search_grids(radius_mm, step_mm, coarse_to_fine):
+    """Per-axis offset grids of a translation search: the full grid of half-width
+    radius_mm at step_mm, or (coarse_to_fine) shrinking 5-point grids -- spacing
+    radius/2, then half the previous spacing around the best offset so far -- down to
+    step_mm."""
+    if not coarse_to_fine:
+        return [np.arange(-radius_mm, radius_mm + 1e-9, step_mm)]
+    grids, r = [], radius_mm
+    while True:
+        s = max(r / 2, step_mm)
+        grids.append(np.arange(-2, 3) * s)
+        if s <= step_mm * (1 + 1e-9):
+            return grids
+        r = s
+
+
 def search_translations(ctx, geom, p0, poses, elem, meas, radius_mm, step_mm, first_frame=1, batch=512,
-                        mask=None):
+                        mask=None, coarse_to_fine=True):
     """Stage 2 coarse search: for every frame from `first_frame` on, translation
-    offsets on a cubic grid of half-width radius_mm are scored by the NC loss of
-    Eq. 3 (candidates are evaluated as extra frames of one forward call) and the
-    frame takes the best candidate (Top-1).  Returns the per-frame best scores."""
-    ax = np.arange(-radius_mm, radius_mm + 1e-9, step_mm)
-    offs = np.array(list(itertools.product(ax, ax, ax)))
+    offsets are scored by the NC loss of Eq. 3 (candidates are evaluated as extra
+    frames of one forward call) and the frame takes the best candidate (Top-1).  The
+    offsets are the cubic grid of half-width radius_mm at step_mm, or with
+    coarse_to_fine shrinking 5-point grids around the best offset so far (375
+    candidates for a 1.2 mm radius at 0.15 mm against 4913).  Returns the per-frame
+    best scores."""
     P = poses.cpu().numpy()
     dev = poses.device
     best_scores = []
+    grids = search_grids(radius_mm, step_mm, coarse_to_fine)
     for f in range(first_frame, geom["n_frames"]):
         best, best_pose = math.inf, None
-        for c0 in range(0, len(offs), batch):
-            o = offs[c0:c0 + batch]
-            cand = np.repeat(P[f:f + 1], len(o), axis=0)
-            cand[:, :, 3] += o
-            gk = dict(geom, n_frames=len(o))
-            sim = ctx.forward(gk, p0, elem, torch.from_numpy(cand).to(dev))
-            sc = ctx.nc_scores(sim, meas[f], None if mask is None else mask[f]).cpu().numpy()
-            i = int(np.argmin(sc))
-            if sc[i] < best:
-                best, best_pose = float(sc[i]), cand[i]
+        centre = P[f].copy()
+        for ax in grids:
+            offs = np.array(list(itertools.product(ax, ax, ax)))
+            for c0 in range(0, len(offs), batch):
+                o = offs[c0:c0 + batch]
+                cand = np.repeat(centre[None], len(o), axis=0)
+                cand[:, :, 3] += o
+                gk = dict(geom, n_frames=len(o))
+                sim = ctx.forward(gk, p0, elem, torch.from_numpy(cand).to(dev))
+                sc = ctx.nc_scores(sim, meas[f], None if mask is None else mask[f]).cpu().numpy()
+                i = int(np.argmin(sc))
+                if sc[i] < best:
+                    best, best_pose = float(sc[i]), cand[i]
+            centre = best_pose.copy()
         P[f] = best_pose
         best_scores.append(best)
     poses.copy_(torch.from_numpy(P).to(dev))
@@ -348,7 +371,7 @@ def reconstruct(ctx: binding.Context, geom_fine, elem, meas, poses_init, cfg: C2
             for _ in range(cfg.search_rounds):
                 search_translations(ctx, geom, p0, poses, elem_d, meas_l, cfg.search_radius_mm,
                                     cfg.search_step_mm, first_frame=1 if cfg.fix_frame0 else 0,
-                                    batch=cfg.search_batch, mask=mask)
+                                    batch=cfg.search_batch, mask=mask, coarse_to_fine=cfg.search_coarse_to_fine)
                 adam = binding.AdamState(geom, dev, lr_vol=cfg.lr_vol * decay, lr_rot=cfg.lr_rot * decay,
                                          lr_trans=cfg.lr_trans * decay, nonneg=cfg.nonneg,
                                          fix_frame0=cfg.fix_frame0)

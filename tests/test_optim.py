@@ -92,3 +92,22 @@ def test_time_decimation_factor():
         assert optim.time_decimation(fine, optim.level_geometry(fine, (n, n, n)), cfg) == k
     assert optim.time_decimation(synth.make_geom((64, 64, 64), 0.1, 4, 1, 100),
                                  optim.level_geometry(fine, (16, 16, 16)), cfg) == 1
+
+
+def test_search_grids():
+    """Full grid: every offset at step_mm within the radius.  Coarse to fine: 5-point
+    grids whose spacing halves from radius / 2 down to step_mm, so the union of the
+    nested grids reaches every offset of the full grid from the right centre, with
+    far fewer candidates."""
+    full = optim.search_grids(1.2, 0.15, False)
+    assert len(full) == 1 and len(full[0]) == 17
+    np.testing.assert_allclose(full[0][[0, -1]], [-1.2, 1.2])
+    grids = optim.search_grids(1.2, 0.15, True)
+    np.testing.assert_allclose([g[1] - g[0] for g in grids], [0.6, 0.3, 0.15])
+    assert all(len(g) == 5 and abs(g[2]) < 1e-12 for g in grids)
+    assert sum(len(g) ** 3 for g in grids) == 375
+    # nested reach: the sum of one offset per level covers the full grid's span
+    assert abs(sum(g[-1] for g in grids) - 2.1) < 1e-9
+    # a radius already at the step: one 5-point grid at step_mm
+    one = optim.search_grids(0.1, 0.1, True)
+    assert len(one) == 1 and abs(one[0][1] - one[0][0] - 0.1) < 1e-12
