@@ -280,8 +280,10 @@ def search_translations(ctx, geom, p0, poses, elem, meas, radius_mm, step_mm, fi
                 i = int(np.argmin(sc))
                 if sc[i] < best:
                     best, best_pose = float(sc[i]), cand[i]
-            centre = best_pose.copy()
-        P[f] = best_pose
+            if best_pose is not None:  # no finite score (no signal at any candidate): keep the pose
+                centre = best_pose.copy()
+        if best_pose is not None:
+            P[f] = best_pose
         best_scores.append(best)
     poses.copy_(torch.from_numpy(P).to(dev))
     return best_scores
