@@ -204,6 +204,17 @@ def make_workload(seed_offset=0, n_frames=64, workload="full_scan", sigma=None):
     return scan, p_init, poses_init
 
 
+def fwd_smem_bytes_per_pair(geom):
+    """Algorithmic shared-memory bytes per voxel-element pair of the forward: the load and
+    store (4 bytes each) of every window slot the pair writes -- S - 1 slots of the
+    running-sum window for S >= 3, the two slots of the direct dipole for S = 2, with
+    S = floor(2 sup / h) + 2 slots and sup = a0 or 4 sigma."""
+    h = geom["c_mm_per_us"] / geom["fs_mhz"]
+    sup = 4 * geom["sigma_mm"] if geom.get("kernel") == "gauss" else geom["a0_mm"]
+    S = int(np.floor(2 * sup / h)) + 2
+    return 8 * (S - 1 if S >= 3 else 2)
+
+
 def pairs_and_m(geom):
     h = geom["c_mm_per_us"] / geom["fs_mhz"]
     sup = 4 * geom["sigma_mm"] if geom.get("kernel") == "gauss" else geom["a0_mm"]
@@ -465,10 +476,7 @@ def run_native(args):
     smem_tbs = binding.smem_probe(local)
     out["smem_rmw_probe_tbs"] = smem_tbs
     if "fwd_cube" in per_kernel:
-        h_mm = geom["c_mm_per_us"] / geom["fs_mhz"]
-        sup = 4 * geom["sigma_mm"] if gauss else geom["a0_mm"]
-        S = int(np.floor(2 * sup / h_mm)) + 2
-        bpp = 8 * (S - 1 if S >= 3 else 2)
+        bpp = fwd_smem_bytes_per_pair(geom)
         launches_f = per_kernel["fwd_cube"]["launches"] / args.steps
         tbs = pairs * bpp / launches_f / (per_kernel["fwd_cube"]["ms_avg"] * 1e-3) / 1e12
         out["roofline_fwd"] = {"bound": "smem", "kernel": "fwd_cube", "achieved": tbs, "peak": smem_tbs,

@@ -54,3 +54,13 @@ def test_clock_summary_parses_nvidia_smi_rows(tmp_path):
     s = c.summary()
     assert s["sm_max_mhz"] == 2032 and s["sm_mhz"] == pytest.approx(2021.0) and s["reasons"] == ["sw_power_cap"]
     assert s["samples"] == 2
+
+
+def test_forward_shared_bytes_per_pair():
+    """24 bytes per pair on the full scan (S = 4: three running-sum slots), 88 for the
+    Gaussian at sigma = 0.05 mm (S = 12), 16 for a sphere narrower than a sample (S = 2)."""
+    from paper_2604_09643_b300 import synth
+    g = synth.make_geom((8, 8, 8), 0.1, 4, 1, 64)
+    assert bench.fwd_smem_bytes_per_pair(g) == 24
+    assert bench.fwd_smem_bytes_per_pair(dict(g, kernel="gauss", sigma_mm=0.05)) == 88
+    assert bench.fwd_smem_bytes_per_pair(dict(g, a0_mm=0.015)) == 16
