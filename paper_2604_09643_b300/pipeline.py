@@ -46,6 +46,10 @@ class PipelineConfig:
     tgv: tuple | None = None             # (alpha1, alpha0, eps, lr_w) for Stages 1 and 5
     search_radius_mm: float = 1.5        # Stage 2 grid half-width around the prior position
     search_step_mm: float = 0.25
+    # grid at twice the step, then 3x3x3 at the step around its 2 Top-K best: Stage 2 of the
+    # bowl in 1.4 s instead of 2.4 s, same final error, but fewer Stage 2 elements within the
+    # inlier tolerance (65% against 77%), so the full grid stays the default
+    search_coarse_to_fine: bool = False
     top_k: int = 4
     refine_steps: int = 60
     refine_lr_mm: float = 0.02
@@ -121,24 +125,44 @@ def stage2_localise(ctx, geom, p0, elem, pose_b0, meas_b, cfg):
     dev = ctx.device
     E, T = meas_b.shape
     prior = elem @ pose_b0[:, :3].T + pose_b0[:, 3]
-    ax = np.arange(-cfg.search_radius_mm, cfg.search_radius_mm + 1e-9, cfg.search_step_mm)
-    offs = np.array(list(itertools.product(ax, ax, ax)))
-    K = len(offs)
     ident = _T(_IDENTITY, dev)
     s0 = cfg.smoothing[0]
     meas_s0 = ctx.lowpass(meas_b, s0) if s0 > 0 else meas_b
-    # coarse search: Top-K candidates per element under the widest smoothing
-    top = np.zeros((E, cfg.top_k, 3))
-    for j0 in range(0, E, cfg.element_batch):
-        js = np.arange(j0, min(E, j0 + cfg.element_batch))
-        pts = (prior[js, None, :] + offs[None, :, :]).reshape(-1, 3)
-        sim = ctx.forward(_points_geom(geom, len(pts)), p0, _T(pts, dev), ident)
-        if s0 > 0:
-            sim = ctx.lowpass(sim, s0)
-        _, nc = ctx.nc_grad(sim, meas_s0[j0:j0 + len(js)], meas_repeat=K)
-        nc = nc.reshape(len(js), K).cpu().numpy()
-        best = np.argsort(nc, axis=1, kind="stable")[:, :cfg.top_k]
-        top[js] = pts.reshape(len(js), K, 3)[np.arange(len(js))[:, None], best]
+
+    def grid(radius, step):
+        ax = np.arange(-radius, radius + 1e-9, step)
+        return np.array(list(itertools.product(ax, ax, ax)))
+
+    def top_of(cands, keep):
+        """cands [E][K][3] -> the `keep` best (lowest NC under the widest smoothing) per element."""
+        K = cands.shape[1]
+        out = np.zeros((E, keep, 3))
+        for j0 in range(0, E, cfg.element_batch):
+            js = np.arange(j0, min(E, j0 + cfg.element_batch))
+            pts = cands[js].reshape(-1, 3)
+            sim = ctx.forward(_points_geom(geom, len(pts)), p0, _T(pts, dev), ident)
+            if s0 > 0:
+                sim = ctx.lowpass(sim, s0)
+            _, nc = ctx.nc_grad(sim, meas_s0[j0:j0 + len(js)], meas_repeat=K)
+            nc = nc.reshape(len(js), K).cpu().numpy()
+            order = np.argsort(nc, axis=1, kind="stable")
+            for r, j in enumerate(js):  # the best distinct positions (neighbourhoods may overlap)
+                pts_j = cands[j][order[r]]
+                _, first = np.unique(np.round(pts_j, 6), axis=0, return_index=True)
+                pick = np.sort(first)[:keep]
+                out[j, :len(pick)] = pts_j[pick]
+                out[j, len(pick):] = pts_j[pick[-1]]
+        return out
+
+    # coarse search: Top-K candidates per element under the widest smoothing; with
+    # coarse_to_fine a grid at twice the step first, then 3x3x3 at the step around its
+    # 2 Top-K best (343 + 216 candidates per element for 1.5 mm at 0.25 mm, against 2197)
+    if cfg.search_coarse_to_fine:
+        c1 = top_of(prior[:, None, :] + grid(cfg.search_radius_mm, 2 * cfg.search_step_mm)[None], 2 * cfg.top_k)
+        loc = grid(cfg.search_step_mm, cfg.search_step_mm)
+        top = top_of((c1[:, :, None, :] + loc[None, None]).reshape(E, -1, 3), cfg.top_k)
+    else:
+        top = top_of(prior[:, None, :] + grid(cfg.search_radius_mm, cfg.search_step_mm)[None], cfg.top_k)
     # gradient refinement of all priors at once, smoothing decaying in phases
     X = top.reshape(-1, 3).copy()
     m = np.zeros_like(X)
