@@ -133,8 +133,9 @@ def stage2_localise(ctx, geom, p0, elem, pose_b0, meas_b, cfg):
         ax = np.arange(-radius, radius + 1e-9, step)
         return np.array(list(itertools.product(ax, ax, ax)))
 
-    def top_of(cands, keep):
-        """cands [E][K][3] -> the `keep` best (lowest NC under the widest smoothing) per element."""
+    def top_of(cands, keep, distinct=False):
+        """cands [E][K][3] -> the `keep` best (lowest NC under the widest smoothing) per
+        element; `distinct` drops repeated positions (overlapping neighbourhoods)."""
         K = cands.shape[1]
         out = np.zeros((E, keep, 3))
         for j0 in range(0, E, cfg.element_batch):
@@ -146,7 +147,10 @@ def stage2_localise(ctx, geom, p0, elem, pose_b0, meas_b, cfg):
             _, nc = ctx.nc_grad(sim, meas_s0[j0:j0 + len(js)], meas_repeat=K)
             nc = nc.reshape(len(js), K).cpu().numpy()
             order = np.argsort(nc, axis=1, kind="stable")
-            for r, j in enumerate(js):  # the best distinct positions (neighbourhoods may overlap)
+            if not distinct:
+                out[js] = cands[js][np.arange(len(js))[:, None], order[:, :keep]]
+                continue
+            for r, j in enumerate(js):
                 pts_j = cands[j][order[r]]
                 _, first = np.unique(np.round(pts_j, 6), axis=0, return_index=True)
                 pick = np.sort(first)[:keep]
@@ -160,7 +164,7 @@ def stage2_localise(ctx, geom, p0, elem, pose_b0, meas_b, cfg):
     if cfg.search_coarse_to_fine:
         c1 = top_of(prior[:, None, :] + grid(cfg.search_radius_mm, 2 * cfg.search_step_mm)[None], 2 * cfg.top_k)
         loc = grid(cfg.search_step_mm, cfg.search_step_mm)
-        top = top_of((c1[:, :, None, :] + loc[None, None]).reshape(E, -1, 3), cfg.top_k)
+        top = top_of((c1[:, :, None, :] + loc[None, None]).reshape(E, -1, 3), cfg.top_k, distinct=True)
     else:
         top = top_of(prior[:, None, :] + grid(cfg.search_radius_mm, cfg.search_step_mm)[None], cfg.top_k)
     # gradient refinement of all priors at once, smoothing decaying in phases
