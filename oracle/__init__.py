@@ -68,7 +68,7 @@ def load(path: str):
     L.oracle_pose_grad.argtypes = [g, fp, dp, dp, ctypes.c_void_p, dp, ctypes.c_void_p]
     L.oracle_element_gradient_rows.argtypes = [g, fp, dp, dp, ctypes.c_void_p, ctypes.c_int64, dp]
     L.oracle_element_gradient_bounds.argtypes = [g, fp, dp, dp, ctypes.c_void_p, ctypes.c_int64,
-                                                 ctypes.c_double, dp, dp]
+                                                 ctypes.c_double, dp, dp, ctypes.c_void_p]
     L.oracle_loss.argtypes = [g, dp, dp, ctypes.c_void_p, dp]
     L.oracle_loss.restype = ctypes.c_double
     return L
@@ -189,16 +189,20 @@ def element_gradient_rows(geom, p0, gsig, xw, rows):
     return out
 
 
-def element_gradient_bounds(geom, p0, gsig, xw, rows, eps):
+def element_gradient_bounds(geom, p0, gsig, xw, rows, eps, counts=False):
     """(Gmid, Ghalf) [len(rows)][3]: every one-sided choice of the derivative at
-    support-edge boundaries within eps mm of +-a0 lies in Gmid +- Ghalf."""
+    support-edge boundaries within eps mm of +-a0 lies in Gmid +- Ghalf.  With
+    ``counts`` also the number of such boundaries per row that carry a nonzero
+    term (0: the row's gradient is the strict one whatever side is taken)."""
     g = make_geom(geom)
     r, rp = _opt_ptr(rows, np.int64)
     mid = np.zeros((len(r), 3))
     half = np.zeros((len(r), 3))
+    n = np.zeros(len(r), dtype=np.int64)
     lib().oracle_element_gradient_bounds(ctypes.byref(g), np.ascontiguousarray(p0, dtype=np.float32),
-                                         _f64(gsig), _f64(xw), rp, len(r), float(eps), mid, half)
-    return mid, half
+                                         _f64(gsig), _f64(xw), rp, len(r), float(eps), mid, half,
+                                         n.ctypes.data_as(ctypes.c_void_p))
+    return (mid, half, n) if counts else (mid, half)
 
 
 def loss(geom, sig, meas, mask=None):

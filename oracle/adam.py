@@ -13,8 +13,14 @@ differ (rad, mm).  Frames flagged fixed (the gauge frame) are not moved.  The
 optional non-negativity projection of the volume follows the paper's remark
 that photoacoustic initial pressures are positive.
 
-Pinned: the first step with eps -> 0 moves every parameter by exactly
--lr * sign(g), a closed form of the definition.
+Pinned by closed forms of the moment recurrences (geometric sums, eps = 0):
+the first step moves every parameter by exactly -lr sign(g); a constant
+gradient keeps doing so at every step (bias corrections); alternating +-g gives
+steps lr (1-b1)/(1+b1) and -lr (1-b1+b1^2)/(1+b1+b1^2) at k = 2, 3; g then 0
+gives -lr [b1/(1+b1)] / sqrt(b2/(1+b2)) at k = 2 (separates b1 from b2); a fixed
+frame keeps its pose while its moments advance.  Planted mistakes (swapped
+betas, |g| in place of g^2, missing or frozen bias corrections, swapped
+rotation and translation rates, a right-hand retraction) each fail one of these.
 """
 from __future__ import annotations
 

@@ -268,16 +268,19 @@ void oracle_element_gradient_rows(const oracle_geom* g, const float* p0, const d
  * sum_n g_n dW_n/dd, or nothing.  Gmid takes half of every such c_b and Ghalf
  * their half-magnitudes (componentwise, times |x - r| / d), so every choice of
  * sides lies in [Gmid - Ghalf, Gmid + Ghalf].  With eps = 0, Gmid equals the
- * strict gradient and Ghalf is 0. */
+ * strict gradient and Ghalf is 0.  namb (may be NULL) receives per row the number
+ * of such boundaries whose c_b is not zero: a row with none has a single
+ * admissible gradient, the strict one. */
 void oracle_element_gradient_bounds(const oracle_geom* g, const float* p0, const double* gsig,
                                     const double* xw, const int64_t* rows, int64_t n_rows, double eps,
-                                    double* Gmid, double* Ghalf) {
+                                    double* Gmid, double* Ghalf, int64_t* namb) {
   const double h = g->c / g->fs, rho = oracle_support(g);
 #pragma omp parallel for schedule(dynamic, 1)
   for (int64_t k = 0; k < n_rows; ++k) {
     const double* x = xw + 3 * rows[k];
     const double* gs = gsig + rows[k] * g->n_samples;
     double mid[3] = {0, 0, 0}, half[3] = {0, 0, 0};
+    int64_t count = 0;
     for (int iz = 0; iz < g->nz; ++iz)
       for (int iy = 0; iy < g->ny; ++iy)
         for (int ix = 0; ix < g->nx; ++ix) {
@@ -298,6 +301,7 @@ void oracle_element_gradient_bounds(const oracle_geom* g, const float* p0, const
             const double strict = fabs(wb) < rho ? cb : 0.0;
             s += 0.5 * cb - strict;
             amb += 0.5 * fabs(cb);
+            if (cb != 0.0) ++count;
           }
           for (int a = 0; a < 3; ++a) {
             mid[a] += p * s * (x[a] - r[a]) / d;
@@ -308,6 +312,7 @@ void oracle_element_gradient_bounds(const oracle_geom* g, const float* p0, const
       Gmid[3 * k + a] = mid[a];
       Ghalf[3 * k + a] = half[a];
     }
+    if (namb) namb[k] = count;
   }
 }
 

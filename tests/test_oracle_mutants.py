@@ -124,3 +124,59 @@ def test_tgv_mutant_is_caught(name, monkeypatch):
     fails = [n for n, bad in (("sparse", oc.check_tgv_sparse() > 1e-12), ("fd", oc.check_tgv_fd() > 1e-7),
                                ("constant", oc.check_tgv_constant() > 1e-14)) if bad]
     assert fails, f"TGV mutant {name} passed every pin"
+
+
+# ----------------------------------------------------------------------------- Adam and retraction (Python)
+
+ADAM_MUTANTS = {
+    # (module, old, new)
+    "betas_swapped": ("adam", "m = b1 * np.asarray(m, dtype=np.float64) + (1 - b1) * grad\n",
+                      "m = b2 * np.asarray(m, dtype=np.float64) + (1 - b2) * grad\n"),
+    "second_moment_of_g_not_g2": ("adam", "v = b2 * np.asarray(v, dtype=np.float64) + (1 - b2) * grad * grad\n",
+                                  "v = b2 * np.asarray(v, dtype=np.float64) + (1 - b2) * np.abs(grad)\n"),
+    "no_bias_correction_of_m": ("adam", "mh = m / (1 - b1 ** k)\n    vh = v / (1 - b2 ** k)\n    out",
+                                "mh = m\n    vh = v / (1 - b2 ** k)\n    out"),
+    "bias_correction_fixed_at_step_1": ("adam", "mh = m / (1 - b1 ** k)\n    vh = v / (1 - b2 ** k)\n    out",
+                                        "mh = m / (1 - b1)\n    vh = v / (1 - b2)\n    out"),
+    "pose_betas_swapped": ("adam", "m = b1 * np.asarray(m, dtype=np.float64) + (1 - b1) * grad6",
+                           "m = b2 * np.asarray(m, dtype=np.float64) + (1 - b2) * grad6"),
+    "pose_rates_swapped": ("adam", "lr = np.array([lr_rot] * 3 + [lr_trans] * 3)",
+                           "lr = np.array([lr_trans] * 3 + [lr_rot] * 3)"),
+    "fixed_frame_moments_not_updated": ("adam", "        if fixed is not None and fixed[f]:\n            continue\n",
+                                        "        if fixed is not None and fixed[f]:\n            m[f] = 0.0\n"
+                                        "            continue\n"),
+    "retraction_on_the_right": ("rigid", "out[:, :3] = E @ pose[:, :3]", "out[:, :3] = pose[:, :3] @ E"),
+    "translation_not_rotated": ("rigid", "out[:, 3] = E @ pose[:, 3] + xi[3:]", "out[:, 3] = pose[:, 3] + xi[3:]"),
+}
+
+ADAM_PINS = ["test_adam_first_step_is_signed_lr", "test_adam_pose_first_step_moves_by_signed_lr",
+             "test_adam_constant_gradient_steps_by_lr_every_step", "test_adam_alternating_gradient_closed_form",
+             "test_adam_gradient_then_zero_separates_the_betas",
+             "test_adam_pose_moments_follow_the_same_closed_forms", "test_retraction_closed_forms",
+             "test_adam_pose_fixed_frame_keeps_pose_but_updates_moments"]
+
+
+@pytest.mark.parametrize("name", sorted(ADAM_MUTANTS))
+def test_adam_mutant_is_caught(name, monkeypatch):
+    import importlib
+
+    from tests import test_oracle_pins as pins
+
+    modname, old, new = ADAM_MUTANTS[name]
+    mod = importlib.import_module(f"oracle.{modname}")
+    src = open(mod.__file__).read()
+    assert src.count(old) == 1, f"mutation anchor for {name} not found"
+    mut = type(mod)(mod.__name__)
+    mut.__dict__["__package__"] = "oracle"
+    exec(compile(src.replace(old, new), mod.__file__, "exec"), mut.__dict__)
+    if modname == "rigid":
+        # adam_poses retracts through rigid.apply_twist: give it the mutated one too
+        monkeypatch.setattr(pins.adam, "apply_twist", mut.apply_twist)
+    monkeypatch.setattr(pins, modname, mut)
+    fails = []
+    for t in ADAM_PINS:
+        try:
+            getattr(pins, t)()
+        except AssertionError:
+            fails.append(t)
+    assert fails, f"Adam mutant {name} passed every pin"

@@ -175,6 +175,95 @@ def test_adam_pose_first_step_moves_by_signed_lr():
     assert math.isclose(np.linalg.det(out[1][:, :3]), 1.0, rel_tol=1e-14)
 
 
+# Multi-step Adam pins.  Adam (Kingma and Ba 2015, Algorithm 1) keeps
+# m_k = b1 m_{k-1} + (1 - b1) g_k and v_k = b2 v_{k-1} + (1 - b2) g_k^2 from zero and
+# steps by -lr m_k / (1 - b1^k) / sqrt(v_k / (1 - b2^k)) (eps = 0).  For the gradient
+# sequences below the moments are geometric sums with closed forms:
+#  - constant g:        m_k = (1 - b1^k) g, v_k = (1 - b2^k) g^2, so every step is -lr sign(g);
+#  - alternating g, -g: m_2 = -(1 - b1)^2 g, m_3 = (1 - b1)(1 - b1 + b1^2) g, v_k = (1 - b2^k) g^2,
+#    so step 2 is +lr (1 - b1) / (1 + b1) sign(g) and step 3 -lr (1 - b1 + b1^2) / (1 + b1 + b1^2) sign(g);
+#  - g then 0:          m_2 = b1 (1 - b1) g, v_2 = b2 (1 - b2) g^2, so step 2 is
+#    -lr [b1 / (1 + b1)] / sqrt(b2 / (1 + b2)) sign(g).
+# The last one separates b1 from b2; the first needs the bias corrections at every k
+# and v built from g^2 (|g| != 1).
+ADAM_B1, ADAM_B2 = 0.8, 0.95
+
+
+def _adam_seq(grads, lr=0.1, b1=ADAM_B1, b2=ADAM_B2):
+    """Parameter after each step of the volume Adam on one scalar, from 0."""
+    p, m, v, out = np.zeros(1), np.zeros(1), np.zeros(1), []
+    for k, g in enumerate(grads, start=1):
+        p, m, v = adam.adam_volume(p, np.array([g]), m, v, k, lr=lr, b1=b1, b2=b2, eps=0.0)
+        out.append(float(p[0]))
+    return np.diff(np.concatenate([[0.0], out]))  # the steps
+
+
+def test_adam_constant_gradient_steps_by_lr_every_step():
+    for g in (3.0, -0.25):
+        steps = _adam_seq([g] * 4)
+        assert np.abs(steps - (-0.1 * np.sign(g))).max() < 1e-14
+
+
+def test_adam_alternating_gradient_closed_form():
+    b1 = ADAM_B1
+    steps = _adam_seq([2.0, -2.0, 2.0])
+    assert abs(steps[0] + 0.1) < 1e-15
+    assert abs(steps[1] - 0.1 * (1 - b1) / (1 + b1)) < 1e-14
+    assert abs(steps[2] + 0.1 * (1 - b1 + b1 * b1) / (1 + b1 + b1 * b1)) < 1e-14
+
+
+def test_adam_gradient_then_zero_separates_the_betas():
+    b1, b2 = ADAM_B1, ADAM_B2
+    steps = _adam_seq([-5.0, 0.0])
+    assert abs(steps[1] - 0.1 * (b1 / (1 + b1)) / math.sqrt(b2 / (1 + b2))) < 1e-14
+
+
+def test_adam_pose_moments_follow_the_same_closed_forms():
+    """The twist Adam keeps per-component moments like the volume's; rotation and
+    translation take their own rates."""
+    b1, b2 = ADAM_B1, ADAM_B2
+    poses = np.tile(np.eye(3, 4), (1, 1, 1))
+    m, v = np.zeros((1, 6)), np.zeros((1, 6))
+    seq = [np.array([[2.0, -5.0, 1.5, -2.0, -5.0, 0.7]]), np.array([[-2.0, 0.0, 1.5, 2.0, 0.0, 0.7]])]
+    dxis = []
+    for k, g6 in enumerate(seq, start=1):
+        poses, m, v, dxi = adam.adam_poses(poses, g6, m, v, k, lr_rot=1e-3, lr_trans=1e-2, b1=b1, b2=b2, eps=0.0)
+        dxis.append(dxi[0])
+    lr = np.array([1e-3] * 3 + [1e-2] * 3)
+    alt = (1 - b1) / (1 + b1)
+    zero = (b1 / (1 + b1)) / math.sqrt(b2 / (1 + b2))
+    expect2 = lr * np.array([alt, zero, -1.0, -alt, zero, -1.0])
+    assert np.abs(dxis[0] - (-lr * np.sign(seq[0][0]))).max() < 1e-17
+    assert np.abs(dxis[1] - expect2).max() < 1e-16
+
+
+def test_retraction_closed_forms():
+    """The left retraction of the twist (w, v): about z by theta the rotation is
+    [[c, -s, 0], [s, c, 0], [0, 0, 1]] applied on the left of both R and t; a pure
+    translation adds v to t and leaves R alone."""
+    rng = np.random.default_rng(8)
+    pose = np.zeros((3, 4))
+    pose[:, :3] = rigid.so3_exp(rng.normal(size=3))
+    pose[:, 3] = rng.normal(size=3) * 4
+    th = 0.3
+    Rz = np.array([[math.cos(th), -math.sin(th), 0.0], [math.sin(th), math.cos(th), 0.0], [0.0, 0.0, 1.0]])
+    out = rigid.apply_twist(pose, [0.0, 0.0, th, 0.0, 0.0, 0.0])
+    assert np.abs(out[:, :3] - Rz @ pose[:, :3]).max() < 1e-15
+    assert np.abs(out[:, 3] - Rz @ pose[:, 3]).max() < 1e-14
+    v = np.array([0.1, -0.2, 0.3])
+    out = rigid.apply_twist(pose, np.concatenate([np.zeros(3), v]))
+    assert np.array_equal(out[:, :3], pose[:, :3]) and np.abs(out[:, 3] - (pose[:, 3] + v)).max() < 1e-15
+
+
+def test_adam_pose_fixed_frame_keeps_pose_but_updates_moments():
+    poses = np.tile(np.eye(3, 4), (2, 1, 1))
+    g6 = np.array([[1.0, 2, 3, 4, 5, 6], [1.0, 2, 3, 4, 5, 6]])
+    out, m, v, _ = adam.adam_poses(poses, g6, np.zeros((2, 6)), np.zeros((2, 6)), 1, 1e-3, 1e-2,
+                                   fixed=np.array([True, False]))
+    assert np.array_equal(out[0], poses[0]) and not np.array_equal(out[1], poses[1])
+    assert np.array_equal(m[0], m[1]) and np.array_equal(v[0], v[1]) and np.abs(m[0]).min() > 0
+
+
 def test_kink_band_reduces_to_strict_gradient_and_contains_it():
     """The one-sided-ambiguity band of the element gradient: with eps = 0 it is the
     strict gradient; with eps > 0 it contains the strict value and its width grows
@@ -190,9 +279,16 @@ def test_kink_band_reduces_to_strict_gradient_and_contains_it():
     mid0, half0 = oracle.element_gradient_bounds(geom, p0, g, xw, rows, 0.0)
     assert np.abs(mid0 - strict).max() <= 1e-13 * np.abs(strict).max() and half0.max() == 0.0
     mid1, half1 = oracle.element_gradient_bounds(geom, p0, g, xw, rows, 1e-3)
-    mid2, half2 = oracle.element_gradient_bounds(geom, p0, g, xw, rows, 5e-3)
+    mid2, half2, n2 = oracle.element_gradient_bounds(geom, p0, g, xw, rows, 5e-3, counts=True)
     assert np.all(np.abs(strict - mid1) <= half1 * (1 + 1e-12) + 1e-15)
     assert half2.sum() >= half1.sum() > 0.0
+    # the count of ambiguous boundaries: none at eps = 0; a row without any has a
+    # zero-width band centred on the strict gradient
+    _, _, n0 = oracle.element_gradient_bounds(geom, p0, g, xw, rows, 0.0, counts=True)
+    assert not n0.any() and n2.sum() > 0
+    clean = n2 == 0
+    assert np.all((half2[clean] == 0.0)) and np.all(half2[~clean].sum(axis=1) > 0.0)
+    assert np.abs(mid2[clean] - strict[clean]).max(initial=0.0) <= 1e-13 * np.abs(strict).max()
 
 
 def test_nc_loss_invariances():
