@@ -130,6 +130,16 @@ int pasfm_create(pasfm_ctx** out, int device);
 /* Free the context and its workspace.  NULL is accepted. */
 int pasfm_destroy(pasfm_ctx* ctx);
 
+/* Bound, in SM clock cycles, of the kernels' wait for each copy they stage with
+ * TMA (default 2e9, about 1 s; a negative value restores it).  A wait that runs
+ * out sets PASFM_STATUS_TIMEOUT, the kernel skips its compute, lets its copies in
+ * flight land (waiting for them with the default bound) and exits; pasfm_status()
+ * then returns PASFM_ETIMEOUT and the outputs are unspecified.  0 makes every such
+ * wait report the timeout at once: a deterministic way to exercise that error
+ * path.  Calls that stage nothing with TMA (unaligned or 16-bit arrays) have no
+ * such wait.  Takes effect for later calls on the context. */
+int pasfm_set_wait_limit(pasfm_ctx* ctx, int64_t cycles);
+
 /* Device bytes of workspace the calls need for `geom` (host-only, no CUDA call). */
 int pasfm_workspace_size(const pasfm_geom* geom, size_t* bytes);
 
@@ -293,7 +303,9 @@ int pasfm_smem_probe(int device, double* tbs_out);
  * run -- code hosted inside an application that owns all device memory through
  * its own pool, or a real-time loop that cannot afford the latency and implicit
  * synchronisation of cudaMalloc/cudaFree.  It computes what pasfm_pose_grad
- * computes (same arguments minus the context, same kernels and results) but
+ * computes (same arguments minus the context, same kernels; the same results
+ * within the pose-gradient tolerance, since for the sphere the backward here reads
+ * g itself where pasfm_pose_grad stages its first differences) but
  * keeps all of its scratch in one fixed array of PASFM_NOALLOC_SCRATCH_BYTES
  * that the library declares at file scope in device memory; every GPU that
  * loads the library holds that array until the process exits.  It calls no
@@ -307,8 +319,11 @@ int pasfm_smem_probe(int device, double* tbs_out);
  *  - All calls share the one array, which keeps what the last call left in it;
  *    calls whose work overlaps on the GPU (other streams, other host threads)
  *    race on it.  Serialise them.
- *  - The element-inside-grid check runs but is not reported (there is no
- *    context status word); outputs are then unspecified, accesses stay in bounds. */
+ *  - There is no context status word.  A device-side failure (an element
+ *    within the pulse support of the grid, a staged-copy wait that ran out, a
+ *    clamped sample index) is reported by filling grad6_out, and gelem_out when
+ *    given, with NaN; the return value is still PASFM_OK.  Accesses stay in
+ *    bounds either way. */
 #define PASFM_NOALLOC_SCRATCH_BYTES (64u * 1024u * 1024u)
 int pasfm_pose_grad_noalloc(const pasfm_geom* geom, const void* p0, const double* elem, const double* pose,
                             const void* g, const uint8_t* mask, double* grad6_out, double* gelem_out,

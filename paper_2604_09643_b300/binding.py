@@ -70,6 +70,7 @@ _SIGS = {
     "pasfm_workspace_size": ([_G, ctypes.POINTER(_SZ)], _I),
     "pasfm_reserve": ([_VP, _G], _I),
     "pasfm_set_partial_budget": ([_VP, _SZ], _I),
+    "pasfm_set_wait_limit": ([_VP, ctypes.c_int64], _I),
     "pasfm_element_positions": ([_VP, _G, _VP, _VP, _VP, _VP], _I),
     "pasfm_forward": ([_VP, _G, _VP, _VP, _VP, _VP, _VP], _I),
     "pasfm_adjoint": ([_VP, _G, _VP, _VP, _VP, _VP, _VP], _I),
@@ -304,6 +305,11 @@ class Context:
 
     def set_partial_budget(self, nbytes):
         _check(lib().pasfm_set_partial_budget(self.handle, int(nbytes)))
+
+    def set_wait_limit(self, cycles):
+        """Bound (SM clock cycles) of the kernels' wait for each TMA-staged copy; a
+        negative value restores the default, 0 makes every such wait time out at once."""
+        _check(lib().pasfm_set_wait_limit(self.handle, int(cycles)))
 
     def element_positions(self, geom, elem, pose, out=None, stream=None):
         F, E = geom["n_frames"], geom["n_elem"]

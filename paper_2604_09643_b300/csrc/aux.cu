@@ -86,8 +86,10 @@ __global__ void __launch_bounds__(256) fwd_reduce_kernel(const RedParams P) {
       nmin = min(nmin, __shfl_xor_sync(0xffffffffu, nmin, o));
       nmax = max(nmax, __shfl_xor_sync(0xffffffffu, nmax, o));
     }
+    // 64-bit sums: a cube whose window base was never written (a timed-out forward CTA)
+    // may hold any value, and every access below stays in bounds whatever it is
     const int lo = max(nmin, 0);
-    const int hi = min(nmax + P.W, P.Nt);
+    const int hi = static_cast<int>(min(static_cast<int64_t>(nmax) + P.W, static_cast<int64_t>(P.Nt)));
     const int64_t grow = static_cast<int64_t>(P.f_begin) * P.E + row;
     em.keep = P.mask ? (P.mask[grow] != 0) : true;
     const int64_t base = grow * P.Nt;
@@ -102,9 +104,9 @@ __global__ void __launch_bounds__(256) fwd_reduce_kernel(const RedParams P) {
         float v[kRedUnroll][LANES];
 #pragma unroll
         for (int u = 0; u < kRedUnroll; ++u) {
-          const int ou = cc + u < P.ncubes ? n0[cc + u] - cs : INT_MIN / 2;
+          const int64_t ou = cc + u < P.ncubes ? static_cast<int64_t>(n0[cc + u]) - cs : INT_MIN / 2;
           const bool okc = ou < len && ou + P.W > 0;  // the cube's window meets this chunk
-          o[u] = okc ? ou : INT_MIN / 2;
+          o[u] = okc ? static_cast<int>(ou) : INT_MIN / 2;
           const float* src = part + static_cast<int64_t>(cc + u) * P.W;
 #pragma unroll
           for (int m = 0; m < LANES; ++m) {

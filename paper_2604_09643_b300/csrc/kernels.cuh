@@ -233,7 +233,7 @@ __global__ void __launch_bounds__(256, 2)
 
   // 4. wait for the tile; flag rows that hold any nonzero voxel
   bool ok = true;
-  if (P.use_tma) ok = mbar_wait_bounded(bar, 0, P.status);
+  if (P.use_tma) ok = mbar_wait_limited(bar, 0, P.status, P.wait_cycles);
   if (__syncthreads_or(!ok)) {
     if (tid == 0) mbar_wait_bounded(bar, 0, P.status);  // let the copy land before exit
     return;
@@ -667,7 +667,7 @@ __global__ void __launch_bounds__(C* C, (C == 16 ? 3 : 8))
   unsigned seen = 0;  // largest raw window index at the row ends (see fwd_cube_kernel)
   for (int b = 0; b < nb; ++b) {
     const int buf = b & 1;
-    const bool ok = mbar_wait_bounded(&bar[buf], (b >> 1) & 1, P.status);
+    const bool ok = mbar_wait_limited(&bar[buf], (b >> 1) & 1, P.status, P.wait_cycles);
     const int cnt = min(kBatch, nl - b * kBatch);
     const float* wb = win + buf * kBatch * WP;
     for (int e = 0; ok && e < cnt; ++e) {

@@ -76,6 +76,19 @@ PFN_cuTensorMapEncodeTiled_v12000 encoder() {
   return fn;
 }
 
+// This entry point has no context status word to report through, so a device-side
+// failure recorded in the scratch status word (a staged-copy wait that ran out, which
+// leaves per-cube partials unwritten; an element inside the pulse support of the grid;
+// a clamped sample index) turns the outputs into NaN, which the caller can test.
+__global__ void noalloc_report_kernel(const unsigned* __restrict__ status, double* __restrict__ grad6, int64_t n6,
+                                      double* __restrict__ gelem, int64_t nelem) {
+  if (*status == 0u) return;
+  const double nan = __longlong_as_double(0x7ff8000000000000LL);
+  for (int64_t i = threadIdx.x; i < n6; i += blockDim.x) grad6[i] = nan;
+  if (gelem)
+    for (int64_t i = threadIdx.x; i < nelem; i += blockDim.x) gelem[i] = nan;
+}
+
 int launch_ok(const char* what) {
   const cudaError_t e = cudaPeekAtLastError();
   if (e == cudaSuccess) return PASFM_OK;
@@ -129,7 +142,8 @@ extern "C" int pasfm_pose_grad_noalloc(const pasfm_geom* geom, const void* p0, c
   double* gpart = reinterpret_cast<double*>(sb + kStatusBytes + xw_bytes);
   double* Gm = gelem_out ? gelem_out : reinterpret_cast<double*>(sb + kStatusBytes + xw_bytes + gpart_bytes);
 
-  // only the status word must start at zero; every other scratch byte used is written before it is read
+  // only the status word must start at zero; every other scratch byte used is written before it is
+  // read, unless a kernel records a failure there, in which case the outputs become NaN (below)
   if (cudaMemsetAsync(status, 0, sizeof(unsigned), st) != cudaSuccess) {
     cudaGetLastError();
     return report_error(PASFM_ECUDA, "pasfm_pose_grad_noalloc: cudaMemsetAsync failed");
@@ -188,6 +202,7 @@ extern "C" int pasfm_pose_grad_noalloc(const pasfm_geom* geom, const void* p0, c
   P.dz = geom->dz;
   set_bwd_profile(pl, &P);
   P.use_tma = use_tma;
+  P.wait_cycles = kWaitCycles;
   P.status = status;
   const size_t smem = pl.C == 16 ? BwdLayout<16>::total(pl.WP) : BwdLayout<8>::total(pl.WP);
   const cudaError_t e = bwd_launcher(pl.K, pl.S)(pl.C, 2, map, P, dim3(pl.ncubes), smem, st);
@@ -200,5 +215,8 @@ extern "C" int pasfm_pose_grad_noalloc(const pasfm_geom* geom, const void* p0, c
   rc = launch_ok("pasfm_pose_grad_noalloc: pose_rows launch failed");
   if (rc != PASFM_OK) return rc;
   grad6_kernel<<<F, 256, 0, st>>>(xw, Gm, E, grad6_out);
-  return launch_ok("pasfm_pose_grad_noalloc: grad6 launch failed");
+  rc = launch_ok("pasfm_pose_grad_noalloc: grad6 launch failed");
+  if (rc != PASFM_OK) return rc;
+  noalloc_report_kernel<<<1, 256, 0, st>>>(status, grad6_out, int64_t(F) * 6, gelem_out, rows * 3);
+  return launch_ok("pasfm_pose_grad_noalloc: status report launch failed");
 }

@@ -174,6 +174,7 @@ struct pasfm_ctx {
   Buf xw, part, n0, gres, vgrad, gpart, G, grad6, lpart, lscalar, taps, vparts, gw, tpart, gdiff;
   int sms = 0;  // streaming multiprocessors of the device
   size_t budget = kDefaultPartialBudget;
+  long long wait_cycles = kWaitCycles;  // bound of the kernels' first wait for each staged copy
   bool timing = false;
   std::vector<Rec> recs;
   std::vector<cudaEvent_t> pool;
@@ -382,6 +383,7 @@ int run_forward(pasfm_ctx* ctx, const Geo& G, const Plan& pl, const void* p0, co
   set_profile(pl, P);
   P.p0_scale = static_cast<float>(pulse_scale(pl));
   P.use_tma = use_tma;
+  P.wait_cycles = ctx->wait_cycles;
   P.status = ctx->status;
 
   const int threads = 32 * pl.fwd_warps;
@@ -502,6 +504,7 @@ int run_backward(pasfm_ctx* ctx, const Geo& G, const Plan& pl, int mode, const v
   set_bwd_profile(pl, &P);
   P.use_tma = use_tma;
   P.diff = diff ? 1 : 0;
+  P.wait_cycles = ctx->wait_cycles;
   P.status = ctx->status;
   const size_t smem = pl.C == 16 ? BwdLayout<16>::total(pl.WP) : BwdLayout<8>::total(pl.WP);
   const int per_sm = bwd_occupancy(pl.K, pl.S)(pl.C, mode, smem);
@@ -595,6 +598,7 @@ int run_tgv(pasfm_ctx* ctx, const Geo& G, const void* p0, const float* w, double
   P.alpha0 = static_cast<float>(alpha0);
   P.eps2 = static_cast<float>(eps * eps);
   P.use_tma = use_tma;
+  P.wait_cycles = ctx->wait_cycles;
   P.status = ctx->status;
   cudaEvent_t t = ctx->begin(st);
   tgv_kernel<<<grid, tgv_threads(), smem, st>>>(umap, wmap, gmap, P);
@@ -629,7 +633,7 @@ int prepare(pasfm_ctx* ctx, const pasfm_geom* geom, Geo* G, Plan* pl) {
 
 extern "C" {
 
-int pasfm_abi_version(void) { return 2; }
+int pasfm_abi_version(void) { return 3; }
 
 const char* pasfm_last_error(void) { return g_err.c_str(); }
 
@@ -677,6 +681,12 @@ int pasfm_destroy(pasfm_ctx* ctx) {
 int pasfm_set_partial_budget(pasfm_ctx* ctx, size_t bytes) {
   if (!ctx) return fail(PASFM_EINVAL, "ctx is NULL");
   ctx->budget = bytes ? bytes : kDefaultPartialBudget;
+  return PASFM_OK;
+}
+
+int pasfm_set_wait_limit(pasfm_ctx* ctx, int64_t cycles) {
+  if (!ctx) return fail(PASFM_EINVAL, "ctx is NULL");
+  ctx->wait_cycles = cycles < 0 ? kWaitCycles : static_cast<long long>(cycles);
   return PASFM_OK;
 }
 

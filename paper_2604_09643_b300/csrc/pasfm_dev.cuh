@@ -69,6 +69,7 @@ struct FwdParams {
   float h, supf, sup2, nb_shift, p0_scale, inv_hf, cb1;
   GaussConst gs;
   int use_tma;
+  long long wait_cycles;  // bound of the first wait for each staged copy (SM clock cycles)
   unsigned* status;
 };
 
@@ -83,6 +84,7 @@ struct TgvParams {
   int nx, ny, nz;
   float inv_dx, inv_dy, inv_dz, alpha1, alpha0, eps2;
   int use_tma;
+  long long wait_cycles;  // bound of the first wait for each staged copy (SM clock cycles)
   unsigned* status;
 };
 
@@ -120,6 +122,7 @@ struct BwdParams {
   GaussConst gs;
   int use_tma;
   int diff;             // sphere: the staged trace is the difference g_n - g_(n-1)
+  long long wait_cycles;  // bound of the first wait for each staged copy (SM clock cycles)
   unsigned* status;
 };
 
@@ -160,18 +163,32 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Wait for phase `parity` of `bar` for at most kWaitCycles; on expiry set the
-// TIMEOUT status bit and return false (callers then skip the compute and exit).
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, unsigned* status) {
+// Wait for phase `parity` of `bar` for at most `limit` SM clock cycles; on expiry set
+// the TIMEOUT status bit and return false (callers then skip the compute, let their
+// copies in flight land with mbar_wait_bounded and exit).  A limit <= 0 reports the
+// expiry at once without looking at the barrier: the host's wait-limit setting uses it
+// to exercise that error path deterministically.
+__device__ __forceinline__ bool mbar_wait_limited(uint64_t* bar, uint32_t parity, unsigned* status,
+                                                  long long limit) {
+  if (limit <= 0) {
+    atomicOr(status, PASFM_STATUS_TIMEOUT);
+    return false;
+  }
   if (mbar_try_wait(bar, parity)) return true;
   const long long t0 = clock64();
   while (true) {
     if (mbar_try_wait(bar, parity)) return true;
-    if (clock64() - t0 > kWaitCycles) {
+    if (clock64() - t0 > limit) {
       atomicOr(status, PASFM_STATUS_TIMEOUT);
       return false;
     }
   }
+}
+
+// The same with the full bound kWaitCycles (~1 s): the drain of copies in flight
+// before a CTA exits.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, unsigned* status) {
+  return mbar_wait_limited(bar, parity, status, kWaitCycles);
 }
 
 // 2-D tiled TMA load (coordinates in elements, x innermost) completing on `bar`.

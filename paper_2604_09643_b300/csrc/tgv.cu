@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(TN, 4)
     // one thread polls the barrier; the others sleep in the block barrier below rather than
     // spend issue slots that the co-resident tiles' arithmetic needs (the barrier orders the
     // copies' completion, observed by thread 0, before every thread's reads)
-    if (tid == 0) ok = mbar_wait_bounded(&S.bar, 0, P.status);
+    if (tid == 0) ok = mbar_wait_limited(&S.bar, 0, P.status, P.wait_cycles);
   } else {
     for (int k = tid; k < RN; k += blockDim.x) {
       const int rx = k % RX, ry = (k / RX) % RY, rz = k / (RX * RY);

@@ -119,6 +119,20 @@ def _nc_rows(ctx, geom, p0, points, meas_rows, sigma, repeat):
     return nc.reshape(-1), G[0]
 
 
+def select_top(cands, scores, keep, distinct=False):
+    """The `keep` candidate positions (cands [K][3]) of lowest score, best first (ties in
+    candidate order).  With `distinct`, a position that repeats a better one (to 1e-6 mm;
+    overlapping search neighbourhoods) is skipped, and when fewer than `keep` distinct
+    positions remain the list is padded with its last entry."""
+    order = np.argsort(scores, kind="stable")
+    pts = np.asarray(cands, dtype=np.float64)[order]
+    if not distinct:
+        return pts[:keep]
+    _, first = np.unique(np.round(pts, 6), axis=0, return_index=True)
+    pick = np.sort(first)[:keep]
+    return np.concatenate([pts[pick], np.repeat(pts[pick[-1:]], keep - len(pick), axis=0)])
+
+
 def stage2_localise(ctx, geom, p0, elem, pose_b0, meas_b, cfg):
     """Independent positions of the elements of view B (Stage 2).  Returns
     (positions [E][3], final NC [E])."""
@@ -146,16 +160,8 @@ def stage2_localise(ctx, geom, p0, elem, pose_b0, meas_b, cfg):
                 sim = ctx.lowpass(sim, s0)
             _, nc = ctx.nc_grad(sim, meas_s0[j0:j0 + len(js)], meas_repeat=K)
             nc = nc.reshape(len(js), K).cpu().numpy()
-            order = np.argsort(nc, axis=1, kind="stable")
-            if not distinct:
-                out[js] = cands[js][np.arange(len(js))[:, None], order[:, :keep]]
-                continue
             for r, j in enumerate(js):
-                pts_j = cands[j][order[r]]
-                _, first = np.unique(np.round(pts_j, 6), axis=0, return_index=True)
-                pick = np.sort(first)[:keep]
-                out[j, :len(pick)] = pts_j[pick]
-                out[j, len(pick):] = pts_j[pick[-1]]
+                out[j] = select_top(cands[j], nc[r], keep, distinct)
         return out
 
     # coarse search: Top-K candidates per element under the widest smoothing; with

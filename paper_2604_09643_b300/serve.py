@@ -4,8 +4,9 @@ Freehand scans arrive as requests, each asking for a number of gradient steps of
 the joint volume + pose reconstruction.  The server:
 
 * admits a waiting request when its device footprint fits the free HBM (minus a
-  reserve), refuses with a status one that could never fit, and otherwise keeps
-  it queued until running scans finish and release memory;
+  reserve), refuses with a status one that could never fit or that does not fit
+  while no scan is running, and otherwise keeps it queued until running scans
+  finish and release memory (their cached blocks are returned to the driver);
 * keeps every admitted scan resident: its volume, poses, measurements, Adam
   state and a private library context (workspace) on its own CUDA stream;
 * each iteration keeps up to ``inflight`` steps enqueued per scan, so kernels
@@ -205,6 +206,13 @@ class Server:
                                            None, None, float("nan"), self._now() - req.arrival_s, []))
                 continue
             if dec == WAIT:
+                if not self.active:
+                    # nothing running will free memory for it: waiting could last forever
+                    self.queue.popleft()
+                    self.results.append(Result(req.id, f"rejected: needs {need} bytes, {free} free with no scan "
+                                                       f"running", 0, None, None, float("nan"),
+                                               self._now() - req.arrival_s, []))
+                    continue
                 return
             self.queue.popleft()
             self.active.append((_Scan(req, self.device, self._now()), self._now() - req.arrival_s))
@@ -225,6 +233,10 @@ class Server:
                     self.results.append(scan.finish(self._now(), wait))
                 else:
                     keep.append((scan, wait))
+            if len(keep) < len(self.active):
+                # hand the retired scans' blocks back to the driver, whose free-memory
+                # figure the admission reads (the caching allocator would keep them)
+                torch.cuda.empty_cache()
             self.active = keep
             if not self.active and self.queue:
                 delay = self.queue[0].arrival_s - self._now()

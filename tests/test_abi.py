@@ -42,7 +42,7 @@ def test_binding_covers_every_declared_symbol():
 
 
 def test_abi_version():
-    assert binding.lib().pasfm_abi_version() == 2
+    assert binding.lib().pasfm_abi_version() == 3
 
 
 def _geom(**kw):
@@ -92,3 +92,7 @@ def test_create_without_device_fails_cleanly():
 def test_binding_refuses_host_tensors():
     with pytest.raises(ValueError):
         binding._ptr(torch.zeros(4), torch.float32, "x")
+
+
+def test_wait_limit_needs_a_context():
+    assert binding.lib().pasfm_set_wait_limit(None, 0) == -1

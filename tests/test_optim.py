@@ -111,3 +111,22 @@ def test_search_grids():
     # a radius already at the step: one 5-point grid at step_mm
     one = optim.search_grids(0.1, 0.1, True)
     assert len(one) == 1 and abs(one[0][1] - one[0][0] - 0.1) < 1e-12
+
+
+def test_stage2_top_k_selection_deduplicates_and_pads():
+    """Stage 2's coarse-to-fine search evaluates overlapping 3x3x3 neighbourhoods, so a
+    position can appear several times; the Top-K keeps each once, best score first, and
+    pads with the last distinct one when too few remain."""
+    from paper_2604_09643_b300.pipeline import select_top
+    a, b, c = np.array([0.0, 0, 0]), np.array([0.25, 0, 0]), np.array([0, 0.25, 0])
+    cands = np.stack([b, a, c, a + 1e-9, b, c])
+    scores = np.array([-0.5, -0.9, -0.1, -0.8, -0.5, -0.2])
+    top = select_top(cands, scores, 4, distinct=True)
+    assert np.allclose(top, [a, b, c, c])                        # a (twice), b (twice), c (twice): 3 distinct
+    assert np.allclose(select_top(cands, scores, 2, distinct=True), [a, b])
+    # without de-duplication the repeats stay, in score order
+    assert np.allclose(select_top(cands, scores, 4), [a, a + 1e-9, b, b])
+    # where the grids coincide (no repeats) both options give the same list
+    uniq = np.stack([a, b, c])
+    s3 = np.array([0.3, -0.1, 0.2])
+    assert np.array_equal(select_top(uniq, s3, 3, distinct=True), select_top(uniq, s3, 3))

@@ -60,3 +60,19 @@ def test_failing_scan_is_isolated(cuda_device):
     res = {r.id: r for r in srv.run()}
     assert res[9].status.startswith("failed")
     assert res[0].status == "ok" and res[1].status == "ok"
+
+
+def test_released_memory_admits_a_waiting_scan(cuda_device):
+    """With the device's real free memory: the reserve leaves room for one of two equal
+    scans, so the second waits until the first finishes, releases its workspace and
+    tensors (returned to the driver), and is then admitted."""
+    a, b = _request(20, 64, 8, 16, 1024, 0.0, steps=3), _request(21, 64, 8, 16, 1024, 0.0, steps=3)
+    torch.cuda.empty_cache()
+    free, _ = torch.cuda.mem_get_info()
+    fp = serve.footprint_bytes(a.geom)
+    srv = serve.Server(device=0, reserve_bytes=int(free - 1.2 * fp))
+    srv.submit(a)
+    srv.submit(b)
+    res = {r.id: r for r in srv.run(max_seconds=120)}
+    assert res[20].status == "ok" and res[21].status == "ok", [r.status for r in res.values()]
+    assert res[21].admitted_s >= res[20].finished_s
