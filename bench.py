@@ -512,10 +512,10 @@ def run_serving(args):
         warm = serve.request_from_spec(dict(specs[0], id=-1, arrival_s=0.0, n=64, n_frames=8, m=8),
                                        ctx, steps=max(args.warmup, 3))
     torch.cuda.synchronize()
-    srv = serve.Server(device=0)
+    srv = serve.Server(device=0, mode=args.serve_mode)
     srv.submit(warm)
     srv.run()
-    srv = serve.Server(device=0)
+    srv = serve.Server(device=0, mode=args.serve_mode)
     for r in reqs:
         srv.submit(r)
     with ClockSampler(0) as clk:
@@ -530,9 +530,10 @@ def run_serving(args):
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
            "data": "synthetic",
            "config": {"workload": WORKLOAD_SERVING, "requests": len(specs), "steps_per_request": args.serve_steps,
+                      "scheduling": args.serve_mode,
                       "arrivals": "seeded Poisson stream, mean 4 scans/s, first requests in arrival order",
                       "l2": "inputs larger than L2 (each scan's measurements 64 MiB-2.4 GiB)"},
-           "offered_steps_per_s": offered, "arrival_span_s": span,
+           "offered_steps_per_s": offered, "arrival_span_s": span, "iterations": rep["iterations"],
            "step_ms_p50": rep["step_ms_p50"], "step_ms_p99": rep["step_ms_p99"],
            "queue_wait_s_p50": rep["queue_wait_s_p50"], "queue_wait_s_p99": rep["queue_wait_s_p99"],
            "completed": rep["completed"], "rejected": rep["rejected"], "failed": rep["failed"],
@@ -729,6 +730,9 @@ def main():
     ap.add_argument("--sigma", type=float, default=0.05, help="Gaussian width (mm) for --kernel gauss")
     ap.add_argument("--serve-requests", type=int, default=12, help="serving: requests taken from the stream")
     ap.add_argument("--serve-steps", type=int, default=4, help="serving: gradient steps per request")
+    ap.add_argument("--serve-mode", choices=["batched", "streams"], default="batched",
+                    help="serving: one batched step over the resident scans per iteration, or each scan's own "
+                         "steps on its own stream")
     ap.add_argument("--storage", choices=["f32", "bf16", "f16"], default="f32",
                     help="storage type of the volume and the measurements (arithmetic stays FP32)")
     args = ap.parse_args()

@@ -192,6 +192,29 @@ int pasfm_step(pasfm_ctx* ctx, const pasfm_geom* geom, void* p0, double* pose, c
                const void* meas, const uint8_t* mask, pasfm_adam* state, double* loss_out,
                void* stream);
 
+/* A10 -- one gradient step (pasfm_step's semantics and results) for each of n
+ * resident scans, issued on one stream as batched launches: the scans whose hot
+ * kernels share an instantiation and pulse profile (pulse, slot count, cube and
+ * window size, sampling, wait bound; at most 16 per launch) have their forward, its
+ * reduction and their fused adjoint / pose gradient each run as ONE persistent launch
+ * per frame-chunk round, whose CTAs take (scan, cube, frame, element group) and
+ * (scan, cube, part) tiles from a shared list until it is exhausted.  Each scan's
+ * tiles are exactly those of its own pasfm_step, so its results are bit-identical
+ * alone, in any mix and to pasfm_step.  The small per-scan kernels (element
+ * positions, loss sum, part sums, element-gradient sums, Adam) are launched per scan.
+ *   ctxs[i]: a distinct context per scan (its workspace), all on one device;
+ *   geoms[i], p0[i], pose[i], elem[i], meas[i], mask[i] (mask may be NULL, or mask[i]
+ *   NULL), states[i], loss_out[i] (loss_out may be NULL, or loss_out[i] NULL): as for
+ *   pasfm_step, per scan.  Host arrays of n entries; each scan's arrays are device
+ *   memory as for pasfm_step.
+ *   trace_ns: device uint64 [n][2] or NULL; receives per scan the globaltimer
+ *   (ns) at its first batched tile's start and its last batched tile's end over the
+ *   forward and backward launches (how the scans' work overlapped on the device).
+ * n = 0 is a no-op.  Each context's status word receives its own scan's errors. */
+int pasfm_step_batch(int n, pasfm_ctx* const* ctxs, const pasfm_geom* geoms, void* const* p0, double* const* pose,
+                     const double* const* elem, const void* const* meas, const uint8_t* const* mask,
+                     pasfm_adam* states, double* const* loss_out, uint64_t* trace_ns, void* stream);
+
 /* F3 -- smoothed second-order total generalized variation of the volume, the
  * regulariser of Stages 1 and 5 (Eq. 2, lambda L_TGV; lambda folded into the
  * weights):

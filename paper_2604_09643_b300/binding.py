@@ -79,6 +79,7 @@ _SIGS = {
     "pasfm_step": ([_VP, _G, _VP, _VP, _VP, _VP, _VP, ctypes.POINTER(PasfmAdam), _VP, _VP], _I),
     "pasfm_tgv_grad": ([_VP, _G, _VP, _VP, ctypes.c_double, ctypes.c_double, ctypes.c_double, _VP, _I, _VP, _VP,
                         _VP], _I),
+    "pasfm_step_batch": ([_I, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP], _I),
     "pasfm_step_tgv": ([_VP, _G, _VP, _VP, _VP, _VP, _VP, ctypes.POINTER(PasfmAdam), ctypes.POINTER(PasfmTgv),
                         _VP, _VP, _VP], _I),
     "pasfm_apply_twists": ([_VP, _I, _VP, _VP, _VP, _VP], _I),
@@ -443,6 +444,36 @@ class Context:
 
     def launch_count(self):
         return int(lib().pasfm_launch_count(self.handle))
+
+
+def step_batch(ctxs, geoms, p0s, poses, elems, meas, adams, masks=None, loss_outs=None, trace=None, stream=None):
+    """pasfm_step_batch: one gradient step for each scan i (its own Context, geometry,
+    volume, poses, template, measurements, AdamState, optional mask and loss output),
+    the hot kernels of scans sharing an instantiation batched into one launch per phase.
+    trace: optional int64 device tensor [n][2] of per-scan first-start / last-end times (ns)."""
+    n = len(ctxs)
+    if not all(len(x) == n for x in (geoms, p0s, poses, elems, meas, adams)):
+        raise ValueError("every per-scan list needs one entry per scan")
+    if n == 0:
+        return
+    device = ctxs[0].device
+    G = (PasfmGeom * n)(*[make_geom(g, dtype_vol=p.dtype, dtype_sig=m.dtype) for g, p, m in zip(geoms, p0s, meas)])
+    handles = (_VP * n)(*[c.handle for c in ctxs])
+    states = (PasfmAdam * n)(*[a.c for a in adams])
+    arr = lambda xs, dt, what, none=False: (_VP * n)(*[_ptr(x, dt, what, allow_none=none) for x in xs])
+    mk = arr(masks, torch.uint8, "mask", True) if masks is not None else None
+    lo = arr(loss_outs, torch.float64, "loss_out", True) if loss_outs is not None else None
+    tr = None
+    if trace is not None:
+        if trace.dtype != torch.int64 or tuple(trace.shape) != (n, 2) or not trace.is_cuda:
+            raise ValueError("trace must be an int64 CUDA tensor of shape (n, 2)")
+        tr = ctypes.c_void_p(trace.data_ptr())
+    rc = lib().pasfm_step_batch(n, handles, G, arr(p0s, _VOL, "p0"), arr(poses, torch.float64, "pose"),
+                                arr(elems, torch.float64, "elem"), arr(meas, _VOL, "meas"), mk, states, lo, tr,
+                                _stream(stream, device))
+    for a, st in zip(adams, states):   # the library advanced each state's step count
+        a.c.step = st.step
+    _check(rc)
 
 
 class TgvState:

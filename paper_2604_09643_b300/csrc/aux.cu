@@ -66,10 +66,10 @@ __device__ __forceinline__ void block_loss(double lsum, double* out, int warp, i
 // ceil(W / 32) words per lane and cube, so that only the window's own words are
 // loaded and kRedUnroll cubes' loads are in flight at once.
 template <int LANES>
-__global__ void __launch_bounds__(256) fwd_reduce_kernel(const RedParams P) {
+__device__ __forceinline__ void fwd_reduce_block(const RedParams& P, int block) {
   extern __shared__ float racc[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int row = blockIdx.x * 8 + warp;
+  const int row = block * 8 + warp;
   float* acc = racc + warp * kRedChunk;
   Emitter em{P.sig_out, P.g_out, P.meas, P.dtype_sig, true, 0.0};
   if (row < P.n_rows) {
@@ -129,7 +129,22 @@ __global__ void __launch_bounds__(256) fwd_reduce_kernel(const RedParams P) {
       __syncwarp();
     }
   }
-  if (P.loss_part) block_loss(em.lsum, P.loss_part + P.loss_offset + blockIdx.x, warp, lane);
+  if (P.loss_part) block_loss(em.lsum, P.loss_part + P.loss_offset + block, warp, lane);
+}
+
+template <int LANES>
+__global__ void __launch_bounds__(256) fwd_reduce_kernel(const RedParams P) {
+  fwd_reduce_block<LANES>(P, blockIdx.x);
+}
+
+// The reductions of several scans' chunks (same window length) in one launch: scan s
+// owns blocks [blocks[s], blocks[s + 1]), each summing 8 of its traces as above.
+template <int LANES>
+__global__ void __launch_bounds__(256) fwd_reduce_batch_kernel(const __grid_constant__ RedBatch B) {
+  const int b = blockIdx.x;
+  int s = 0;
+  while (b >= B.blocks[s + 1]) ++s;
+  fwd_reduce_block<LANES>(B.R[s], b - B.blocks[s]);
 }
 
 size_t fwd_reduce_smem() { return size_t(8) * kRedChunk * 4; }
@@ -146,6 +161,31 @@ cudaError_t reduce_launch_l(const RedParams& P, int blocks, cudaStream_t st) {
 }
 }  // namespace
 
+template <int LANES>
+cudaError_t reduce_batch_launch_l(const RedBatch& B, cudaStream_t st) {
+  const size_t smem = fwd_reduce_smem();
+  cudaError_t e = cudaFuncSetAttribute(fwd_reduce_batch_kernel<LANES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(smem));
+  if (e != cudaSuccess) return e;
+  fwd_reduce_batch_kernel<LANES><<<B.blocks[B.n], 256, smem, st>>>(B);
+  return cudaGetLastError();
+}
+
+cudaError_t fwd_reduce_batch_launch(const RedBatch& B, int W, cudaStream_t st) {
+  if (B.n <= 0 || B.blocks[B.n] == 0) return cudaSuccess;
+  switch ((W + 31) / 32) {
+    case 1: return reduce_batch_launch_l<1>(B, st);
+    case 2: return reduce_batch_launch_l<2>(B, st);
+    case 3: return reduce_batch_launch_l<3>(B, st);
+    case 4: return reduce_batch_launch_l<4>(B, st);
+    case 5: return reduce_batch_launch_l<5>(B, st);
+    case 6: return reduce_batch_launch_l<6>(B, st);
+    case 7: return reduce_batch_launch_l<7>(B, st);
+    case 8: return reduce_batch_launch_l<8>(B, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 cudaError_t fwd_reduce_launch(const RedParams& P, int blocks, cudaStream_t st) {
   switch ((P.W + 31) / 32) {
     case 1: return reduce_launch_l<1>(P, blocks, st);
@@ -157,6 +197,15 @@ cudaError_t fwd_reduce_launch(const RedParams& P, int blocks, cudaStream_t st) {
     case 7: return reduce_launch_l<7>(P, blocks, st);
     case 8: return reduce_launch_l<8>(P, blocks, st);
     default: return cudaErrorInvalidValue;
+  }
+}
+
+// trace[s] = (max, 0) for the batched launches' per-scan tile intervals.
+__global__ void trace_init_kernel(unsigned long long* trace, int n) {
+  const int i = threadIdx.x;
+  if (i < n) {
+    trace[2 * i] = ~0ull;
+    trace[2 * i + 1] = 0ull;
   }
 }
 

@@ -17,6 +17,9 @@ __global__ void elem_pos_kernel(const double* elem, const double* pose, double* 
 // fwd_reduce_kernel<LANES> for LANES = ceil(W / 32), launched with 8 warps and
 // 8 * kRedChunk floats of dynamic shared memory
 cudaError_t fwd_reduce_launch(const RedParams& P, int blocks, cudaStream_t st);
+// the same over several scans' chunks in one launch (window length W shared)
+cudaError_t fwd_reduce_batch_launch(const RedBatch& B, int W, cudaStream_t st);
+__global__ void trace_init_kernel(unsigned long long* trace, int n);
 size_t fwd_reduce_smem();
 __global__ void loss_rows_kernel(const float* sig, const void* meas, int dtype, const uint8_t* mask, float* g,
                                  double* loss_part, int n_rows, int Nt);
@@ -57,6 +60,13 @@ using FwdLaunch = cudaError_t (*)(int C, const CUtensorMap& map, const FwdParams
                                   size_t smem, cudaStream_t st);
 using BwdLaunch = cudaError_t (*)(int C, int mode, const CUtensorMap& map, const BwdParams& P, dim3 grid,
                                   size_t smem, cudaStream_t st);
+// persistent batched launches over several scans (grid = CTAs to keep resident)
+using FwdBatchLaunch = cudaError_t (*)(int C, const TmaBatch& maps, const FwdBatch& B, int ctas, int threads,
+                                       size_t smem, cudaStream_t st);
+using BwdBatchLaunch = cudaError_t (*)(int C, int mode, const TmaBatch& maps, const BwdBatch& B, int ctas,
+                                       size_t smem, cudaStream_t st);
+// resident CTAs per SM of the batched kernels (0 if the query fails)
+using FwdBatchOccupancy = int (*)(int C, int threads, size_t smem);
 
 // Launchers of the hot kernels for pulse profile K and slot count S; null when
 // (K, S) is not compiled (sphere: S = 2..16, Gaussian: S = 2..32).
@@ -75,6 +85,10 @@ using BwdOccupancy = int (*)(int C, int mode, size_t smem);
 FwdLaunch fwd_launcher(int K, int S);
 BwdLaunch bwd_launcher(int K, int S);
 BwdOccupancy bwd_occupancy(int K, int S);
+FwdBatchLaunch fwd_batch_launcher(int K, int S);
+BwdBatchLaunch bwd_batch_launcher(int K, int S);
+FwdBatchOccupancy fwd_batch_occupancy(int K, int S);
+BwdOccupancy bwd_batch_occupancy(int K, int S);
 
 // Adds the n_parts per-part adjoint sums in part order into vol (or overwrites it).
 __global__ void sum_parts_kernel(const float* parts, int n_parts, int64_t nvox, float* vol, int accumulate);

@@ -169,58 +169,72 @@ __host__ __device__ constexpr int fwd_win_offset() {
   return ((fwd_tile_bytes<C>() + C * C + 16 + 127) / 128) * 128;
 }
 
+// Shared-memory layout of a forward CTA: the p0 tile, row flags, the staging barrier and
+// the per-warp windows.
+template <int C>
+struct FwdSmem {
+  float* tile;
+  uint8_t* rowflag;
+  uint64_t* bar;
+  float* win;
+  __device__ explicit FwdSmem(unsigned char* smem)
+      : tile(reinterpret_cast<float*>(smem)),
+        rowflag(smem + fwd_tile_bytes<C>()),
+        bar(reinterpret_cast<uint64_t*>(smem + ((fwd_tile_bytes<C>() + C * C + 7) / 8) * 8)),
+        win(reinterpret_cast<float*>(smem + fwd_win_offset<C>())) {}
+};
+
+// One forward tile: cube c (of ncubes) of frame fl of the launch's frame chunk against
+// element group eg.  Q holds what every scan of a launch shares (pulse profile, sample
+// slots, window length, wait bound); G the scan's own fields (grid, frames, arrays,
+// status).  A single-scan launch passes its one parameter block for both.  The caller
+// has initialised the staging barrier; `parity` is the phase this tile's copy completes.
+// Returns false when that copy's wait ran out: the copy has landed and the CTA must exit.
 template <int C, int S, int K>
-__global__ void __launch_bounds__(256, 2)
-    fwd_cube_kernel(const __grid_constant__ CUtensorMap p0map, const FwdParams P) {
-  extern __shared__ __align__(128) unsigned char smem[];
-  float* tile = reinterpret_cast<float*>(smem);
-  uint8_t* rowflag = smem + fwd_tile_bytes<C>();
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + ((fwd_tile_bytes<C>() + C * C + 7) / 8) * 8);
-  float* win = reinterpret_cast<float*>(smem + fwd_win_offset<C>());
+__device__ __forceinline__ bool fwd_tile(const CUtensorMap* p0map, const FwdParams& Q, const FwdParams& G,
+                                         const FwdSmem<C>& sm, int c, int ncubes, int fl, int eg, uint32_t parity) {
+  float* tile = sm.tile;
+  uint8_t* rowflag = sm.rowflag;
+  uint64_t* bar = sm.bar;
+  float* win = sm.win;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int nwarps = blockDim.x >> 5;
-  const int c = blockIdx.x;
-  const int ncubes = gridDim.x;
-  const int cx = c % P.ncx, cy = (c / P.ncx) % P.ncy, cz = c / (P.ncx * P.ncy);
-  const int fl = blockIdx.y, f = P.f_begin + fl;
-  const int j = (blockIdx.z * nwarps + warp) * kWarp + lane;
-  const bool valid = j < P.E;
-  const int jj = valid ? j : P.E - 1;
+  const int cx = c % G.ncx, cy = (c / G.ncx) % G.ncy, cz = c / (G.ncx * G.ncy);
+  const int f = G.f_begin + fl;
+  const int j = (eg * nwarps + warp) * kWarp + lane;
+  const bool valid = j < G.E;
+  const int jj = valid ? j : G.E - 1;
 
   // 1. stage the p0 cube (zero outside the grid)
-  if (P.use_tma) {
+  if (G.use_tma) {
     if (tid == 0) {
-      mbar_init(bar, 1);
-      fence_mbar_init();
-    }
-    __syncthreads();
-    if (tid == 0) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // earlier tiles' reads of `tile`
       mbar_arrive_expect_tx(bar, fwd_tile_bytes<C>());
-      tma_load_3d(tile, &p0map, bar, cx * C, cy * C, cz * C);
+      tma_load_3d(tile, p0map, bar, cx * C, cy * C, cz * C);
     }
   } else {
     for (int k = tid; k < C * C * C; k += blockDim.x) {
       const int lx = k % C, ly = (k / C) % C, lz = k / (C * C);
       const int ix = cx * C + lx, iy = cy * C + ly, iz = cz * C + lz;
       float v = 0.f;
-      if (ix < P.nx && iy < P.ny && iz < P.nz)
-        v = load_elem(P.p0, (static_cast<int64_t>(iz) * P.ny + iy) * P.nx + ix, P.dtype_vol);
+      if (ix < G.nx && iy < G.ny && iz < G.nz)
+        v = load_elem(G.p0, (static_cast<int64_t>(iz) * G.ny + iy) * G.nx + ix, G.dtype_vol);
       tile[k] = v;
     }
   }
 
   // 2. zero this lane's window column
-  float* col = win + warp * P.W * kWarp + lane;
-  for (int k = 0; k < P.W; ++k) col[k * kWarp] = 0.f;
+  float* col = win + warp * Q.W * kWarp + lane;
+  for (int k = 0; k < Q.W; ++k) col[k * kWarp] = 0.f;
 
   // 3. per-(cube, element) reference in FP64
-  const double* xp = P.xw + (static_cast<int64_t>(f) * P.E + jj) * 3;
+  const double* xp = G.xw + (static_cast<int64_t>(f) * G.E + jj) * 3;
   const double hc = 0.5 * (C - 1);
-  const PairRef R = make_ref(xp[0], xp[1], xp[2], P.ox + P.dx * (cx * C + hc), P.oy + P.dy * (cy * C + hc),
-                             P.oz + P.dz * (cz * C + hc), P.sup, P.tau0, P.inv_h);
-  const int nb_rel = static_cast<int>(floorf(R.phim - P.nb_shift)) - 1;
-  const float dxf = static_cast<float>(P.dx), dyf = static_cast<float>(P.dy), dzf = static_cast<float>(P.dz);
+  const PairRef R = make_ref(xp[0], xp[1], xp[2], G.ox + G.dx * (cx * C + hc), G.oy + G.dy * (cy * C + hc),
+                             G.oz + G.dz * (cz * C + hc), Q.sup, Q.tau0, Q.inv_h);
+  const int nb_rel = static_cast<int>(floorf(R.phim - Q.nb_shift)) - 1;
+  const float dxf = static_cast<float>(G.dx), dyf = static_cast<float>(G.dy), dzf = static_cast<float>(G.dz);
   float Pix[C];
 #pragma unroll
   for (int ix = 0; ix < C; ++ix) {
@@ -233,10 +247,10 @@ __global__ void __launch_bounds__(256, 2)
 
   // 4. wait for the tile; flag rows that hold any nonzero voxel
   bool ok = true;
-  if (P.use_tma) ok = mbar_wait_limited(bar, 0, P.status, P.wait_cycles);
+  if (G.use_tma) ok = mbar_wait_limited(bar, parity, G.status, Q.wait_cycles);
   if (__syncthreads_or(!ok)) {
-    if (tid == 0) mbar_wait_bounded(bar, 0, P.status);  // let the copy land before exit
-    return;
+    if (tid == 0) mbar_wait_bounded(bar, parity, G.status);  // let the copy land before exit
+    return false;
   }
   for (int r = tid; r < C * C; r += blockDim.x) {
     bool nz = false;
@@ -247,7 +261,7 @@ __global__ void __launch_bounds__(256, 2)
   __syncthreads();
 
   // 5. pair loop: every voxel of the cube against this lane's element
-  const unsigned max_idx = static_cast<unsigned>(P.W - S);
+  const unsigned max_idx = static_cast<unsigned>(Q.W - S);
   const int idx_bias = kMagicBits + nb_rel;
   // Clamp detection.  A voxel's distance to the element is convex along a row, and the
   // first slot index grows with the distance, so a row's largest index is at one of its
@@ -279,7 +293,7 @@ __global__ void __launch_bounds__(256, 2)
           for (int u = 0; u < 4; u += 2) {
             const int i = i4 + u;
             const float2 pv = u == 0 ? make_float2(pv4.x, pv4.y) : make_float2(pv4.z, pv4.w);
-            const PairMath2 m = pair_math2(add2(Pix2[i / 2], f2(Crow)), R.dc2, R.dcf, R.phim, P.inv_hf, P.h, P.cb1,
+            const PairMath2 m = pair_math2(add2(Pix2[i / 2], f2(Crow)), R.dc2, R.dcf, R.phim, Q.inv_hf, Q.h, Q.cb1,
                                            idx_bias);
             if (i == 0) seen = max(seen, m.idx0);
             if (i + 1 == C - 1) seen = max(seen, m.idx1);
@@ -289,16 +303,16 @@ __global__ void __launch_bounds__(256, 2)
             float2 c[S - 1];  // b_{k+1} - b_0
             if constexpr (K == PASFM_KERNEL_GAUSS) {
               float2 E[S];
-              gauss_boundaries2<S>(m.beta1, P.h, P.gs, E);
+              gauss_boundaries2<S>(m.beta1, Q.h, Q.gs, E);
 #pragma unroll
-              for (int k = 0; k <= S - 2; ++k) c[k] = fma2(E[k + 1], f2(-1.f), f2(P.gs.e_clamp));
+              for (int k = 0; k <= S - 2; ++k) c[k] = fma2(E[k + 1], f2(-1.f), f2(Q.gs.e_clamp));
             } else {
               float2 beta = m.beta1;
 #pragma unroll
               for (int k = 0; k <= S - 2; ++k) {
-                if (k > 0) beta = add2(beta, f2(P.h));
-                const float2 bc = (k == S - 2) ? min2(beta, P.supf) : beta;
-                c[k] = fma2(bc, bc, f2(-P.sup2));
+                if (k > 0) beta = add2(beta, f2(Q.h));
+                const float2 bc = (k == S - 2) ? min2(beta, Q.supf) : beta;
+                c[k] = fma2(bc, bc, f2(-Q.sup2));
               }
             }
 #pragma unroll
@@ -313,18 +327,18 @@ __global__ void __launch_bounds__(256, 2)
         // whose difference cancels in homogeneous regions, so the weights go in directly.
 #pragma unroll
         for (int i = 0; i < C; ++i) {
-          const PairMath m = pair_math(Pix[i] + Crow, R.dc2, R.dcf, R.phim, P.inv_hf, P.h, P.cb1, idx_bias);
+          const PairMath m = pair_math(Pix[i] + Crow, R.dc2, R.dcf, R.phim, Q.inv_hf, Q.h, Q.cb1, idx_bias);
           if (i == 0 || i == C - 1) seen = max(seen, m.idx);
           float* slot = col + min(m.idx, max_idx) * kWarp;
           const float s = prow[i] * m.rs;
           float w;
           if constexpr (K == PASFM_KERNEL_GAUSS) {
             float E[S];
-            gauss_boundaries<S>(m.beta1, P.h, P.gs, E);
-            w = E[1] - P.gs.e_clamp;
+            gauss_boundaries<S>(m.beta1, Q.h, Q.gs, E);
+            w = E[1] - Q.gs.e_clamp;
           } else {
-            const float bc = fminf(m.beta1, P.supf);
-            w = fmaf(-bc, bc, P.sup2);
+            const float bc = fminf(m.beta1, Q.supf);
+            w = fmaf(-bc, bc, Q.sup2);
           }
           slot[0] = fmaf(s, w, slot[0]);
           slot[kWarp] = fmaf(-s, w, slot[kWarp]);
@@ -332,31 +346,82 @@ __global__ void __launch_bounds__(256, 2)
       }
     }
   }
-  if (seen > max_idx) atomicOr(P.status, PASFM_STATUS_INDEX_CLAMPED);
+  if (seen > max_idx) atomicOr(G.status, PASFM_STATUS_INDEX_CLAMPED);
 
   // 6. flush the window (its first difference for S >= 3) as this cube's partial trace
   //    (scaled by 1 / (4 h), or sigma^2 / (2 h))
   __syncwarp();
   if (valid) {
-    const int64_t row = static_cast<int64_t>(fl) * P.E + j;
-    float* dst = P.part + (row * ncubes + c) * P.W;
+    const int64_t row = static_cast<int64_t>(fl) * G.E + j;
+    float* dst = G.part + (row * ncubes + c) * Q.W;
     float prev = 0.f;
-    for (int k = 0; k < P.W; k += 4) {
+    for (int k = 0; k < Q.W; k += 4) {
       const float c0 = col[(k + 0) * kWarp], c1 = col[(k + 1) * kWarp], c2 = col[(k + 2) * kWarp],
                   c3 = col[(k + 3) * kWarp];
       float4 v;
       if constexpr (S >= 3) {  // minus the running sum: T_k = W_{k-1} - W_k
-        v.x = (prev - c0) * P.p0_scale;
-        v.y = (c0 - c1) * P.p0_scale;
-        v.z = (c1 - c2) * P.p0_scale;
-        v.w = (c2 - c3) * P.p0_scale;
+        v.x = (prev - c0) * Q.p0_scale;
+        v.y = (c0 - c1) * Q.p0_scale;
+        v.z = (c1 - c2) * Q.p0_scale;
+        v.w = (c2 - c3) * Q.p0_scale;
         prev = c3;
       } else {
-        v = make_float4(c0 * P.p0_scale, c1 * P.p0_scale, c2 * P.p0_scale, c3 * P.p0_scale);
+        v = make_float4(c0 * Q.p0_scale, c1 * Q.p0_scale, c2 * Q.p0_scale, c3 * Q.p0_scale);
       }
       *reinterpret_cast<float4*>(dst + k) = v;
     }
-    P.n0tab[row * ncubes + c] = R.Nc + nb_rel;
+    G.n0tab[row * ncubes + c] = R.Nc + nb_rel;
+  }
+  return true;
+}
+
+
+template <int C, int S, int K>
+__global__ void __launch_bounds__(256, 2)
+    fwd_cube_kernel(const __grid_constant__ CUtensorMap p0map, const FwdParams P) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const FwdSmem<C> sm(smem);
+  if (threadIdx.x == 0) {
+    mbar_init(sm.bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  fwd_tile<C, S, K>(&p0map, P, P, sm, blockIdx.x, gridDim.x, blockIdx.y, blockIdx.z, 0);
+}
+
+// Persistent forward over the tiles of several scans that share one instantiation and
+// profile (one launch per serving iteration and group): CTAs take tiles from a global
+// counter until the list is exhausted.  Scan s owns tiles [tiles[s], tiles[s + 1]), a
+// tile being (cube, frame of the chunk, element group) with the cube fastest, exactly
+// the block coordinates of its single-scan launch, so a scan's results do not depend on
+// the other scans of the batch.
+template <int C, int S, int K>
+__global__ void __launch_bounds__(256, 2)
+    fwd_batch_kernel(const __grid_constant__ TmaBatch maps, const __grid_constant__ FwdBatch B) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ int s_tile;
+  const FwdSmem<C> sm(smem);
+  if (threadIdx.x == 0) {
+    mbar_init(sm.bar, 1);
+    fence_mbar_init();
+  }
+  uint32_t phase = 0;  // completed phases of the staging barrier
+  const int total = B.tiles[B.n];
+  while (true) {
+    if (threadIdx.x == 0) s_tile = atomicAdd(B.counter, 1);
+    __syncthreads();  // also: the previous tile's shared memory is free
+    const int t = s_tile;
+    if (t >= total) break;
+    int s = 0;
+    while (t >= B.tiles[s + 1]) ++s;
+    const FwdParams& G = B.G[s];
+    const int local = t - B.tiles[s], nc = B.ncubes[s];
+    const int c = local % nc, rest = local / nc;
+    const unsigned long long t0 = B.trace ? globaltimer() : 0ull;
+    if (!fwd_tile<C, S, K>(&maps.m[s], B.Q, G, sm, c, nc, rest % B.fc[s], rest / B.fc[s], phase & 1)) return;
+    if (G.use_tma) ++phase;
+    if (B.trace && threadIdx.x == 0) trace_tile(B.trace, s, t0);
+    __syncthreads();  // every thread is past s_tile before thread 0 takes the next tile
   }
 }
 
@@ -531,12 +596,20 @@ __device__ __forceinline__ void bwd_thread_row(int tid, int& ty, int& tz) {
 // live in shared memory), whose 24 warps hide the dependent chains better than two CTAs
 // at 128 registers, at the price of a few spilled registers (measured 2% faster on the
 // sphere, 4% on the Gaussian at S = 12); eight 8^3 CTAs.
+// One backward tile: cube c (of ncubes) against part `part` of the (frame, element) items
+// of the launch's frame chunk.  Q holds what every scan of a launch shares (pulse profile,
+// slot count, staged window length, wait bound), G the scan's own fields; a single-scan
+// launch passes its one parameter block for both.  The caller has initialised the two
+// staging barriers; par0 / par1 are the phases their next completions carry.  Returns
+// false when a staged-copy wait ran out: the copies in flight have landed and the CTA must
+// exit.  On return every batch this tile staged has been waited for; *nbatches receives
+// their count (batch b used buffer b & 1).
 template <int C, int S, int K, bool ADJ, bool POSE>
-__global__ void __launch_bounds__(C* C, (C == 16 ? 3 : 8))
-    bwd_cube_kernel(const __grid_constant__ CUtensorMap gmap, const BwdParams P) {
+__device__ __forceinline__ bool bwd_tile(const CUtensorMap* gmap, const BwdParams& Q, const BwdParams& G,
+                                         unsigned char* smem, int c, int ncubes, int part, uint32_t par0,
+                                         uint32_t par1, int* nbatches) {
   using L = BwdLayout<C>;
-  extern __shared__ __align__(128) unsigned char smem[];
-  const int WP = P.WP;
+  const int WP = Q.WP;
   float* win = reinterpret_cast<float*>(smem);
   float4* refa = reinterpret_cast<float4*>(smem + L::refa_off(WP));
   float4* refb = reinterpret_cast<float4*>(smem + L::refb_off(WP));
@@ -547,16 +620,15 @@ __global__ void __launch_bounds__(C* C, (C == 16 ? 3 : 8))
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L::bar_off(WP));
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int c = blockIdx.x, ncubes = gridDim.x;
-  const int cx = c % P.ncx, cy = (c / P.ncx) % P.ncy, cz = c / (P.ncx * P.ncy);
+  const int cx = c % G.ncx, cy = (c / G.ncx) % G.ncy, cz = c / (G.ncx * G.ncy);
   int ty, tz;
   bwd_thread_row<C>(tid, ty, tz);
   const int iy = cy * C + ty, iz = cz * C + tz;
-  const bool row_in = iy < P.ny && iz < P.nz;
+  const bool row_in = iy < G.ny && iz < G.nz;
 
-  const float dxf = static_cast<float>(P.dx);
-  const float qy = (ty - 0.5f * (C - 1)) * static_cast<float>(P.dy);
-  const float qz = (tz - 0.5f * (C - 1)) * static_cast<float>(P.dz);
+  const float dxf = static_cast<float>(G.dx);
+  const float qy = (ty - 0.5f * (C - 1)) * static_cast<float>(G.dy);
+  const float qz = (tz - 0.5f * (C - 1)) * static_cast<float>(G.dz);
 
   // p0 and p0 q_x along this thread's row, voxels (2k, 2k + 1)
   float2 p0s2[POSE ? C / 2 : 1], p0qx2[POSE ? C / 2 : 1];
@@ -564,8 +636,8 @@ __global__ void __launch_bounds__(C* C, (C == 16 ? 3 : 8))
 #pragma unroll
     for (int k = 0; k < C; ++k) {
       const int ix = cx * C + k;
-      const float v = (row_in && ix < P.nx)
-                          ? load_elem(P.p0, (static_cast<int64_t>(iz) * P.ny + iy) * P.nx + ix, P.dtype_vol) * P.scale
+      const float v = (row_in && ix < G.nx)
+                          ? load_elem(G.p0, (static_cast<int64_t>(iz) * G.ny + iy) * G.nx + ix, G.dtype_vol) * Q.scale
                           : 0.f;
       const float vq = v * ((k - 0.5f * (C - 1)) * dxf);
       if (k % 2) {
@@ -587,19 +659,15 @@ __global__ void __launch_bounds__(C* C, (C == 16 ? 3 : 8))
   }
 
   const double hc = 0.5 * (C - 1);
-  const double rcx = P.ox + P.dx * (cx * C + hc), rcy = P.oy + P.dy * (cy * C + hc),
-               rcz = P.oz + P.dz * (cz * C + hc);
+  const double rcx = G.ox + G.dx * (cx * C + hc), rcy = G.oy + G.dy * (cy * C + hc),
+               rcz = G.oz + G.dz * (cz * C + hc);
   // this CTA's share of the (frame, element) items: [ib, ib + nl)
-  const int ib = blockIdx.y * P.part_items;
-  const int nl = max(0, min(P.n_items - ib, P.part_items));
+  const int ib = part * G.part_items;
+  const int nl = max(0, min(G.n_items - ib, G.part_items));
   const int nb = (nl + kBatch - 1) / kBatch;
-
-  if (tid == 0) {
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
-    fence_mbar_init();
-  }
-  __syncthreads();
+  *nbatches = nb;
+  // phase of batch b's completion on its buffer b & 1
+  auto parity = [&](int b) -> uint32_t { return ((b & 1 ? par1 : par0) + (b >> 1)) & 1u; };
 
   // producer: one warp stages batch b into buffer buf (lane l handles trace l)
   auto issue = [&](int b, int buf) {
@@ -608,14 +676,14 @@ __global__ void __launch_bounds__(C* C, (C == 16 ? 3 : 8))
     float* wdst = win + (buf * kBatch + lane) * WP;
     int x0 = 0, row = 0;
     if (it < ib + nl) {
-      const int fl = it / P.E, j = it % P.E;
-      const int f = P.f_begin + fl;
-      row = f * P.E + j;
-      const double* xp = P.xw + static_cast<int64_t>(row) * 3;
-      const PairRef R = make_ref(xp[0], xp[1], xp[2], rcx, rcy, rcz, P.sup, P.tau0, P.inv_h);
-      const int n0 = R.Nc + static_cast<int>(floorf(R.phim - P.nb_shift)) - 1;
+      const int fl = it / G.E, j = it % G.E;
+      const int f = G.f_begin + fl;
+      row = f * G.E + j;
+      const double* xp = G.xw + static_cast<int64_t>(row) * 3;
+      const PairRef R = make_ref(xp[0], xp[1], xp[2], rcx, rcy, rcz, Q.sup, Q.tau0, Q.inv_h);
+      const int n0 = R.Nc + static_cast<int>(floorf(R.phim - Q.nb_shift)) - 1;
       x0 = n0 & ~3;
-      const float mk = (POSE && P.mask) ? (P.mask[row] ? 1.f : 0.f) : 1.f;
+      const float mk = (POSE && G.mask) ? (G.mask[row] ? 1.f : 0.f) : 1.f;
       refa[buf * kBatch + lane] = make_float4(R.m2ux, R.m2uy, R.m2uz, R.dc2);
       // the x part of A, q_x (q_x - 2 u_x), for the C voxels of a row: the same for every
       // row of the cube, so formed once per trace
@@ -631,19 +699,22 @@ __global__ void __launch_bounds__(C* C, (C == 16 ? 3 : 8))
         refu[(buf * kBatch + lane) * 3 + 1] = R.uy;
         refu[(buf * kBatch + lane) * 3 + 2] = R.uz;
       }
-      if (!P.use_tma) {  // plain loads with zero fill outside [0, Nt)
-        const int64_t base = static_cast<int64_t>(row) * P.Nt;
+      if (!G.use_tma) {  // plain loads with zero fill outside [0, Nt)
+        const int64_t base = static_cast<int64_t>(row) * G.Nt;
         for (int k = 0; k < WP; ++k) {
           const int n = x0 + k;
-          wdst[k] = (n >= 0 && n < P.Nt) ? load_elem(P.g, base + n, P.dtype_sig) : 0.f;
+          wdst[k] = (n >= 0 && n < G.Nt) ? load_elem(G.g, base + n, G.dtype_sig) : 0.f;
         }
       }
     }
-    if (P.use_tma) {
+    if (G.use_tma) {
       __syncwarp();  // the warp's reference writes happen before lane 0's (releasing) arrival
-      if (lane == 0) mbar_arrive_expect_tx(&bar[buf], static_cast<uint32_t>(cnt * WP * 4));
+      if (lane == 0) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // earlier reads of the buffer
+        mbar_arrive_expect_tx(&bar[buf], static_cast<uint32_t>(cnt * WP * 4));
+      }
       __syncwarp();
-      if (it < ib + nl) tma_load_2d(wdst, &gmap, &bar[buf], x0, row);
+      if (it < ib + nl) tma_load_2d(wdst, gmap, &bar[buf], x0, row);
     } else {
       __threadfence_block();
       __syncwarp();
@@ -667,7 +738,7 @@ __global__ void __launch_bounds__(C* C, (C == 16 ? 3 : 8))
   unsigned seen = 0;  // largest raw window index at the row ends (see fwd_cube_kernel)
   for (int b = 0; b < nb; ++b) {
     const int buf = b & 1;
-    const bool ok = mbar_wait_limited(&bar[buf], (b >> 1) & 1, P.status, P.wait_cycles);
+    const bool ok = mbar_wait_limited(&bar[buf], parity(b), G.status, Q.wait_cycles);
     const int cnt = min(kBatch, nl - b * kBatch);
     const float* wb = win + buf * kBatch * WP;
     for (int e = 0; ok && e < cnt; ++e) {
@@ -682,12 +753,12 @@ __global__ void __launch_bounds__(C* C, (C == 16 ? 3 : 8))
       for (int k2 = 0; k2 < C / 2; ++k2) {
         const int k = 2 * k2;
         const float2 A = add2(pe[k2], f2(Crow));
-        const PairMath2 m = pair_math2(A, ra.w, rb.x, rb.y, P.inv_hf, P.h, P.cb1, idx_bias);
+        const PairMath2 m = pair_math2(A, ra.w, rb.x, rb.y, Q.inv_hf, Q.h, Q.cb1, idx_bias);
         if (k == 0) seen = max(seen, m.idx0);
         if (k + 1 == C - 1) seen = max(seen, m.idx1);
         float2 S1, S2 = f2(0.f);
         float lam;
-        slot_sums2<S, K, POSE, !ADJ>(wv + min(m.idx0, max_idx), wv + min(m.idx1, max_idx), m.beta1, P, S1, S2, lam);
+        slot_sums2<S, K, POSE, !ADJ>(wv + min(m.idx0, max_idx), wv + min(m.idx1, max_idx), m.beta1, Q, S1, S2, lam);
         const float2 t1 = mul2(m.rs, S1);
         if (ADJ) bacc[k2] = add2(bacc[k2], t1);
         if (POSE) {  // minus the coefficient: p0 (1/d^2) (t1 - dW/dd boundary term)
@@ -722,10 +793,10 @@ __global__ void __launch_bounds__(C* C, (C == 16 ? 3 : 8))
     }
     if (__syncthreads_or(!ok)) {
       if (tid == 0) {  // let copies in flight land before the CTA exits
-        mbar_wait_bounded(&bar[buf], (b >> 1) & 1, P.status);
-        if (b + 1 < nb) mbar_wait_bounded(&bar[buf ^ 1], ((b + 1) >> 1) & 1, P.status);
+        mbar_wait_bounded(&bar[buf], parity(b), G.status);
+        if (b + 1 < nb) mbar_wait_bounded(&bar[buf ^ 1], parity(b + 1), G.status);
       }
-      return;
+      return false;
     }
     if (warp == b % L::NW) {
       if (POSE && lane < cnt) {
@@ -739,7 +810,7 @@ __global__ void __launch_bounds__(C* C, (C == 16 ? 3 : 8))
         }
         const float mk = refb[buf * kBatch + lane].w;
         const double* u = refu + (buf * kBatch + lane) * 3;
-        double* gp = P.gpart + (static_cast<int64_t>(ib + b * kBatch + lane) * ncubes + c) * 3;
+        double* gp = G.gpart + (static_cast<int64_t>(ib + b * kBatch + lane) * ncubes + c) * 3;
         gp[0] = mk * (u[0] * r0 - r1);
         gp[1] = mk * (u[1] * r0 - r2);
         gp[2] = mk * (u[2] * r0 - r3);
@@ -748,23 +819,76 @@ __global__ void __launch_bounds__(C* C, (C == 16 ? 3 : 8))
       if (b + 2 < nb) issue(b + 2, buf);
     }
   }
-  if (seen > max_idx) atomicOr(P.status, PASFM_STATUS_INDEX_CLAMPED);
+  if (seen > max_idx) atomicOr(G.status, PASFM_STATUS_INDEX_CLAMPED);
 
   if (ADJ && row_in) {
     // one part: straight into the volume; several: into this part's slice of vol_parts,
     // summed in part order by sum_parts_kernel
-    const int64_t nvox = static_cast<int64_t>(P.nx) * P.ny * P.nz;
-    float* out = (P.n_parts > 1 ? P.vol_parts + blockIdx.y * nvox : P.vol) +
-                 (static_cast<int64_t>(iz) * P.ny + iy) * P.nx;
-    const bool add = P.n_parts == 1 && P.accumulate;
+    const int64_t nvox = static_cast<int64_t>(G.nx) * G.ny * G.nz;
+    float* out = (G.n_parts > 1 ? G.vol_parts + part * nvox : G.vol) +
+                 (static_cast<int64_t>(iz) * G.ny + iy) * G.nx;
+    const bool add = G.n_parts == 1 && G.accumulate;
 #pragma unroll
     for (int k = 0; k < C; ++k) {
       const int ix = cx * C + k;
-      if (ix < P.nx) {
-        const float v = accs[k * L::NT + tid] * P.scale;
+      if (ix < G.nx) {
+        const float v = accs[k * L::NT + tid] * Q.scale;
         out[ix] = add ? out[ix] + v : v;
       }
     }
+  }
+  return true;
+}
+
+
+template <int C, int S, int K, bool ADJ, bool POSE>
+__global__ void __launch_bounds__(C* C, (C == 16 ? 3 : 8))
+    bwd_cube_kernel(const __grid_constant__ CUtensorMap gmap, const BwdParams P) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + BwdLayout<C>::bar_off(P.WP));
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  int nb;
+  bwd_tile<C, S, K, ADJ, POSE>(&gmap, P, P, smem, blockIdx.x, gridDim.x, blockIdx.y, 0, 0, &nb);
+}
+
+// Persistent backward over the tiles of several scans sharing one instantiation and
+// profile: a tile is (cube, part), the cube fastest, as the block coordinates of the
+// scan's single-scan launch (the same part split), so its results do not depend on the
+// batch.  The two staging barriers keep their phases across tiles.
+template <int C, int S, int K, bool ADJ, bool POSE>
+__global__ void __launch_bounds__(C* C, (C == 16 ? 3 : 8))
+    bwd_batch_kernel(const __grid_constant__ TmaBatch maps, const __grid_constant__ BwdBatch B) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ int s_tile;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + BwdLayout<C>::bar_off(B.Q.WP));
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_mbar_init();
+  }
+  uint32_t par0 = 0, par1 = 0;
+  const int total = B.tiles[B.n];
+  while (true) {
+    if (threadIdx.x == 0) s_tile = atomicAdd(B.counter, 1);
+    __syncthreads();  // also: the previous tile's shared memory is free
+    const int t = s_tile;
+    if (t >= total) break;
+    int s = 0;
+    while (t >= B.tiles[s + 1]) ++s;
+    const int local = t - B.tiles[s], nc = B.ncubes[s];
+    const unsigned long long t0 = B.trace ? globaltimer() : 0ull;
+    int nb = 0;
+    if (!bwd_tile<C, S, K, ADJ, POSE>(&maps.m[s], B.Q, B.G[s], smem, local % nc, nc, local / nc, par0, par1, &nb))
+      return;
+    par0 ^= ((nb + 1) >> 1) & 1u;  // batches 0, 2, 4, ... completed on buffer 0
+    par1 ^= (nb >> 1) & 1u;
+    if (B.trace && threadIdx.x == 0) trace_tile(B.trace, s, t0);
+    __syncthreads();  // every thread is past s_tile before thread 0 takes the next tile
   }
 }
 

@@ -46,6 +46,90 @@ static int bwd_occupancy_c(size_t smem) {
   return n;
 }
 
+template <int C>
+static cudaError_t fwd_batch_launch_c(const TmaBatch& maps, const FwdBatch& B, int ctas, int threads, size_t smem,
+                                      cudaStream_t st) {
+  auto k = fwd_batch_kernel<C, PASFM_S, PASFM_K>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  if (e != cudaSuccess) return e;
+  k<<<ctas, threads, smem, st>>>(maps, B);
+  return cudaPeekAtLastError();
+}
+
+template <int C>
+static int fwd_batch_occupancy_c(int threads, size_t smem) {
+  auto k = fwd_batch_kernel<C, PASFM_S, PASFM_K>;
+  int n = 0;
+  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, threads, smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
+}
+
+template <int C, bool ADJ, bool POSE>
+static cudaError_t bwd_batch_launch_c(const TmaBatch& maps, const BwdBatch& B, int ctas, size_t smem,
+                                      cudaStream_t st) {
+  auto k = bwd_batch_kernel<C, PASFM_S, PASFM_K, ADJ, POSE>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  if (e != cudaSuccess) return e;
+  k<<<ctas, C * C, smem, st>>>(maps, B);
+  return cudaPeekAtLastError();
+}
+
+template <int C, bool ADJ, bool POSE>
+static int bwd_batch_occupancy_c(size_t smem) {
+  auto k = bwd_batch_kernel<C, PASFM_S, PASFM_K, ADJ, POSE>;
+  int n = 0;
+  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, C * C, smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
+}
+
+cudaError_t PASFM_NAME(fwd_batch_launch)(int C, const TmaBatch& maps, const FwdBatch& B, int ctas, int threads,
+                                         size_t smem, cudaStream_t st) {
+  if (C == 16) return fwd_batch_launch_c<16>(maps, B, ctas, threads, smem, st);
+  if (C == 8) return fwd_batch_launch_c<8>(maps, B, ctas, threads, smem, st);
+  return cudaErrorInvalidValue;
+}
+
+int PASFM_NAME(fwd_batch_occupancy)(int C, int threads, size_t smem) {
+  if (C == 16) return fwd_batch_occupancy_c<16>(threads, smem);
+  if (C == 8) return fwd_batch_occupancy_c<8>(threads, smem);
+  return 0;
+}
+
+cudaError_t PASFM_NAME(bwd_batch_launch)(int C, int mode, const TmaBatch& maps, const BwdBatch& B, int ctas,
+                                         size_t smem, cudaStream_t st) {
+  if (C == 16) {
+    if (mode == 1) return bwd_batch_launch_c<16, true, false>(maps, B, ctas, smem, st);
+    if (mode == 2) return bwd_batch_launch_c<16, false, true>(maps, B, ctas, smem, st);
+    if (mode == 3) return bwd_batch_launch_c<16, true, true>(maps, B, ctas, smem, st);
+  } else if (C == 8) {
+    if (mode == 1) return bwd_batch_launch_c<8, true, false>(maps, B, ctas, smem, st);
+    if (mode == 2) return bwd_batch_launch_c<8, false, true>(maps, B, ctas, smem, st);
+    if (mode == 3) return bwd_batch_launch_c<8, true, true>(maps, B, ctas, smem, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+int PASFM_NAME(bwd_batch_occupancy)(int C, int mode, size_t smem) {
+  if (C == 16) {
+    if (mode == 1) return bwd_batch_occupancy_c<16, true, false>(smem);
+    if (mode == 2) return bwd_batch_occupancy_c<16, false, true>(smem);
+    if (mode == 3) return bwd_batch_occupancy_c<16, true, true>(smem);
+  } else if (C == 8) {
+    if (mode == 1) return bwd_batch_occupancy_c<8, true, false>(smem);
+    if (mode == 2) return bwd_batch_occupancy_c<8, false, true>(smem);
+    if (mode == 3) return bwd_batch_occupancy_c<8, true, true>(smem);
+  }
+  return 0;
+}
+
 cudaError_t PASFM_NAME(fwd_launch)(int C, const CUtensorMap& map, const FwdParams& P, dim3 grid,
                                              int threads, size_t smem, cudaStream_t st) {
   if (C == 16) return fwd_launch_c<16>(map, P, grid, threads, smem, st);

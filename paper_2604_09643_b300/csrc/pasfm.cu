@@ -171,7 +171,7 @@ int frames_per_chunk(size_t per_frame, size_t budget, int F) {
 struct pasfm_ctx {
   int device = 0;
   unsigned* status = nullptr;
-  Buf xw, part, n0, gres, vgrad, gpart, G, grad6, lpart, lscalar, taps, vparts, gw, tpart, gdiff;
+  Buf xw, part, n0, gres, vgrad, gpart, G, grad6, lpart, lscalar, taps, vparts, gw, tpart, gdiff, bcount;
   int sms = 0;  // streaming multiprocessors of the device
   size_t budget = kDefaultPartialBudget;
   long long wait_cycles = kWaitCycles;  // bound of the kernels' first wait for each staged copy
@@ -330,24 +330,14 @@ int run_elem_pos(pasfm_ctx* ctx, const Geo& G, const double* elem, const double*
   return check_launch("elem_pos");
 }
 
-// Forward over all frames: per-cube kernels then the ordered reduction.
-// Writes sig_out (may be null) and/or the masked residual g_out with loss.
-int run_forward(pasfm_ctx* ctx, const Geo& G, const Plan& pl, const void* p0, const double* xw, float* sig_out,
-                float* g_out, const void* meas, const uint8_t* mask, double* loss_out, cudaStream_t st) {
+// Forward parameter block and p0 staging map of one scan (every field but f_begin), and
+// its partial-result workspace for frame chunks of Fc frames.
+int fwd_setup(pasfm_ctx* ctx, const Geo& G, const Plan& pl, const void* p0, const double* xw, int Fc, FwdParams* out,
+              CUtensorMap* map) {
   const pasfm_geom& g = G.g;
-  const int F = g.n_frames, E = g.n_elem, Nt = g.n_samples;
-  const int Fc = frames_per_chunk(fwd_per_frame(G, pl), ctx->budget, F);
-  TRY(ctx->ensure(ctx->part, size_t(Fc) * E * pl.ncubes * pl.W * 4));
-  TRY(ctx->ensure(ctx->n0, size_t(Fc) * E * pl.ncubes * 4));
-  const int n_chunks = (F + Fc - 1) / Fc;
-  const int blocks_total = static_cast<int>((G.n_rows + 7) / 8) + n_chunks;
-  if (g_out) {
-    TRY(ctx->ensure(ctx->lpart, size_t(blocks_total) * 8));
-    TRY(ctx->ensure(ctx->lscalar, 8));
-  }
-
-  CUtensorMap map;
-  std::memset(&map, 0, sizeof map);
+  TRY(ctx->ensure(ctx->part, size_t(Fc) * g.n_elem * pl.ncubes * pl.W * 4));
+  TRY(ctx->ensure(ctx->n0, size_t(Fc) * g.n_elem * pl.ncubes * 4));
+  std::memset(map, 0, sizeof *map);
   int use_tma = 0;
   auto enc = encode_fn();
   if (enc && g.dtype_vol == PASFM_F32 && g.nx % 4 == 0 && aligned16(p0)) {
@@ -355,12 +345,11 @@ int run_forward(pasfm_ctx* ctx, const Geo& G, const Plan& pl, const void* p0, co
     cuuint64_t strides[2] = {cuuint64_t(g.nx) * 4, cuuint64_t(g.nx) * g.ny * 4};
     cuuint32_t box[3] = {cuuint32_t(pl.C), cuuint32_t(pl.C), cuuint32_t(pl.C)};
     cuuint32_t es[3] = {1, 1, 1};
-    if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(p0), dims, strides, box, es,
+    if (enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(p0), dims, strides, box, es,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS)
       use_tma = 1;
   }
-
   FwdParams P{};
   P.xw = xw;
   P.p0 = p0;
@@ -372,7 +361,7 @@ int run_forward(pasfm_ctx* ctx, const Geo& G, const Plan& pl, const void* p0, co
   P.nz = g.nz;
   P.ncx = pl.ncx;
   P.ncy = pl.ncy;
-  P.E = E;
+  P.E = g.n_elem;
   P.W = pl.W;
   P.ox = g.ox;
   P.oy = g.oy;
@@ -385,10 +374,55 @@ int run_forward(pasfm_ctx* ctx, const Geo& G, const Plan& pl, const void* p0, co
   P.use_tma = use_tma;
   P.wait_cycles = ctx->wait_cycles;
   P.status = ctx->status;
+  *out = P;
+  return PASFM_OK;
+}
+
+size_t fwd_smem(const Plan& pl) {
+  return size_t(pl.C == 16 ? fwd_win_offset<16>() : fwd_win_offset<8>()) + size_t(pl.fwd_warps) * pl.W * 32 * 4;
+}
+
+// Reduction of one frame chunk [fb, fb + fc) of a scan's forward partials.
+RedParams red_params(const FwdParams& P, const Geo& G, const Plan& pl, int fb, int fc, float* sig_out, float* g_out,
+                     const void* meas, const uint8_t* mask, double* loss_part, int loss_off) {
+  RedParams R{};
+  R.part = P.part;
+  R.n0tab = P.n0tab;
+  R.E = G.g.n_elem;
+  R.f_begin = fb;
+  R.n_rows = fc * G.g.n_elem;
+  R.ncubes = pl.ncubes;
+  R.W = pl.W;
+  R.Nt = G.g.n_samples;
+  R.sig_out = sig_out;
+  R.g_out = g_out;
+  R.meas = meas;
+  R.dtype_sig = G.g.dtype_sig;
+  R.mask = mask;
+  R.loss_part = loss_part;
+  R.loss_offset = loss_off;
+  return R;
+}
+
+// Forward over all frames: per-cube kernels then the ordered reduction.
+// Writes sig_out (may be null) and/or the masked residual g_out with loss.
+int run_forward(pasfm_ctx* ctx, const Geo& G, const Plan& pl, const void* p0, const double* xw, float* sig_out,
+                float* g_out, const void* meas, const uint8_t* mask, double* loss_out, cudaStream_t st) {
+  const pasfm_geom& g = G.g;
+  const int F = g.n_frames;
+  const int Fc = frames_per_chunk(fwd_per_frame(G, pl), ctx->budget, F);
+  const int n_chunks = (F + Fc - 1) / Fc;
+  const int blocks_total = static_cast<int>((G.n_rows + 7) / 8) + n_chunks;
+  if (g_out) {
+    TRY(ctx->ensure(ctx->lpart, size_t(blocks_total) * 8));
+    TRY(ctx->ensure(ctx->lscalar, 8));
+  }
+  FwdParams P;
+  CUtensorMap map;
+  TRY(fwd_setup(ctx, G, pl, p0, xw, Fc, &P, &map));
 
   const int threads = 32 * pl.fwd_warps;
-  const size_t smem = size_t(pl.C == 16 ? fwd_win_offset<16>() : fwd_win_offset<8>()) +
-                      size_t(pl.fwd_warps) * pl.W * 32 * 4;
+  const size_t smem = fwd_smem(pl);
   int loss_off = 0;
   for (int fb = 0; fb < F; fb += Fc) {
     const int fc = std::min(Fc, F - fb);
@@ -402,22 +436,8 @@ int run_forward(pasfm_ctx* ctx, const Geo& G, const Plan& pl, const void* p0, co
       return fail(PASFM_ECUDA, "fwd_cube launch: %s", cudaGetErrorString(e));
     }
 
-    RedParams R{};
-    R.part = P.part;
-    R.n0tab = P.n0tab;
-    R.E = E;
-    R.f_begin = fb;
-    R.n_rows = fc * E;
-    R.ncubes = pl.ncubes;
-    R.W = pl.W;
-    R.Nt = Nt;
-    R.sig_out = sig_out;
-    R.g_out = g_out;
-    R.meas = meas;
-    R.dtype_sig = g.dtype_sig;
-    R.mask = mask;
-    R.loss_part = g_out ? static_cast<double*>(ctx->lpart.p) : nullptr;
-    R.loss_offset = loss_off;
+    const RedParams R = red_params(P, G, pl, fb, fc, sig_out, g_out, meas, mask,
+                                   g_out ? static_cast<double*>(ctx->lpart.p) : nullptr, loss_off);
     const int rblocks = (R.n_rows + 7) / 8;
     t = ctx->begin(st);
     const cudaError_t re = fwd_reduce_launch(R, rblocks, st);
@@ -435,14 +455,14 @@ int run_forward(pasfm_ctx* ctx, const Geo& G, const Plan& pl, const void* p0, co
   return PASFM_OK;
 }
 
-// Backward: mode 1 adjoint into vol, 2 pose gradient into G rows, 3 both.  For the sphere
-// the kernel reads the traces' first differences (its slot sums need only those), formed
-// here into the workspace.
-int run_backward(pasfm_ctx* ctx, const Geo& G, const Plan& pl, int mode, const void* p0, const double* xw,
-                 const void* gsig_in, int dtype_in, const uint8_t* mask, float* vol, double* Gout,
-                 cudaStream_t st) {
+// Backward parameter block and trace staging map of one scan (every field but the frame
+// chunk's f_begin, n_items, accumulate and part split), with the workspace it needs for
+// frame chunks of Fc frames.  For the sphere the kernel reads the traces' first
+// differences (its slot sums need only those), formed here into the workspace.
+int bwd_setup(pasfm_ctx* ctx, const Geo& G, const Plan& pl, int mode, const void* p0, const double* xw,
+              const void* gsig_in, int dtype_in, const uint8_t* mask, float* vol, int Fc, BwdParams* out,
+              CUtensorMap* map, cudaStream_t st) {
   const pasfm_geom& g = G.g;
-  const int F = g.n_frames, E = g.n_elem;
   const bool diff = pl.K == PASFM_KERNEL_SPHERE;
   const void* gsig = gsig_in;
   int dtype_sig = dtype_in, Nt = g.n_samples;
@@ -459,12 +479,10 @@ int run_backward(pasfm_ctx* ctx, const Geo& G, const Plan& pl, int mode, const v
     dtype_sig = PASFM_F32;
     Nt = Ntd;
   }
-  const bool pose = mode & 2;
-  const int Fc = pose ? frames_per_chunk(bwd_per_frame(G, pl), ctx->budget, F) : std::max(F, 1);
-  if (pose) TRY(ctx->ensure(ctx->gpart, size_t(Fc) * E * pl.ncubes * 24));
+  if (mode & 2) TRY(ctx->ensure(ctx->gpart, size_t(Fc) * g.n_elem * pl.ncubes * 24));
+  if (mode & 1) TRY(ctx->ensure(ctx->vparts, size_t(G.nvox) * 4 * kMaxParts));
 
-  CUtensorMap map;
-  std::memset(&map, 0, sizeof map);
+  std::memset(map, 0, sizeof *map);
   int use_tma = 0;
   auto enc = encode_fn();
   if (enc && dtype_sig == PASFM_F32 && Nt % 4 == 0 && aligned16(gsig) && pl.WP <= 256) {
@@ -472,7 +490,7 @@ int run_backward(pasfm_ctx* ctx, const Geo& G, const Plan& pl, int mode, const v
     cuuint64_t strides[1] = {cuuint64_t(Nt) * 4};
     cuuint32_t box[2] = {cuuint32_t(pl.WP), 1};
     cuuint32_t es[2] = {1, 1};
-    if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(gsig), dims, strides, box, es,
+    if (enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(gsig), dims, strides, box, es,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS)
       use_tma = 1;
@@ -484,6 +502,7 @@ int run_backward(pasfm_ctx* ctx, const Geo& G, const Plan& pl, int mode, const v
   P.g = gsig;
   P.mask = mask;
   P.vol = vol;
+  P.vol_parts = static_cast<float*>(ctx->vparts.p);
   P.gpart = static_cast<double*>(ctx->gpart.p);
   P.dtype_vol = g.dtype_vol;
   P.dtype_sig = dtype_sig;
@@ -492,7 +511,7 @@ int run_backward(pasfm_ctx* ctx, const Geo& G, const Plan& pl, int mode, const v
   P.nz = g.nz;
   P.ncx = pl.ncx;
   P.ncy = pl.ncy;
-  P.E = E;
+  P.E = g.n_elem;
   P.Nt = Nt;
   P.WP = pl.WP;
   P.ox = g.ox;
@@ -506,19 +525,40 @@ int run_backward(pasfm_ctx* ctx, const Geo& G, const Plan& pl, int mode, const v
   P.diff = diff ? 1 : 0;
   P.wait_cycles = ctx->wait_cycles;
   P.status = ctx->status;
-  const size_t smem = pl.C == 16 ? BwdLayout<16>::total(pl.WP) : BwdLayout<8>::total(pl.WP);
+  *out = P;
+  return PASFM_OK;
+}
+
+size_t bwd_smem(const Plan& pl) { return pl.C == 16 ? BwdLayout<16>::total(pl.WP) : BwdLayout<8>::total(pl.WP); }
+
+// Frame chunk [fb, fb + fc) of a backward: items, accumulation and the split of every
+// cube's items into parts (per_sm: resident CTAs of the single-scan kernel per SM).
+void bwd_chunk(pasfm_ctx* ctx, const Plan& pl, int E, int fb, int fc, int per_sm, BwdParams* P) {
+  P->f_begin = fb;
+  P->n_items = fc * E;
+  P->accumulate = fb > 0;
+  P->n_parts = choose_parts(pl.ncubes, P->n_items, per_sm * ctx->sms);
+  P->part_items = P->n_parts > 1 ? ((P->n_items + P->n_parts - 1) / P->n_parts + 31) / 32 * 32 : P->n_items;
+}
+
+// Backward: mode 1 adjoint into vol, 2 pose gradient into G rows, 3 both.
+int run_backward(pasfm_ctx* ctx, const Geo& G, const Plan& pl, int mode, const void* p0, const double* xw,
+                 const void* gsig_in, int dtype_in, const uint8_t* mask, float* vol, double* Gout,
+                 cudaStream_t st) {
+  const pasfm_geom& g = G.g;
+  const int F = g.n_frames, E = g.n_elem;
+  const bool pose = mode & 2;
+  const int Fc = pose ? frames_per_chunk(bwd_per_frame(G, pl), ctx->budget, F) : std::max(F, 1);
+  BwdParams P;
+  CUtensorMap map;
+  TRY(bwd_setup(ctx, G, pl, mode, p0, xw, gsig_in, dtype_in, mask, vol, Fc, &P, &map, st));
+  const size_t smem = bwd_smem(pl);
   const int per_sm = bwd_occupancy(pl.K, pl.S)(pl.C, mode, smem);
   const bool adj = mode & 1;
-  if (adj) TRY(ctx->ensure(ctx->vparts, size_t(G.nvox) * 4 * kMaxParts));
 
   for (int fb = 0; fb < F; fb += Fc) {
     const int fc = std::min(Fc, F - fb);
-    P.f_begin = fb;
-    P.n_items = fc * E;
-    P.accumulate = fb > 0;
-    P.n_parts = choose_parts(pl.ncubes, P.n_items, per_sm * ctx->sms);
-    P.part_items = P.n_parts > 1 ? ((P.n_items + P.n_parts - 1) / P.n_parts + 31) / 32 * 32 : P.n_items;
-    P.vol_parts = static_cast<float*>(ctx->vparts.p);
+    bwd_chunk(ctx, pl, E, fb, fc, per_sm, &P);
     cudaEvent_t t = ctx->begin(st);
     cudaError_t e = bwd_launcher(pl.K, pl.S)(pl.C, mode, map, P, dim3(pl.ncubes, P.n_parts), smem, st);
     ctx->end("bwd_cube", t, st);
@@ -621,6 +661,314 @@ int run_grad6(pasfm_ctx* ctx, const Geo& G, const double* xw, const double* Gm, 
   return check_launch("grad6");
 }
 
+// ---------------------------------------------------------------------------
+// Batched gradient step over several scans (pasfm_step_batch)
+// ---------------------------------------------------------------------------
+int prepare(pasfm_ctx* ctx, const pasfm_geom* geom, Geo* G, Plan* pl);
+
+// Fields of the forward parameters that every scan of one batched launch must share.
+bool same_fwd_profile(const FwdParams& a, const FwdParams& b) {
+  return a.W == b.W && a.tau0 == b.tau0 && a.inv_h == b.inv_h && a.sup == b.sup && a.h == b.h &&
+         a.supf == b.supf && a.sup2 == b.sup2 && a.nb_shift == b.nb_shift && a.p0_scale == b.p0_scale &&
+         a.inv_hf == b.inv_hf && a.cb1 == b.cb1 && std::memcmp(&a.gs, &b.gs, sizeof a.gs) == 0 &&
+         a.wait_cycles == b.wait_cycles;
+}
+
+bool same_bwd_profile(const BwdParams& a, const BwdParams& b) {
+  return a.WP == b.WP && a.tau0 == b.tau0 && a.inv_h == b.inv_h && a.sup == b.sup && a.h == b.h &&
+         a.supf == b.supf && a.sup2 == b.sup2 && a.nb_shift == b.nb_shift && a.scale == b.scale &&
+         a.inv_hf == b.inv_hf && a.cb1 == b.cb1 && a.lam == b.lam && a.diff == b.diff &&
+         std::memcmp(&a.gs, &b.gs, sizeof a.gs) == 0 && a.wait_cycles == b.wait_cycles;
+}
+
+struct BatchScan {  // one scan of a batched step
+  pasfm_ctx* ctx;
+  Geo G;
+  Plan pl;
+  pasfm_adam* state;
+  void* p0;
+  double* pose;
+  double* loss_out;
+  int mode;             // backward: 1 volume, 2 poses, 3 both, 0 none
+  int Fc, nfc;          // forward frames per chunk, chunks
+  int Fb, nbc;          // backward frames per chunk, chunks
+  int loss_off;         // loss partial blocks so far
+  int per_sm;           // resident single-scan backward CTAs per SM (part split)
+  FwdParams fp;
+  BwdParams bp;
+  CUtensorMap fmap, bmap;
+};
+
+// Scans grouped by what one batched launch needs them to share; groups of at most
+// kMaxBatch.  key(a, b) says whether scans a and b may share a launch.
+template <class Key>
+std::vector<std::vector<int>> group_scans(const std::vector<int>& idx, Key key) {
+  std::vector<std::vector<int>> groups;
+  for (int i : idx) {
+    bool placed = false;
+    for (auto& g : groups)
+      if (int(g.size()) < kMaxBatch && key(g.front(), i)) {
+        g.push_back(i);
+        placed = true;
+        break;
+      }
+    if (!placed) groups.push_back({i});
+  }
+  return groups;
+}
+
+int step_batch(int n, pasfm_ctx* const* ctxs, const pasfm_geom* geoms, void* const* p0s, double* const* poses,
+               const double* const* elems, const void* const* meas, const uint8_t* const* masks,
+               pasfm_adam* states, double* const* loss_outs, unsigned long long* trace, cudaStream_t st) {
+  if (n < 0) return fail(PASFM_EINVAL, "negative scan count");
+  if (n == 0) return PASFM_OK;
+  if (trace && n > 1024) return fail(PASFM_EINVAL, "trace_ns: at most 1024 scans");
+  if (!ctxs || !geoms || !p0s || !poses || !elems || !meas || !states)
+    return fail(PASFM_EINVAL, "NULL array argument");
+  std::vector<BatchScan> sc(n);
+  for (int i = 0; i < n; ++i) {
+    BatchScan& b = sc[i];
+    b.ctx = ctxs[i];
+    for (int k = 0; k < i; ++k)
+      if (ctxs[k] == b.ctx) return fail(PASFM_EINVAL, "scans %d and %d share a context", k, i);
+    TRY(prepare(b.ctx, &geoms[i], &b.G, &b.pl));
+    if (b.ctx->device != ctxs[0]->device) return fail(PASFM_EINVAL, "scan %d is on another device", i);
+    b.state = &states[i];
+    b.p0 = p0s[i];
+    b.pose = poses[i];
+    b.loss_out = loss_outs ? loss_outs[i] : nullptr;
+    const pasfm_adam* a = b.state;
+    if (b.G.nvox == 0 || b.G.n_rows == 0 || b.G.g.n_samples == 0)
+      return fail(PASFM_EINVAL, "scan %d: a step needs a non-empty volume, array and record", i);
+    if (!b.p0 || !b.pose || !elems[i] || !meas[i]) return fail(PASFM_EINVAL, "scan %d: NULL array argument", i);
+    const bool uv = !(a->flags & PASFM_ADAM_FREEZE_VOLUME), up = !(a->flags & PASFM_ADAM_FREEZE_POSES);
+    if ((uv && (!a->m_vol || !a->v_vol)) || (up && (!a->m_pose || !a->v_pose)))
+      return fail(PASFM_EINVAL, "scan %d: Adam moment array is NULL", i);
+    if (!(a->beta1 >= 0 && a->beta1 < 1 && a->beta2 >= 0 && a->beta2 < 1 && a->eps >= 0))
+      return fail(PASFM_EINVAL, "scan %d: Adam betas must lie in [0, 1) and eps >= 0", i);
+    b.mode = (uv ? 1 : 0) | (up ? 2 : 0);
+  }
+  TRY(set_device(ctxs[0]));
+  pasfm_ctx* lead = ctxs[0];
+
+  // workspaces, element positions, forward parameters
+  int n_counters = 0;
+  for (int i = 0; i < n; ++i) {
+    BatchScan& b = sc[i];
+    pasfm_ctx* c = b.ctx;
+    const Geo& G = b.G;
+    const int F = G.g.n_frames;
+    TRY(c->ensure(c->xw, size_t(G.n_rows) * 24));
+    TRY(c->ensure(c->gres, size_t(G.n_rows) * G.g.n_samples * 4));
+    TRY(c->ensure(c->vgrad, size_t(G.nvox) * 4));
+    TRY(c->ensure(c->G, size_t(G.n_rows) * 24));
+    TRY(c->ensure(c->grad6, size_t(F) * 48));
+    b.Fc = frames_per_chunk(fwd_per_frame(G, b.pl), c->budget, F);
+    b.nfc = (F + b.Fc - 1) / b.Fc;
+    TRY(c->ensure(c->lpart, (size_t(G.n_rows + 7) / 8 + b.nfc) * 8));
+    TRY(c->ensure(c->lscalar, 8));
+    b.Fb = (b.mode & 2) ? frames_per_chunk(bwd_per_frame(G, b.pl), c->budget, F) : std::max(F, 1);
+    b.nbc = b.mode ? (F + b.Fb - 1) / b.Fb : 0;
+    b.loss_off = 0;
+    n_counters += b.nfc + b.nbc;
+    TRY(run_elem_pos(c, G, elems[i], b.pose, static_cast<double*>(c->xw.p), st));
+    TRY(fwd_setup(c, G, b.pl, b.p0, static_cast<double*>(c->xw.p), b.Fc, &b.fp, &b.fmap));
+  }
+  // tile counters; sized generously so that later batches do not regrow the buffer
+  // (a reallocation's cudaFree would synchronise the device)
+  TRY(lead->ensure(lead->bcount, std::max<size_t>(size_t(n_counters), 4096) * sizeof(int)));
+  int* counters = static_cast<int*>(lead->bcount.p);
+  int next_counter = 0;
+  CUDA_TRY(cudaMemsetAsync(counters, 0, size_t(n_counters) * sizeof(int), st));
+  if (trace) {
+    trace_init_kernel<<<1, std::max(32, ((n + 31) / 32) * 32), 0, st>>>(trace, n);
+    TRY(check_launch("trace_init"));
+  }
+
+  std::vector<int> all(n);
+  for (int i = 0; i < n; ++i) all[i] = i;
+
+  // forward, one launch per group and frame-chunk round, then the groups' reductions
+  const auto fwd_groups = group_scans(all, [&](int a, int b) {
+    const Plan &p = sc[a].pl, &q = sc[b].pl;
+    return p.K == q.K && p.S == q.S && p.C == q.C && p.fwd_warps == q.fwd_warps &&
+           same_fwd_profile(sc[a].fp, sc[b].fp);
+  });
+  int max_fc = 0;
+  for (auto& b : sc) max_fc = std::max(max_fc, b.nfc);
+  for (int r = 0; r < max_fc; ++r) {
+    for (const auto& grp : fwd_groups) {
+      TmaBatch maps;
+      FwdBatch B;
+      std::memset(&maps, 0, sizeof maps);
+      std::memset(&B, 0, sizeof B);
+      RedBatch RB;
+      std::memset(&RB, 0, sizeof RB);
+      std::vector<int> members;
+      for (int i : grp) {
+        BatchScan& b = sc[i];
+        if (r >= b.nfc) continue;
+        const int k = B.n++;
+        const int fb = r * b.Fc, fc = std::min(b.Fc, b.G.g.n_frames - fb);
+        B.G[k] = b.fp;
+        B.G[k].f_begin = fb;
+        B.ncubes[k] = b.pl.ncubes;
+        B.fc[k] = fc;
+        B.tiles[k + 1] = B.tiles[k] + b.pl.ncubes * fc * b.pl.n_egroups;
+        maps.m[k] = b.fmap;
+        RB.R[k] = red_params(B.G[k], b.G, b.pl, fb, fc, nullptr, static_cast<float*>(b.ctx->gres.p), meas[i],
+                             masks ? masks[i] : nullptr, static_cast<double*>(b.ctx->lpart.p), b.loss_off);
+        RB.blocks[k + 1] = RB.blocks[k] + (RB.R[k].n_rows + 7) / 8;
+        RB.n = B.n;
+        b.loss_off += (RB.R[k].n_rows + 7) / 8;
+        members.push_back(i);
+      }
+      if (B.n == 0) continue;
+      const Plan& pl = sc[members[0]].pl;
+      B.Q = sc[members[0]].fp;
+      B.counter = counters + next_counter++;
+      B.trace = trace;
+      const int threads = 32 * pl.fwd_warps;
+      const size_t smem = fwd_smem(pl);
+      const int per_sm = std::max(1, fwd_batch_occupancy(pl.K, pl.S)(pl.C, threads, smem));
+      const int ctas = std::min(B.tiles[B.n], per_sm * std::max(lead->sms, 1));
+      cudaEvent_t t = lead->begin(st);
+      cudaError_t e = fwd_batch_launcher(pl.K, pl.S)(pl.C, maps, B, ctas, threads, smem, st);
+      lead->end("fwd_cube_batch", t, st);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(PASFM_ECUDA, "fwd_cube batch launch: %s", cudaGetErrorString(e));
+      }
+      t = lead->begin(st);
+      e = fwd_reduce_batch_launch(RB, pl.W, st);
+      lead->end("fwd_reduce_batch", t, st);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(PASFM_ECUDA, "fwd_reduce batch launch: %s", cudaGetErrorString(e));
+      }
+    }
+  }
+  for (auto& b : sc) {
+    double* dst = b.loss_out ? b.loss_out : static_cast<double*>(b.ctx->lscalar.p);
+    cudaEvent_t t = b.ctx->begin(st);
+    sum_kernel<<<1, 256, 0, st>>>(static_cast<double*>(b.ctx->lpart.p), b.loss_off, dst);
+    b.ctx->end("loss_sum", t, st);
+    TRY(check_launch("loss_sum"));
+  }
+
+  // backward (adjoint and / or pose gradient), one launch per group and frame-chunk round
+  std::vector<int> bwd_idx;
+  for (int i = 0; i < n; ++i) {
+    BatchScan& b = sc[i];
+    if (!b.mode) continue;
+    pasfm_ctx* c = b.ctx;
+    TRY(bwd_setup(c, b.G, b.pl, b.mode, b.p0, static_cast<double*>(c->xw.p), c->gres.p, PASFM_F32, nullptr,
+                  static_cast<float*>(c->vgrad.p), b.Fb, &b.bp, &b.bmap, st));
+    b.per_sm = bwd_occupancy(b.pl.K, b.pl.S)(b.pl.C, b.mode, bwd_smem(b.pl));
+    bwd_idx.push_back(i);
+  }
+  const auto bwd_groups = group_scans(bwd_idx, [&](int a, int b) {
+    const Plan &p = sc[a].pl, &q = sc[b].pl;
+    return p.K == q.K && p.S == q.S && p.C == q.C && sc[a].mode == sc[b].mode &&
+           same_bwd_profile(sc[a].bp, sc[b].bp);
+  });
+  int max_bc = 0;
+  for (auto& b : sc) max_bc = std::max(max_bc, b.nbc);
+  for (int r = 0; r < max_bc; ++r) {
+    for (const auto& grp : bwd_groups) {
+      TmaBatch maps;
+      BwdBatch B;
+      std::memset(&maps, 0, sizeof maps);
+      std::memset(&B, 0, sizeof B);
+      std::vector<int> members;
+      for (int i : grp) {
+        BatchScan& b = sc[i];
+        if (r >= b.nbc) continue;
+        const int k = B.n++;
+        const int fb = r * b.Fb, fc = std::min(b.Fb, b.G.g.n_frames - fb);
+        bwd_chunk(b.ctx, b.pl, b.G.g.n_elem, fb, fc, b.per_sm, &b.bp);
+        B.G[k] = b.bp;
+        B.ncubes[k] = b.pl.ncubes;
+        B.tiles[k + 1] = B.tiles[k] + b.pl.ncubes * b.bp.n_parts;
+        maps.m[k] = b.bmap;
+        members.push_back(i);
+      }
+      if (B.n == 0) continue;
+      const BatchScan& lead_scan = sc[members[0]];
+      const Plan& pl = lead_scan.pl;
+      B.Q = lead_scan.bp;
+      B.counter = counters + next_counter++;
+      B.trace = trace;
+      const size_t smem = bwd_smem(pl);
+      const int per_sm = std::max(1, bwd_batch_occupancy(pl.K, pl.S)(pl.C, lead_scan.mode, smem));
+      const int ctas = std::min(B.tiles[B.n], per_sm * std::max(lead->sms, 1));
+      cudaEvent_t t = lead->begin(st);
+      cudaError_t e = bwd_batch_launcher(pl.K, pl.S)(pl.C, lead_scan.mode, maps, B, ctas, smem, st);
+      lead->end("bwd_cube_batch", t, st);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(PASFM_ECUDA, "bwd_cube batch launch: %s", cudaGetErrorString(e));
+      }
+      for (int i : members) {  // per scan: part sums into the volume gradient, element gradients
+        BatchScan& b = sc[i];
+        pasfm_ctx* c = b.ctx;
+        const BwdParams& P = b.bp;
+        const int fc = P.n_items / b.G.g.n_elem;
+        if ((b.mode & 1) && P.n_parts > 1) {
+          const int64_t nv = b.G.nvox;
+          const unsigned blocks = static_cast<unsigned>(std::min<int64_t>((nv + 255) / 256, 148 * 16));
+          t = c->begin(st);
+          sum_parts_kernel<<<blocks, 256, 0, st>>>(P.vol_parts, P.n_parts, nv, P.vol, P.accumulate);
+          c->end("sum_parts", t, st);
+          TRY(check_launch("sum_parts"));
+        }
+        if (b.mode & 2) {
+          const int rows = fc * b.G.g.n_elem;
+          t = c->begin(st);
+          pose_rows_kernel<<<(rows + 7) / 8, 256, 0, st>>>(P.gpart, b.pl.ncubes, rows,
+                                                           int64_t(P.f_begin) * b.G.g.n_elem,
+                                                           static_cast<double*>(c->G.p));
+          c->end("pose_rows", t, st);
+          TRY(check_launch("pose_rows"));
+        }
+      }
+    }
+  }
+
+  // Adam on each scan's poses and volume
+  for (auto& b : sc) {
+    pasfm_ctx* c = b.ctx;
+    pasfm_adam* a = b.state;
+    const int64_t k = a->step + 1;
+    if (b.mode) {
+      const double bc1 = 1.0 - std::pow(a->beta1, double(k));
+      const double bc2 = 1.0 - std::pow(a->beta2, double(k));
+      if (b.mode & 2) {
+        TRY(run_grad6(c, b.G, static_cast<double*>(c->xw.p), static_cast<double*>(c->G.p),
+                      static_cast<double*>(c->grad6.p), st));
+        cudaEvent_t t = c->begin(st);
+        adam_pose_kernel<<<(b.G.g.n_frames + 63) / 64, 64, 0, st>>>(
+            b.pose, static_cast<double*>(c->grad6.p), a->m_pose, a->v_pose, b.G.g.n_frames, a->beta1, a->beta2,
+            bc1, bc2, a->lr_rot, a->lr_trans, a->eps, (a->flags & PASFM_ADAM_FIX_FRAME0) ? 1 : 0, 0);
+        c->end("adam_pose", t, st);
+        TRY(check_launch("adam_pose"));
+      }
+      if (b.mode & 1) {
+        cudaEvent_t t = c->begin(st);
+        adam_vol_kernel<<<static_cast<unsigned>((b.G.nvox + 255) / 256), 256, 0, st>>>(
+            b.p0, b.G.g.dtype_vol, static_cast<float*>(c->vgrad.p), a->m_vol, a->v_vol, b.G.nvox,
+            static_cast<float>(a->beta1), static_cast<float>(a->beta2), static_cast<float>(a->lr_vol / bc1),
+            static_cast<float>(1.0 / std::sqrt(bc2)), static_cast<float>(a->eps),
+            (a->flags & PASFM_ADAM_NONNEG) ? 1 : 0);
+        c->end("adam_vol", t, st);
+        TRY(check_launch("adam_vol"));
+      }
+    }
+    a->step = k;
+  }
+  return PASFM_OK;
+}
+
 int prepare(pasfm_ctx* ctx, const pasfm_geom* geom, Geo* G, Plan* pl) {
   if (!ctx) return fail(PASFM_EINVAL, "ctx is NULL");
   TRY(check_geom(geom, G));
@@ -666,7 +1014,8 @@ int pasfm_destroy(pasfm_ctx* ctx) {
   if (!ctx) return PASFM_OK;
   cudaSetDevice(ctx->device);
   for (Buf* b : {&ctx->xw, &ctx->part, &ctx->n0, &ctx->gres, &ctx->vgrad, &ctx->gpart, &ctx->G, &ctx->grad6,
-                 &ctx->lpart, &ctx->lscalar, &ctx->taps, &ctx->vparts, &ctx->gw, &ctx->tpart, &ctx->gdiff})
+                 &ctx->lpart, &ctx->lscalar, &ctx->taps, &ctx->vparts, &ctx->gw, &ctx->tpart, &ctx->gdiff,
+                 &ctx->bcount})
     if (b->p) cudaFree(b->p);
   for (auto& r : ctx->recs) {
     cudaEventDestroy(r.a);
@@ -944,6 +1293,13 @@ int pasfm_step_tgv(pasfm_ctx* ctx, const pasfm_geom* geom, void* p0, double* pos
   }
   state->step = k;
   return PASFM_OK;
+}
+
+int pasfm_step_batch(int n, pasfm_ctx* const* ctxs, const pasfm_geom* geoms, void* const* p0, double* const* pose,
+                     const double* const* elem, const void* const* meas, const uint8_t* const* mask,
+                     pasfm_adam* states, double* const* loss_out, uint64_t* trace_ns, void* stream) {
+  return step_batch(n, ctxs, geoms, p0, pose, elem, meas, mask, states, loss_out,
+                    reinterpret_cast<unsigned long long*>(trace_ns), static_cast<cudaStream_t>(stream));
 }
 
 int pasfm_apply_twists(pasfm_ctx* ctx, int n_frames, const double* pose, const double* xi, double* pose_out,

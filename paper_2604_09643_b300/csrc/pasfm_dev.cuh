@@ -127,8 +127,62 @@ struct BwdParams {
 };
 
 // ---------------------------------------------------------------------------
+// Batched launches: several scans that share one kernel instantiation and pulse
+// profile in one persistent launch (the serving loop's step over resident scans).
+// The per-scan blocks travel as kernel parameters (constant bank, at most 32 KB).
+// ---------------------------------------------------------------------------
+constexpr int kMaxBatch = 16;  // scans per batched launch
+
+struct TmaBatch {
+  CUtensorMap m[kMaxBatch];  // each scan's staging map (p0 cubes, or trace windows)
+};
+
+struct FwdBatch {
+  FwdParams Q;               // what the scans share: W, the pulse profile, sampling, wait bound
+  FwdParams G[kMaxBatch];    // each scan's own grid, frames, arrays and status word
+  int tiles[kMaxBatch + 1];  // scan s owns tiles [tiles[s], tiles[s + 1])
+  int ncubes[kMaxBatch];     // cubes of scan s
+  int fc[kMaxBatch];         // frames of scan s in this launch's chunk
+  int n;                     // scans in the launch
+  int* counter;              // next tile to take (zero before the launch)
+  unsigned long long* trace; // [scan][2]: first tile start, last tile end (globaltimer ns), or null
+};
+
+struct BwdBatch {
+  BwdParams Q;               // what the scans share: WP, the pulse profile, sampling, wait bound
+  BwdParams G[kMaxBatch];    // each scan's own grid, items, arrays, part split and status word
+  int tiles[kMaxBatch + 1];
+  int ncubes[kMaxBatch];
+  int n;
+  int* counter;
+  unsigned long long* trace;
+};
+
+// kernel parameters are limited to 32764 bytes
+static_assert(sizeof(TmaBatch) + sizeof(FwdBatch) <= 32764, "batched forward parameters too large");
+static_assert(sizeof(TmaBatch) + sizeof(BwdBatch) <= 32764, "batched backward parameters too large");
+
+struct RedBatch {
+  RedParams R[kMaxBatch];    // each scan's rows of this chunk (W shared)
+  int blocks[kMaxBatch + 1]; // scan s owns row blocks [blocks[s], blocks[s + 1])
+  int n;
+};
+
+// ---------------------------------------------------------------------------
 // PTX wrappers
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long globaltimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Widen scan s's [first start, last end] interval by one tile that started at t0.
+__device__ __forceinline__ void trace_tile(unsigned long long* trace, int s, unsigned long long t0) {
+  atomicMin(&trace[2 * s], t0);
+  atomicMax(&trace[2 * s + 1], globaltimer());
+}
+
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }

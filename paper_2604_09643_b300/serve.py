@@ -6,19 +6,28 @@ the joint volume + pose reconstruction.  The server:
 * admits a waiting request when its device footprint fits the free HBM (minus a
   reserve), refuses with a status one that could never fit or that does not fit
   while no scan is running, and otherwise keeps it queued until running scans
-  finish and release memory (their cached blocks are returned to the driver);
+  finish and release memory (cached blocks are returned to the driver when a
+  request waits for memory);
 * keeps every admitted scan resident: its volume, poses, measurements, Adam
-  state and a private library context (workspace) on its own CUDA stream;
-* each iteration keeps up to ``inflight`` steps enqueued per scan, so kernels
-  of different scans overlap on the device, and admits new arrivals between
-  iterations (continuous batching rather than a queue drained one by one);
-* times every step with CUDA events on the scan's stream, records queue wait,
-  and reports p50/p99 step latency and aggregate steps/s;
+  state and a private library context (workspace);
+* runs iterations: each is ONE batched gradient step over every resident scan that
+  still owes steps (pasfm_step_batch), in which the scans sharing a kernel
+  instantiation run their forward, reduction and fused adjoint / pose gradient as
+  one persistent launch per phase, so their work overlaps on the device; up to
+  ``inflight`` iterations are enqueued at a time, and arrivals join at the next
+  iteration (continuous batching rather than a queue drained one by one);
+* times every iteration with CUDA events (a scan's step latency is the duration
+  of the iteration that carried it), records queue wait, and reports p50/p99 step
+  latency and aggregate steps/s;
 * isolates failures: a scan whose loss turns non-finite or whose device status
   word is set is stopped and released while the others continue.
 
-All scans use deterministic kernels with private workspaces, so a scan's result
-does not depend on what else is running.
+``mode="streams"`` keeps the earlier scheduling for comparison: each scan steps
+with its own pasfm_step calls on its own stream, ``inflight`` steps enqueued per
+scan, and the device interleaves the scans' kernels.
+
+A scan's tiles are the same in every batch, and every scan has private workspaces,
+so its result does not depend on what else is running (bit-identical).
 """
 from __future__ import annotations
 
@@ -109,10 +118,10 @@ def request_from_spec(spec: dict, context, *, steps=4, spacing_mm=0.1, standoff_
 
 
 class _Scan:
-    def __init__(self, req: Request, device, now):
+    def __init__(self, req: Request, device, now, stream=None):
         self.req = req
         self.ctx = binding.Context(device)
-        self.stream = torch.cuda.Stream(device)
+        self.stream = stream if stream is not None else torch.cuda.Stream(device)
         self.admitted_s = now
         d = self.ctx.device
         with torch.cuda.stream(self.stream):
@@ -128,7 +137,7 @@ class _Scan:
             self.loss = torch.zeros((), dtype=torch.float64, device=d)
         self.ctx.reserve(req.geom)
         self.issued = 0
-        self.events = deque()   # (start, end) per issued step, oldest first
+        self.events = deque()   # (start, end) per step still running, oldest first
         self.step_ms = []
         self.failed = None
 
@@ -149,9 +158,13 @@ class _Scan:
     def done(self):
         return self.issued >= self.req.steps and not self.events
 
-    def finish(self, now, wait_s):
-        self.stream.synchronize()
-        rc, bits = self.ctx.status(self.stream)
+    def finish(self, now, wait_s, shared_stream=False):
+        # every step's end event has completed (done()); on a stream shared with other
+        # scans' later iterations, read the status on the current stream instead of
+        # waiting for those
+        if not shared_stream:
+            self.stream.synchronize()
+        rc, bits = self.ctx.status(None if shared_stream else self.stream)
         loss = float(self.loss.item())
         status = "ok"
         if rc != 0:
@@ -170,21 +183,40 @@ class _Scan:
         self.p0 = self.poses = self.elem = self.meas = self.adam = self.loss = None
 
 
+def issue_iteration(scans, stream):
+    """One batched gradient step over `scans` on `stream`: every scan's step is timed by
+    the iteration's events (shared), and its pending-event queue gets them."""
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.record(stream)
+    binding.step_batch([x.ctx for x in scans], [x.req.geom for x in scans], [x.p0 for x in scans],
+                       [x.poses for x in scans], [x.elem for x in scans], [x.meas for x in scans],
+                       [x.adam for x in scans], loss_outs=[x.loss for x in scans], stream=stream)
+    e.record(stream)
+    for x in scans:
+        x.events.append((s, e))
+        x.issued += 1
+
+
 class Server:
     """Admit, run and retire reconstruction requests on one GPU."""
 
     def __init__(self, device=0, reserve_bytes=2 << 30, max_active=16, inflight=2, mem_info=None,
-                 clock=time.perf_counter):
+                 clock=time.perf_counter, mode="batched"):
+        if mode not in ("batched", "streams"):
+            raise ValueError("mode must be 'batched' or 'streams'")
         self.device = torch.device("cuda", device) if isinstance(device, int) else device
         self.reserve = reserve_bytes
         self.max_active = max_active
         self.inflight = inflight
+        self.mode = mode
         self.mem_info = mem_info or (lambda: torch.cuda.mem_get_info(self.device))
         self.clock = clock
         self.queue = deque()
         self.active = []
         self.results = []
+        self.iterations = 0
         self.t0 = None
+        self._stream = None
 
     def submit(self, req: Request):
         self.queue.append(req)
@@ -205,6 +237,12 @@ class Server:
                 self.results.append(Result(req.id, f"rejected: needs {need} bytes, device has {total}", 0,
                                            None, None, float("nan"), self._now() - req.arrival_s, []))
                 continue
+            if dec == WAIT and torch.cuda.memory_reserved(self.device) > torch.cuda.memory_allocated(self.device):
+                # retired scans' blocks may still sit in the caching allocator: hand them back
+                # to the driver (this synchronises, so only when a request is waiting for memory)
+                torch.cuda.empty_cache()
+                free, total = self.mem_info()
+                dec = admission(need, free, total, self.reserve)
             if dec == WAIT:
                 if not self.active:
                     # nothing running will free memory for it: waiting could last forever
@@ -215,28 +253,43 @@ class Server:
                     continue
                 return
             self.queue.popleft()
-            self.active.append((_Scan(req, self.device, self._now()), self._now() - req.arrival_s))
+            if self.mode == "batched" and self._stream is None:
+                self._stream = torch.cuda.Stream(self.device)
+            stream = self._stream if self.mode == "batched" else None
+            self.active.append((_Scan(req, self.device, self._now(), stream), self._now() - req.arrival_s))
+
+    def _issue(self):
+        if self.mode == "streams":
+            for scan, _ in self.active:
+                scan.poll()
+                while scan.issued < scan.req.steps and len(scan.events) < self.inflight:
+                    scan.issue()
+            return
+        # batched: keep up to `inflight` iterations enqueued; an iteration takes every
+        # resident scan that still owes a step and has fewer than `inflight` in flight
+        while True:
+            for scan, _ in self.active:
+                scan.poll()
+            due = [scan for scan, _ in self.active
+                   if scan.issued < scan.req.steps and len(scan.events) < self.inflight]
+            if not due:
+                return
+            issue_iteration(due, self._stream)
+            self.iterations += 1
 
     def run(self, max_seconds=None):
         """Serve until the queue and the active set are empty (or max_seconds)."""
         self.t0 = self.clock()
         while self.queue or self.active:
             self._admit()
-            for scan, _ in self.active:
-                scan.poll()
-                while scan.issued < scan.req.steps and len(scan.events) < self.inflight:
-                    scan.issue()
+            self._issue()
             keep = []
             for scan, wait in self.active:
                 scan.poll()
                 if scan.done():
-                    self.results.append(scan.finish(self._now(), wait))
+                    self.results.append(scan.finish(self._now(), wait, shared_stream=self.mode == "batched"))
                 else:
                     keep.append((scan, wait))
-            if len(keep) < len(self.active):
-                # hand the retired scans' blocks back to the driver, whose free-memory
-                # figure the admission reads (the caching allocator would keep them)
-                torch.cuda.empty_cache()
             self.active = keep
             if not self.active and self.queue:
                 delay = self.queue[0].arrival_s - self._now()
@@ -255,7 +308,8 @@ class Server:
         wall = max((r.finished_s for r in ok), default=0.0)
         steps = sum(r.steps for r in ok)
         pct = lambda v, q: float(np.percentile(v, q)) if v else None
-        return {"requests": len(self.results), "completed": len(ok),
+        return {"mode": self.mode, "iterations": self.iterations if self.mode == "batched" else None,
+                "requests": len(self.results), "completed": len(ok),
                 "rejected": sum(r.status.startswith("rejected") for r in self.results),
                 "failed": sum(r.status.startswith("failed") for r in self.results),
                 "steps": steps, "wall_s": wall, "steps_per_s": steps / wall if wall > 0 else None,

@@ -30,16 +30,20 @@ def _requests():
             _request(2, 40, 4, 8, 1024, 0.05), _request(3, 24, 8, 3, 512, 0.1)]
 
 
-def test_results_are_identical_alone_and_in_the_mix(cuda_device):
+@pytest.mark.parametrize("mode", ["batched", "streams"])
+def test_results_are_identical_alone_and_in_the_mix(cuda_device, mode):
+    """Four scans of different sizes and arrays, arriving while others run: each result
+    is bit-identical to the same request served alone (batched iterations: the scans
+    share launches; streams: the scans' own launches interleave on the device)."""
     reqs = _requests()
     alone = {}
     for r in reqs:
-        srv = serve.Server(device=0)
+        srv = serve.Server(device=0, mode=mode)
         srv.submit(r)
         res = srv.run()
         assert res[0].status == "ok"
         alone[r.id] = res[0]
-    srv = serve.Server(device=0, inflight=2)
+    srv = serve.Server(device=0, inflight=2, mode=mode)
     for r in reqs:
         srv.submit(r)
     mixed = {r.id: r for r in srv.run()}
@@ -52,9 +56,10 @@ def test_results_are_identical_alone_and_in_the_mix(cuda_device):
     assert rep["completed"] == 4 and rep["step_ms_p50"] > 0 and rep["step_ms_p99"] >= rep["step_ms_p50"]
 
 
-def test_failing_scan_is_isolated(cuda_device):
+@pytest.mark.parametrize("mode", ["batched", "streams"])
+def test_failing_scan_is_isolated(cuda_device, mode):
     reqs = _requests()[:2] + [_request(9, 32, 8, 4, 512, 0.0, poison=True)]
-    srv = serve.Server(device=0)
+    srv = serve.Server(device=0, mode=mode)
     for r in reqs:
         srv.submit(r)
     res = {r.id: r for r in srv.run()}
