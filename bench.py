@@ -108,6 +108,20 @@ def kernel_src_hash(kernel="bwd_cube"):
     return h.hexdigest()[:16]
 
 
+def pipes_for(kernel):
+    """Executed pipe figures (ncu) of `kernel` from the committed summaries, if taken on
+    these sources."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "pipes.json")) as fh:
+            t = json.load(fh)
+    except (OSError, ValueError):
+        return None
+    e = t.get(kernel)
+    if not e or e.get("src_sha") != kernel_src_hash(kernel):
+        return None
+    return {k: v for k, v in e.items() if k != "src_sha"}
+
+
 def traffic_for(kernel):
     """DRAM bytes per launch from the committed ncu summary, if taken on these sources."""
     try:
@@ -426,9 +440,12 @@ def run_native(args):
                     "peak_source": f"FP32 148 SM x 128 lanes x 2 flops x {pk['sm_max_mhz']:.0f} MHz "
                                    f"({pk['source']} clock)",
                     "flops_per_pair": fpp, "pairs_per_launch": pairs / launches_per_step,
-                    "note": "flops_per_pair is the frozen algorithmic count; the kernels' rewritten "
-                            "slot sums execute fewer FP32 operations, so frac can pass 1.0; the "
-                            "measured FMA-pipe occupancy (ncu) is in the profile summaries"}
+                    "executed": pipes_for(dom + ("_gauss" if gauss else "")),
+                    "note": "achieved and frac count the frozen algorithmic flops per pair; the kernels' "
+                            "rewritten slot sums execute fewer FP32 operations, so frac can pass 1.0 and "
+                            "does not place the kernel on its roofline: `executed` does (ncu, same "
+                            "sources): the share of cycles the FMA pipe is busy, with issue and warp "
+                            "occupancy"}
     step_flops = pairs * (f_fwd(m) + f_adj(m) + f_pose(m))
     # achieved DRAM bandwidth of the kernels whose per-launch traffic ncu measured on these sources
     hbm = {}
@@ -470,6 +487,10 @@ def run_native(args):
     # context for the derived roofline peak
     out["fp32_probe_tflops"] = {"ffma": binding.fp32_probe(local, packed=False),
                                 "ffma2": binding.fp32_probe(local, packed=True)}
+    # packed half-precision FMA rates (half2, bfloat162): what half-precision slot arithmetic
+    # could gain over the packed FP32 the kernels use
+    out["half_probe_tflops"] = {"hfma2_f16": binding.fp32_probe(local, packed=2),
+                                "hfma2_bf16": binding.fp32_probe(local, packed=3)}
     # and the shared-memory read-modify-write rate of the forward's window pattern, the
     # forward's own roofline: algorithmic shared bytes = read + write of its window slots
     # (S - 1 per pair for S >= 3, 2 for S = 2; 4 bytes each way)
@@ -481,7 +502,8 @@ def run_native(args):
         tbs = pairs * bpp / launches_f / (per_kernel["fwd_cube"]["ms_avg"] * 1e-3) / 1e12
         out["roofline_fwd"] = {"bound": "smem", "kernel": "fwd_cube", "achieved": tbs, "peak": smem_tbs,
                                "unit": "TB/s", "frac": tbs / smem_tbs, "bytes_per_pair": bpp,
-                               "peak_source": "measured: pasfm_smem_probe"}
+                               "peak_source": "measured: pasfm_smem_probe",
+                               "executed": pipes_for("fwd_cube" + ("_gauss" if gauss else ""))}
     if rank == 0:
         print(json.dumps(out))
     ctx.close()

@@ -308,9 +308,11 @@ int pasfm_nc_grad(pasfm_ctx* ctx, int64_t n_rows, int n_samples, const float* si
  * Gaussian width or the grid spacing changes).  Device memory. */
 int pasfm_scale(pasfm_ctx* ctx, int64_t n, double alpha, float* x, void* stream);
 
-/* Measurement aid, no counterpart in the paper -- FP32 FMA throughput of `device`
- * in TFLOP/s (an FMA counts 2 flops): independent FMA chains on every SM, scalar
- * (packed = 0) or Blackwell's packed two-wide FMA on float2 (packed = 1).  Allocates
+/* Measurement aid, no counterpart in the paper -- FMA throughput of `device` in
+ * TFLOP/s (an FMA counts 2 flops): independent FMA chains on every SM, scalar FP32
+ * (packed = 0), Blackwell's packed two-wide FP32 FMA on float2 (packed = 1), or the
+ * packed half-precision FMA on half2 (packed = 2) or bfloat162 (packed = 3); other
+ * values return PASFM_EINVAL.  Allocates
  * and frees 4 bytes of device memory, runs on the default stream and synchronises,
  * about 10 ms; not for use while other work runs on the device.  tflops_out: host. */
 int pasfm_fp32_probe(int device, int packed, double* tflops_out);

@@ -248,9 +248,11 @@ def pasfm_pose_grad_noalloc(geom, p0, elem, pose, g_sig, mask, grad6_out, gelem_
 
 
 def fp32_probe(device=0, packed=False):
-    """Measured FP32 FMA throughput of the device in TFLOP/s (scalar or packed two-wide FMA)."""
+    """Measured FMA throughput of the device in TFLOP/s: scalar FP32 (packed False / 0),
+    packed two-wide FP32 (True / 1), packed half2 (2) or bfloat162 (3)."""
     v = ctypes.c_double()
-    _check(lib().pasfm_fp32_probe(int(device), int(bool(packed)), ctypes.byref(v)))
+    mode = int(packed) if not isinstance(packed, bool) else int(packed)
+    _check(lib().pasfm_fp32_probe(int(device), mode, ctypes.byref(v)))
     return v.value
 
 

@@ -515,12 +515,15 @@ __global__ void __launch_bounds__(256) diff_rows_kernel(const void* __restrict__
 // rounds (a multiple of 16; PACKED: two-wide packed FMAs on float2 chains).  The chains converge to
 // c / (1 - m); their sum is stored only if it equals an impossible value, so no chain
 // can be dropped and the kernel touches no memory.
-template <bool PACKED>
+// Independent FMA chains on every lane.  MODE 0: scalar FP32 (fmaf); 1: packed FP32
+// (two FMAs per lane per instruction, __ffma2_rn on float2); 2: packed FP16 (__hfma2 on
+// half2); 3: packed BF16 (__hfma2 on bfloat162).
+template <int MODE>
 __global__ void __launch_bounds__(256) fp32_probe_kernel(float* out, int iters, float m, float c) {
   constexpr int kProbeChains = 8;
   const float seed = 1e-3f * static_cast<float>(threadIdx.x);
   float s = 0.f;
-  if constexpr (PACKED) {
+  if constexpr (MODE == 1) {
     float2 a[kProbeChains];
 #pragma unroll
     for (int k = 0; k < kProbeChains; ++k) a[k] = make_float2(seed + k, seed - k);
@@ -532,6 +535,30 @@ __global__ void __launch_bounds__(256) fp32_probe_kernel(float* out, int iters, 
     }
 #pragma unroll
     for (int k = 0; k < kProbeChains; ++k) s += a[k].x + a[k].y;
+  } else if constexpr (MODE == 2) {
+    __half2 a[kProbeChains];
+#pragma unroll
+    for (int k = 0; k < kProbeChains; ++k) a[k] = __floats2half2_rn(seed + 0.01f * k, seed - 0.01f * k);
+    const __half2 m2 = __float2half2_rn(m), c2 = __float2half2_rn(c);
+#pragma unroll 16
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+      for (int k = 0; k < kProbeChains; ++k) a[k] = __hfma2(a[k], m2, c2);
+    }
+#pragma unroll
+    for (int k = 0; k < kProbeChains; ++k) s += __low2float(a[k]) + __high2float(a[k]);
+  } else if constexpr (MODE == 3) {
+    __nv_bfloat162 a[kProbeChains];
+#pragma unroll
+    for (int k = 0; k < kProbeChains; ++k) a[k] = __floats2bfloat162_rn(seed + 0.01f * k, seed - 0.01f * k);
+    const __nv_bfloat162 m2 = __float2bfloat162_rn(m), c2 = __float2bfloat162_rn(c);
+#pragma unroll 16
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+      for (int k = 0; k < kProbeChains; ++k) a[k] = __hfma2(a[k], m2, c2);
+    }
+#pragma unroll
+    for (int k = 0; k < kProbeChains; ++k) s += __low2float(a[k]) + __high2float(a[k]);
   } else {
     float a[kProbeChains];
 #pragma unroll
@@ -588,15 +615,18 @@ cudaError_t smem_probe_launch(int blocks, int iters, float* out, cudaStream_t st
   return cudaGetLastError();
 }
 
-double fp32_probe_flops(int blocks, int iters, bool packed) {
-  return double(blocks) * 256.0 * iters * 8 * 2 * (packed ? 2 : 1);
+double fp32_probe_flops(int blocks, int iters, int mode) {
+  return double(blocks) * 256.0 * iters * 8 * 2 * (mode == 0 ? 1 : 2);
 }
 
-cudaError_t fp32_probe_launch(bool packed, int blocks, int iters, float* out, cudaStream_t st) {
-  if (packed)
-    fp32_probe_kernel<true><<<blocks, 256, 0, st>>>(out, iters, 0.9999f, 1e-4f);
-  else
-    fp32_probe_kernel<false><<<blocks, 256, 0, st>>>(out, iters, 0.9999f, 1e-4f);
+cudaError_t fp32_probe_launch(int mode, int blocks, int iters, float* out, cudaStream_t st) {
+  switch (mode) {
+    case 0: fp32_probe_kernel<0><<<blocks, 256, 0, st>>>(out, iters, 0.9999f, 1e-4f); break;
+    case 1: fp32_probe_kernel<1><<<blocks, 256, 0, st>>>(out, iters, 0.9999f, 1e-4f); break;
+    case 2: fp32_probe_kernel<2><<<blocks, 256, 0, st>>>(out, iters, 0.9999f, 1e-4f); break;
+    case 3: fp32_probe_kernel<3><<<blocks, 256, 0, st>>>(out, iters, 0.9999f, 1e-4f); break;
+    default: return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 

@@ -48,8 +48,8 @@ __global__ void scale_kernel(float* x, int64_t n, float alpha);
 // outside [0, Nt)
 __global__ void diff_rows_kernel(const void* g, int dtype, int64_t rows, int Nt, int Ntd, float* D);
 // FP32 throughput probe (fp32_probe_kernel): flops per launch and the launch itself
-double fp32_probe_flops(int blocks, int iters, bool packed);
-cudaError_t fp32_probe_launch(bool packed, int blocks, int iters, float* out, cudaStream_t st);
+double fp32_probe_flops(int blocks, int iters, int mode);
+cudaError_t fp32_probe_launch(int mode, int blocks, int iters, float* out, cudaStream_t st);
 // shared-memory read-modify-write probe (smem_probe_kernel): bytes per launch and the launch
 double smem_probe_bytes(int blocks, int iters);
 cudaError_t smem_probe_launch(int blocks, int iters, float* out, cudaStream_t st);

@@ -1437,6 +1437,7 @@ int pasfm_scale(pasfm_ctx* ctx, int64_t n, double alpha, float* x, void* stream)
 
 int pasfm_fp32_probe(int device, int packed, double* tflops_out) {
   if (!tflops_out) return fail(PASFM_EINVAL, "NULL output");
+  if (packed < 0 || packed > 3) return fail(PASFM_EINVAL, "probe mode %d is not 0..3", packed);
   CUDA_TRY(cudaSetDevice(device));
   int sms = 0;
   CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
@@ -1446,9 +1447,9 @@ int pasfm_fp32_probe(int device, int packed, double* tflops_out) {
   cudaEvent_t a = nullptr, b = nullptr;
   cudaError_t e = cudaEventCreate(&a);
   if (e == cudaSuccess) e = cudaEventCreate(&b);
-  if (e == cudaSuccess) e = fp32_probe_launch(packed != 0, blocks, iters, out, nullptr);  // warm-up
+  if (e == cudaSuccess) e = fp32_probe_launch(packed, blocks, iters, out, nullptr);  // warm-up
   if (e == cudaSuccess) e = cudaEventRecord(a, nullptr);
-  for (int r = 0; e == cudaSuccess && r < reps; ++r) e = fp32_probe_launch(packed != 0, blocks, iters, out, nullptr);
+  for (int r = 0; e == cudaSuccess && r < reps; ++r) e = fp32_probe_launch(packed, blocks, iters, out, nullptr);
   if (e == cudaSuccess) e = cudaEventRecord(b, nullptr);
   if (e == cudaSuccess) e = cudaEventSynchronize(b);
   float ms = 0.f;
@@ -1457,7 +1458,7 @@ int pasfm_fp32_probe(int device, int packed, double* tflops_out) {
   if (b) cudaEventDestroy(b);
   cudaFree(out);
   if (e != cudaSuccess) return fail(PASFM_ECUDA, "fp32 probe: %s", cudaGetErrorString(e));
-  *tflops_out = reps * fp32_probe_flops(blocks, iters, packed != 0) / (ms * 1e-3) / 1e12;
+  *tflops_out = reps * fp32_probe_flops(blocks, iters, packed) / (ms * 1e-3) / 1e12;
   return PASFM_OK;
 }
 

@@ -403,6 +403,11 @@ def test_fp32_probe_is_plausible(ctx):
     for packed in (False, True):
         tf = binding.fp32_probe(0, packed=packed)
         assert 5.0 < tf < 200.0, (packed, tf)
+    for mode in (2, 3):  # packed half2 and bfloat162 FMAs
+        tf = binding.fp32_probe(0, packed=mode)
+        assert 5.0 < tf < 400.0, (mode, tf)
+    with pytest.raises(binding.PasfmError):
+        binding.fp32_probe(0, packed=4)
 
 
 def test_smem_probe_is_plausible(ctx):
