@@ -52,6 +52,11 @@ def admission(footprint, free, total, reserve):
     return ADMIT
 
 
+def step_pairs(geom):
+    """Voxel-element pairs one gradient step of a scan processes (its share of an iteration)."""
+    return int(geom["nx"]) * int(geom["ny"]) * int(geom["nz"]) * int(geom["n_elem"]) * int(geom["n_frames"])
+
+
 def footprint_bytes(geom):
     """Device bytes a resident scan needs: library workspace plus its arrays."""
     import ctypes
@@ -201,9 +206,14 @@ class Server:
     """Admit, run and retire reconstruction requests on one GPU."""
 
     def __init__(self, device=0, reserve_bytes=2 << 30, max_active=16, inflight=2, mem_info=None,
-                 clock=time.perf_counter, mode="batched"):
+                 clock=time.perf_counter, mode="batched", max_iteration_pairs=None):
+        """max_iteration_pairs: optional cap on the voxel-element pairs of one iteration (the
+        resident scans' steps together): a request that would take the iteration past it
+        waits, unless nothing is running.  It bounds the step latency (an iteration's
+        duration) at the cost of queue wait; None admits up to max_active scans."""
         if mode not in ("batched", "streams"):
             raise ValueError("mode must be 'batched' or 'streams'")
+        self.max_iteration_pairs = max_iteration_pairs
         self.device = torch.device("cuda", device) if isinstance(device, int) else device
         self.reserve = reserve_bytes
         self.max_active = max_active
@@ -229,6 +239,10 @@ class Server:
             req = self.queue[0]
             if req.arrival_s > self._now():
                 return
+            if (self.max_iteration_pairs is not None and self.active and
+                    sum(step_pairs(x.req.geom) for x, _ in self.active) + step_pairs(req.geom)
+                    > self.max_iteration_pairs):
+                return  # the iteration is full: wait for a resident scan to finish
             free, total = self.mem_info()
             need = footprint_bytes(req.geom)
             dec = admission(need, free, total, self.reserve)

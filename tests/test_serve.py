@@ -40,3 +40,30 @@ def test_request_that_does_not_fit_with_nothing_running_is_refused():
     res = srv.run()
     assert len(res) == 1 and res[0].status.startswith("rejected") and "no scan running" in res[0].status
     assert not srv.queue
+
+
+def test_iteration_work_cap_holds_requests_until_the_iteration_has_room(monkeypatch):
+    """With max_iteration_pairs, a request that would take the resident scans' pairs per
+    step past the cap waits (FIFO) while others run; with nothing running it is admitted
+    whatever its size.  Host logic only: scans are stand-ins."""
+    GB = 1 << 30
+    admitted = []
+
+    class FakeScan:
+        def __init__(self, req, device, now, stream=None):
+            self.req = req
+            admitted.append(req.id)
+
+    monkeypatch.setattr(serve, "_Scan", FakeScan)
+    srv = serve.Server(device=0, reserve_bytes=0, mem_info=lambda: (100 * GB, 100 * GB),
+                       max_iteration_pairs=2 * serve.step_pairs(_req(0).geom))
+    srv._stream = object()  # no device stream needed for admission
+    srv.t0 = srv.clock()
+    for i in range(4):
+        srv.submit(_req(i))
+    srv._admit()
+    assert admitted == [0, 1] and [r.id for r in srv.queue] == [2, 3]
+    srv.active = []          # the resident scans finished
+    srv.max_iteration_pairs = 1   # smaller than any scan: admitted only into an empty iteration
+    srv._admit()
+    assert admitted == [0, 1, 2] and [r.id for r in srv.queue] == [3]
