@@ -537,7 +537,8 @@ def run_serving(args):
     srv = serve.Server(device=0, mode=args.serve_mode)
     srv.submit(warm)
     srv.run()
-    srv = serve.Server(device=0, mode=args.serve_mode, max_iteration_pairs=args.serve_max_pairs)
+    srv = serve.Server(device=0, mode=args.serve_mode, max_iteration_pairs=args.serve_max_pairs,
+                       iteration_pairs=args.serve_iteration_pairs)
     for r in reqs:
         srv.submit(r)
     with ClockSampler(0) as clk:
@@ -553,6 +554,7 @@ def run_serving(args):
            "data": "synthetic",
            "config": {"workload": WORKLOAD_SERVING, "requests": len(specs), "steps_per_request": args.serve_steps,
                       "scheduling": args.serve_mode, "max_iteration_pairs": args.serve_max_pairs,
+                      "iteration_pairs": args.serve_iteration_pairs,
                       "arrivals": "seeded Poisson stream, mean 4 scans/s, first requests in arrival order",
                       "l2": "inputs larger than L2 (each scan's measurements 64 MiB-2.4 GiB)"},
            "offered_steps_per_s": offered, "arrival_span_s": span, "iterations": rep["iterations"],
@@ -757,6 +759,8 @@ def main():
                          "steps on its own stream")
     ap.add_argument("--serve-max-pairs", type=float, default=None,
                     help="serving: cap on an iteration's voxel-element pairs (resident scans' steps together)")
+    ap.add_argument("--serve-iteration-pairs", type=float, default=None,
+                    help="serving (batched): pair budget of one iteration, filled fair-share")
     ap.add_argument("--storage", choices=["f32", "bf16", "f16"], default="f32",
                     help="storage type of the volume and the measurements (arithmetic stays FP32)")
     args = ap.parse_args()

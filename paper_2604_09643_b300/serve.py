@@ -10,8 +10,9 @@ the joint volume + pose reconstruction.  The server:
   request waits for memory);
 * keeps every admitted scan resident: its volume, poses, measurements, Adam
   state and a private library context (workspace);
-* runs iterations: each is ONE batched gradient step over every resident scan that
-  still owes steps (pasfm_step_batch), in which the scans sharing a kernel
+* runs iterations: each is ONE batched gradient step over the resident scans that
+  still owe steps (all of them, or with an iteration budget the least-served ones that
+  fit: fair share by voxel-element pairs) (pasfm_step_batch), in which the scans sharing a kernel
   instantiation run their forward, reduction and fused adjoint / pose gradient as
   one persistent launch per phase, so their work overlaps on the device; up to
   ``inflight`` iterations are enqueued at a time, and arrivals join at the next
@@ -142,6 +143,7 @@ class _Scan:
             self.loss = torch.zeros((), dtype=torch.float64, device=d)
         self.ctx.reserve(req.geom)
         self.issued = 0
+        self.served_pairs = 0   # voxel-element pairs of the steps issued so far (fair share)
         self.events = deque()   # (start, end) per step still running, oldest first
         self.step_ms = []
         self.failed = None
@@ -200,20 +202,39 @@ def issue_iteration(scans, stream):
     for x in scans:
         x.events.append((s, e))
         x.issued += 1
+        x.served_pairs += step_pairs(x.req.geom)
+
+
+def fair_share(due, budget):
+    """The scans of the next iteration: the least-served first (pairs of the steps issued
+    so far, then arrival order), first fit into `budget` pairs; the least-served scan is
+    always taken, so a scan larger than the budget runs alone in its turn and none starves."""
+    pick, total = [], 0
+    for x in sorted(due, key=lambda x: (x.served_pairs, x.req.arrival_s, x.req.id)):
+        c = step_pairs(x.req.geom)
+        if pick and total + c > budget:
+            continue
+        pick.append(x)
+        total += c
+    return pick
 
 
 class Server:
     """Admit, run and retire reconstruction requests on one GPU."""
 
     def __init__(self, device=0, reserve_bytes=2 << 30, max_active=16, inflight=2, mem_info=None,
-                 clock=time.perf_counter, mode="batched", max_iteration_pairs=None):
-        """max_iteration_pairs: optional cap on the voxel-element pairs of one iteration (the
-        resident scans' steps together): a request that would take the iteration past it
-        waits, unless nothing is running.  It bounds the step latency (an iteration's
-        duration) at the cost of queue wait; None admits up to max_active scans."""
+                 clock=time.perf_counter, mode="batched", max_iteration_pairs=None, iteration_pairs=None):
+        """max_iteration_pairs: optional cap on the voxel-element pairs of all resident scans'
+        steps together: a request that would pass it waits, unless nothing is running; it
+        bounds the step latency at the cost of queue wait (None: up to max_active scans).
+        iteration_pairs: optional budget of one batched iteration; each iteration then takes
+        the least-served resident scans that fit (fair share by pairs), so small scans step
+        in most iterations while a large one steps when its turn comes (None: every
+        resident scan that owes a step, every iteration)."""
         if mode not in ("batched", "streams"):
             raise ValueError("mode must be 'batched' or 'streams'")
         self.max_iteration_pairs = max_iteration_pairs
+        self.iteration_pairs = iteration_pairs
         self.device = torch.device("cuda", device) if isinstance(device, int) else device
         self.reserve = reserve_bytes
         self.max_active = max_active
@@ -288,6 +309,8 @@ class Server:
                    if scan.issued < scan.req.steps and len(scan.events) < self.inflight]
             if not due:
                 return
+            if self.iteration_pairs is not None:
+                due = fair_share(due, self.iteration_pairs)
             issue_iteration(due, self._stream)
             self.iterations += 1
 

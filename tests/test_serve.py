@@ -67,3 +67,22 @@ def test_iteration_work_cap_holds_requests_until_the_iteration_has_room(monkeypa
     srv.max_iteration_pairs = 1   # smaller than any scan: admitted only into an empty iteration
     srv._admit()
     assert admitted == [0, 1, 2] and [r.id for r in srv.queue] == [3]
+
+
+def test_fair_share_fills_the_iteration_with_the_least_served_scans():
+    """The next batched iteration takes scans by pairs served so far (then arrival), first
+    fit into the budget; the least-served is always taken, even when it alone exceeds it."""
+    class S:
+        def __init__(self, i, n, served):
+            self.req = _req(i, n=n)
+            self.served_pairs = served
+
+    small = [S(0, 16, 0), S(1, 16, 10), S(2, 16, 5)]
+    big = S(3, 64, 1)
+    per_small = serve.step_pairs(small[0].req.geom)
+    pick = serve.fair_share(small + [big], 2 * per_small)
+    assert [x.req.id for x in pick] == [0, 2]            # least served first; the big one does not fit
+    pick = serve.fair_share([big, small[1]], per_small)  # the big one is the least served: alone
+    assert [x.req.id for x in pick] == [3]
+    pick = serve.fair_share(small, 10 ** 15)
+    assert sorted(x.req.id for x in pick) == [0, 1, 2]

@@ -30,20 +30,24 @@ def _requests():
             _request(2, 40, 4, 8, 1024, 0.05), _request(3, 24, 8, 3, 512, 0.1)]
 
 
-@pytest.mark.parametrize("mode", ["batched", "streams"])
+@pytest.mark.parametrize("mode", ["batched", "batched_fair_share", "streams"])
 def test_results_are_identical_alone_and_in_the_mix(cuda_device, mode):
     """Four scans of different sizes and arrays, arriving while others run: each result
     is bit-identical to the same request served alone (batched iterations: the scans
-    share launches; streams: the scans' own launches interleave on the device)."""
+    share launches, with the fair-share budget in varying subsets; streams: the scans'
+    own launches interleave on the device)."""
     reqs = _requests()
+    kw = dict(mode="streams") if mode == "streams" else dict(mode="batched")
+    if mode == "batched_fair_share":  # about two of the four scans' steps per iteration
+        kw["iteration_pairs"] = 2 * serve.step_pairs(reqs[0].geom)
     alone = {}
     for r in reqs:
-        srv = serve.Server(device=0, mode=mode)
+        srv = serve.Server(device=0, **kw)
         srv.submit(r)
         res = srv.run()
         assert res[0].status == "ok"
         alone[r.id] = res[0]
-    srv = serve.Server(device=0, inflight=2, mode=mode)
+    srv = serve.Server(device=0, inflight=2, **kw)
     for r in reqs:
         srv.submit(r)
     mixed = {r.id: r for r in srv.run()}
