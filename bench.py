@@ -528,7 +528,7 @@ def run_serving(args):
 
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
-    specs = synth.request_stream()[:args.serve_requests]
+    specs = synth.request_stream(rate_per_s=args.serve_rate)[:args.serve_requests]
     with binding.Context(0) as ctx:
         reqs = [serve.request_from_spec(sp, ctx, steps=args.serve_steps) for sp in specs]
         warm = serve.request_from_spec(dict(specs[0], id=-1, arrival_s=0.0, n=64, n_frames=8, m=8),
@@ -538,7 +538,7 @@ def run_serving(args):
     srv.submit(warm)
     srv.run()
     srv = serve.Server(device=0, mode=args.serve_mode, max_iteration_pairs=args.serve_max_pairs,
-                       iteration_pairs=args.serve_iteration_pairs)
+                       iteration_pairs=args.serve_iteration_pairs or None)
     for r in reqs:
         srv.submit(r)
     with ClockSampler(0) as clk:
@@ -552,10 +552,13 @@ def run_serving(args):
            "warmup": max(args.warmup, 3), "ms_per_step": 1e3 / rep["steps_per_s"] if rep["steps_per_s"] else None,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
            "data": "synthetic",
-           "config": {"workload": WORKLOAD_SERVING, "requests": len(specs), "steps_per_request": args.serve_steps,
+           "config": {"workload": WORKLOAD_SERVING.replace("poisson4", f"poisson{args.serve_rate:g}"),
+                      "requests": len(specs), "steps_per_request": args.serve_steps,
                       "scheduling": args.serve_mode, "max_iteration_pairs": args.serve_max_pairs,
-                      "iteration_pairs": args.serve_iteration_pairs,
-                      "arrivals": "seeded Poisson stream, mean 4 scans/s, first requests in arrival order",
+                      "iteration_pairs": (args.serve_iteration_pairs or None) if args.serve_mode == "batched"
+                      else None,
+                      "arrivals": f"seeded Poisson stream, mean {args.serve_rate:g} scans/s, first requests in "
+                                  "arrival order",
                       "l2": "inputs larger than L2 (each scan's measurements 64 MiB-2.4 GiB)"},
            "offered_steps_per_s": offered, "arrival_span_s": span, "iterations": rep["iterations"],
            "step_ms_p50": rep["step_ms_p50"], "step_ms_p99": rep["step_ms_p99"],
@@ -759,8 +762,10 @@ def main():
                          "steps on its own stream")
     ap.add_argument("--serve-max-pairs", type=float, default=None,
                     help="serving: cap on an iteration's voxel-element pairs (resident scans' steps together)")
-    ap.add_argument("--serve-iteration-pairs", type=float, default=None,
-                    help="serving (batched): pair budget of one iteration, filled fair-share")
+    ap.add_argument("--serve-iteration-pairs", type=float, default=1e12,
+                    help="serving (batched): pair budget of one iteration, filled fair-share (0: every "
+                         "resident scan in every iteration)")
+    ap.add_argument("--serve-rate", type=float, default=4.0, help="serving: mean arrival rate (scans/s)")
     ap.add_argument("--storage", choices=["f32", "bf16", "f16"], default="f32",
                     help="storage type of the volume and the measurements (arithmetic stays FP32)")
     args = ap.parse_args()
