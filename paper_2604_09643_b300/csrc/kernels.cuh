@@ -564,6 +564,16 @@ __device__ __forceinline__ void slot_sums2(const float* ga, const float* gb, flo
 
 constexpr int kBatch = 32;  // traces staged per batch
 
+// hi + lo += v with the rounding error of the addition kept (TwoSum: exact for any order of
+// magnitudes, six FP32 additions)
+__device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float v) {
+  const float s = hi + v;
+  const float bp = s - hi;
+  const float err = (hi - (s - bp)) + (v - bp);
+  hi = s;
+  lo += err;
+}
+
 template <int C>
 struct BwdLayout {
   static constexpr int NT = C * C;
@@ -801,14 +811,20 @@ __device__ __forceinline__ bool bwd_tile(const CUtensorMap* gmap, const BwdParam
     }
     if (warp == b % L::NW) {
       if (POSE && lane < cnt) {
-        double r0 = 0.0, r1 = 0.0, r2 = 0.0, r3 = 0.0;
-        for (int w = 0; w < L::NW; ++w) {
+        // the warps' partial sums, added in warp order in compensated FP32 (Knuth's TwoSum
+        // keeps each addition's rounding error in a second word): as exact as FP64 here and
+        // far cheaper than B300's FP64 adds, which kept this rotating warp behind the others
+        float4 hi = red[(buf * L::NW) * kBatch + lane], lo = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int w = 1; w < L::NW; ++w) {
           const float4 v = red[(buf * L::NW + w) * kBatch + lane];
-          r0 += v.x;
-          r1 += v.y;
-          r2 += v.z;
-          r3 += v.w;
+          two_sum_acc(hi.x, lo.x, v.x);
+          two_sum_acc(hi.y, lo.y, v.y);
+          two_sum_acc(hi.z, lo.z, v.z);
+          two_sum_acc(hi.w, lo.w, v.w);
         }
+        const double r0 = double(hi.x) + lo.x, r1 = double(hi.y) + lo.y, r2 = double(hi.z) + lo.z,
+                     r3 = double(hi.w) + lo.w;
         const float mk = refb[buf * kBatch + lane].w;
         const double* u = refu + (buf * kBatch + lane) * 3;
         double* gp = G.gpart + (static_cast<int64_t>(ib + b * kBatch + lane) * ncubes + c) * 3;
