@@ -53,16 +53,19 @@ struct PairMath {
 
 // idx_bias = kMagicBits + (window slot 0 relative to N_c), so that
 // idx = n_s - (slot 0) comes out of the rounding trick with one integer op.
-__device__ __forceinline__ PairMath pair_math(float A, float dc2, float dcf, float phim, float inv_h, float h,
-                                              float cb1, int idx_bias) {
+// The callers pass A in units of the sample spacing, Ah = A / h (their per-row and
+// per-trace terms are formed scaled), so that D2 = d_c^2 + h Ah and
+// psi = phi_c + Ah / (d + d_c) each take one FMA: d - d_c = A / (d + d_c) without
+// cancellation, and no separate division by h.
+__device__ __forceinline__ PairMath pair_math(float Ah, float dc2, float dcf, float phim, float h, float cb1,
+                                              int idx_bias) {
   PairMath m;
-  const float D2 = dc2 + A;
+  const float D2 = fmaf(h, Ah, dc2);
   m.rs = rsqrtf(D2);
-  const float del = __fdividef(A, fmaf(D2, m.rs, dcf));  // d - d_c = A / (d + d_c), no cancellation
-  const float psi = fmaf(del, inv_h, phim);               // psi_c - N_c - 1/2 + delta / h
-  const float t = psi + kMagic;                           // round to nearest = floor(psi + 1/2)
+  const float psi = fmaf(Ah, __fdividef(1.f, fmaf(D2, m.rs, dcf)), phim);  // psi_c - N_c - 1/2 + delta / h
+  const float t = psi + kMagic;                                             // round to nearest = floor(psi + 1/2)
   m.idx = static_cast<unsigned>(__float_as_int(t) - idx_bias);
-  m.beta1 = fmaf((t - kMagic) - psi, h, cb1);             // (n_s - psi_full) h - a0 + h
+  m.beta1 = fmaf((t - kMagic) - psi, h, cb1);                               // (n_s - psi_full) h - a0 + h
   return m;
 }
 
@@ -84,8 +87,24 @@ struct PairMath2 {
   float2 beta1;
 };
 
-__device__ __forceinline__ PairMath2 pair_math2(float2 A, float dc2, float dcf, float phim, float inv_h, float h,
-                                                float cb1, int idx_bias) {
+__device__ __forceinline__ PairMath2 pair_math2(float2 Ah, float dc2, float dcf, float phim, float h, float cb1,
+                                                int idx_bias) {
+  PairMath2 m;
+  const float2 D2 = fma2(f2(h), Ah, f2(dc2));
+  m.rs = make_float2(rsqrtf(D2.x), rsqrtf(D2.y));
+  const float2 den = fma2(D2, m.rs, f2(dcf));
+  const float2 psi = fma2(Ah, make_float2(__fdividef(1.f, den.x), __fdividef(1.f, den.y)), f2(phim));
+  const float2 t = add2(psi, f2(kMagic));
+  m.idx0 = static_cast<unsigned>(__float_as_int(t.x) - idx_bias);
+  m.idx1 = static_cast<unsigned>(__float_as_int(t.y) - idx_bias);
+  m.beta1 = fma2(fma2(psi, f2(-1.f), add2(t, f2(-kMagic))), f2(h), f2(cb1));
+  return m;
+}
+
+// The same with A itself (the backward): delta = A / (d + d_c) formed first, then
+// psi = phi_c + delta / h.
+__device__ __forceinline__ PairMath2 pair_math2_del(float2 A, float dc2, float dcf, float phim, float inv_h, float h,
+                                                    float cb1, int idx_bias) {
   PairMath2 m;
   const float2 D2 = add2(f2(dc2), A);
   m.rs = make_float2(rsqrtf(D2.x), rsqrtf(D2.y));
@@ -235,11 +254,12 @@ __device__ __forceinline__ bool fwd_tile(const CUtensorMap* p0map, const FwdPara
                              G.oz + G.dz * (cz * C + hc), Q.sup, Q.tau0, Q.inv_h);
   const int nb_rel = static_cast<int>(floorf(R.phim - Q.nb_shift)) - 1;
   const float dxf = static_cast<float>(G.dx), dyf = static_cast<float>(G.dy), dzf = static_cast<float>(G.dz);
+  // the x, y and z parts of A = |q|^2 - 2 q.u, in units of h
   float Pix[C];
 #pragma unroll
   for (int ix = 0; ix < C; ++ix) {
     const float qx = (ix - 0.5f * (C - 1)) * dxf;
-    Pix[ix] = qx * (qx + R.m2ux);
+    Pix[ix] = (qx * Q.inv_hf) * (qx + R.m2ux);
   }
   float2 Pix2[C / 2];
 #pragma unroll
@@ -271,11 +291,11 @@ __device__ __forceinline__ bool fwd_tile(const CUtensorMap* p0map, const FwdPara
   unsigned seen = 0;  // largest raw index at the row ends (a negative one wraps to a huge value)
   for (int lz = 0; lz < C; ++lz) {
     const float qz = (lz - 0.5f * (C - 1)) * dzf;
-    const float Cz = qz * (qz + R.m2uz);
+    const float Cz = (qz * Q.inv_hf) * (qz + R.m2uz);
     for (int ly = 0; ly < C; ++ly) {
       if (!rowflag[lz * C + ly]) continue;
       const float qy = (ly - 0.5f * (C - 1)) * dyf;
-      const float Crow = fmaf(qy, qy + R.m2uy, Cz);
+      const float Crow = fmaf(qy * Q.inv_hf, qy + R.m2uy, Cz);
       const float* prow = tile + (lz * C + ly) * C;
       // The pair's slot weights b_k - b_{k+1} (k = 0..S-1) sum to b_0 - b_S = 0, so for
       // S >= 3 the window holds their running sum, negated: slot k gets b_{k+1} - b_0 for
@@ -293,8 +313,7 @@ __device__ __forceinline__ bool fwd_tile(const CUtensorMap* p0map, const FwdPara
           for (int u = 0; u < 4; u += 2) {
             const int i = i4 + u;
             const float2 pv = u == 0 ? make_float2(pv4.x, pv4.y) : make_float2(pv4.z, pv4.w);
-            const PairMath2 m = pair_math2(add2(Pix2[i / 2], f2(Crow)), R.dc2, R.dcf, R.phim, Q.inv_hf, Q.h, Q.cb1,
-                                           idx_bias);
+            const PairMath2 m = pair_math2(add2(Pix2[i / 2], f2(Crow)), R.dc2, R.dcf, R.phim, Q.h, Q.cb1, idx_bias);
             if (i == 0) seen = max(seen, m.idx0);
             if (i + 1 == C - 1) seen = max(seen, m.idx1);
             float* sa = col + min(m.idx0, max_idx) * kWarp;
@@ -327,7 +346,7 @@ __device__ __forceinline__ bool fwd_tile(const CUtensorMap* p0map, const FwdPara
         // whose difference cancels in homogeneous regions, so the weights go in directly.
 #pragma unroll
         for (int i = 0; i < C; ++i) {
-          const PairMath m = pair_math(Pix[i] + Crow, R.dc2, R.dcf, R.phim, Q.inv_hf, Q.h, Q.cb1, idx_bias);
+          const PairMath m = pair_math(Pix[i] + Crow, R.dc2, R.dcf, R.phim, Q.h, Q.cb1, idx_bias);
           if (i == 0 || i == C - 1) seen = max(seen, m.idx);
           float* slot = col + min(m.idx, max_idx) * kWarp;
           const float s = prow[i] * m.rs;
@@ -760,7 +779,7 @@ __device__ __forceinline__ bool bwd_tile(const CUtensorMap* gmap, const BwdParam
       for (int k2 = 0; k2 < C / 2; ++k2) {
         const int k = 2 * k2;
         const float2 A = add2(pe[k2], f2(Crow));
-        const PairMath2 m = pair_math2(A, ra.w, rb.x, rb.y, Q.inv_hf, Q.h, Q.cb1, idx_bias);
+        const PairMath2 m = pair_math2_del(A, ra.w, rb.x, rb.y, Q.inv_hf, Q.h, Q.cb1, idx_bias);
         if (k == 0) seen = max(seen, m.idx0);
         if (k + 1 == C - 1) seen = max(seen, m.idx1);
         float2 S1, S2 = f2(0.f);

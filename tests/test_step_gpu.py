@@ -136,6 +136,9 @@ def test_step_matches_oracle_over_three_steps(cuda_device, case, mode):
                 assert not adam.m_pose.any() and not adam.v_pose.any(), tag
                 continue
             mp, vp = adam.m_pose.cpu().numpy(), adam.v_pose.cpu().numpy()
+            worst = max(rel_l2(mp[f, blk], ost.m_pose[f, blk]) for f in range(F) for blk in (slice(0, 3), slice(3, 6))
+                        if not (f == 0 and opts.get("fix_frame0")))
+            print(f"{case} {mode} step {k}: worst twist first-moment error {worst:.2e}")
             for f in range(F):
                 for blk in (slice(0, 3), slice(3, 6)):
                     assert rel_l2(mp[f, blk], ost.m_pose[f, blk]) < REL_L2_POSE, (tag, f, blk)
