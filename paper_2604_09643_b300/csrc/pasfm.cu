@@ -144,6 +144,8 @@ int make_plan(const Geo& G, Plan* pl) {
   pl->W = W;
   pl->rho = 0.5 * (C - 1) * diag;
   pl->nb_shift = static_cast<float>(pl->rho / pl->h);
+  // Each staged trace row is a TMA destination, which must start on a 128-byte boundary:
+  // WP stays a multiple of 32 floats (W + 4 covers the window and its 4-aligned start).
   pl->WP = ((W + 4) + 31) & ~31;
   pl->ncx = (g.nx + C - 1) / C;
   pl->ncy = (g.ny + C - 1) / C;

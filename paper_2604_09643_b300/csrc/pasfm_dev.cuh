@@ -29,7 +29,7 @@ struct Plan {
   int C;          // cube side in voxels (8 or 16)
   int S;          // sample slots per voxel-element pair: floor(2 sup / h) + 2
   int W;          // forward window length per element and cube (multiple of 4)
-  int WP;         // backward staged window length (W + 4, multiple of 32)
+  int WP;         // backward staged window length (W + 4, a multiple of 32: 128-byte TMA rows)
   int ncx, ncy, ncz, ncubes;
   int fwd_warps;  // warps (32 elements each) per forward CTA
   int n_egroups;  // element groups of 32 * fwd_warps
