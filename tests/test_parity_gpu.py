@@ -43,6 +43,8 @@ CASES = {
     # narrower than a sample (a0 = 0.015 mm, S = 2); the cases above have S = 7, 4, 4, 4, 10
     "sphere_single_frame_s3": sphere(single_frame_case, 0.03),
     "sphere_ragged_s2": sphere(ragged_case, 0.015),
+    # the largest compiled sphere slot count: S = 16 (a0 = 0.27 mm on the coarse grid, 8^3 cubes)
+    "sphere_coarse_s16": sphere(coarse_case, 0.27),
     # Gaussian kernel (Eq. 1): slot counts S = floor(8 sigma / h) + 2 of 19, 8, 8, 12 and 32 (the largest compiled)
     "gauss_single_frame": gaussian(single_frame_case, 0.08),
     "gauss_ragged": gaussian(ragged_case, 0.03),
@@ -113,7 +115,9 @@ def test_pose_grad(ctx, case, masked):
     (a0 < h / 2, S = 2), whose pairs carry their whole weight in one or two
     samples, so that one pair taking the other one-sided derivative at a support
     edge moves a frame's gradient by about 1e-3 (the oracle's band there is 10-30%
-    of the rotation block, against 2% at S = 4)."""
+    of the rotation block, against 2% at S = 4); and so is the S = 16 sphere, added with
+    4 boundary terms within 1e-7 mm of the edge (0.2% of a row's gradient each) and
+    held to the band from the start."""
     name, geom, p0, elem, poses, xw = case
     g = pose_residual(geom, p0, elem, poses)
     F, E = geom["n_frames"], geom["n_elem"]
@@ -124,7 +128,7 @@ def test_pose_grad(ctx, case, masked):
                                None if mask is None else dev(mask), want_elem=True)
     got6, gotG = got6.cpu().numpy(), gotG.cpu().numpy()
     assert_status_ok(ctx)
-    if name.endswith("ragged_cut") or name == "sphere_ragged_s2":
+    if name.endswith("ragged_cut") or name in ("sphere_ragged_s2", "sphere_coarse_s16"):
         gm = g if mask is None else g * mask[:, :, None]
         mid, half = oracle.element_gradient_bounds(geom, p0, gm, xw, np.arange(F * E), EPS_KINK)
         _band_check(gotG.reshape(-1, 3), got6, mid, half,
