@@ -10,6 +10,12 @@
 
 namespace pasfm {
 
+// fwd_reduce_kernel: samples per warp accumulator, and cubes whose windows a warp loads
+// per step (4 measured fastest on the full scan: 0.67 ms against 0.75 at 8 and 0.83 at 2;
+// at 8 the loads' registers spill and fewer blocks fit an SM)
+constexpr int kRedChunk = 1024;
+constexpr int kRedUnroll = 4;
+
 // x_fj = R_f e_j + t_f in FP64; flag elements closer than a0 to the grid box.
 __global__ void elem_pos_kernel(const double* __restrict__ elem, const double* __restrict__ pose,
                                 double* __restrict__ xw, int F, int E, double lox, double loy, double loz,

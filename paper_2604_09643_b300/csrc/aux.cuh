@@ -6,16 +6,13 @@
 
 namespace pasfm {
 
-constexpr int kRedChunk = 1024;  // samples per warp accumulator in fwd_reduce_kernel
-constexpr int kRedUnroll = 8;    // cubes loaded per step
-constexpr int kRedLanes = 8;     // ceil(W_max / 32), W_max = 256
 constexpr int kMinS = 2, kMaxSSphere = 16, kMaxSGauss = 32;
 
 __global__ void elem_pos_kernel(const double* elem, const double* pose, double* xw, int F, int E, double lox,
                                 double loy, double loz, double hix, double hiy, double hiz, double a0,
                                 unsigned* status);
 // fwd_reduce_kernel<LANES> for LANES = ceil(W / 32), launched with 8 warps and
-// 8 * kRedChunk floats of dynamic shared memory
+// fwd_reduce_smem() bytes of dynamic shared memory
 cudaError_t fwd_reduce_launch(const RedParams& P, int blocks, cudaStream_t st);
 // the same over several scans' chunks in one launch (window length W shared)
 cudaError_t fwd_reduce_batch_launch(const RedBatch& B, int W, cudaStream_t st);
