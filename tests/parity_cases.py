@@ -49,6 +49,20 @@ def tma_case(seed=0):
     return geom, p0, elem, poses
 
 
+def wide_window_case(seed=0):
+    """The largest forward window of 16^3 cubes: 0.17 mm spacing (cube diagonal 2.2 mm
+    of distance range, 118 samples, plus S = 6 slots and the margin: W = 128, the
+    16^3 cap) on an aligned 28 x 24 x 20 grid, 40 elements, 2 frames, Nt = 1024."""
+    geom = synth.make_geom((20, 24, 28), 0.17, 40, 2, 1024)
+    rng = np.random.default_rng(700 + seed)
+    p0 = synth.vessel_tree_phantom(geom, 6, rng)
+    p0 += rng.uniform(0, 0.02, size=p0.shape).astype(np.float32)
+    elem = synth.planar_array(8, 5, 0.6)
+    trng = np.random.default_rng(800 + seed)
+    poses = synth.sweep_poses(2, 0.3, synth.top_face_z(geom) + 3.0, trng)
+    return geom, p0, elem, poses
+
+
 def coarse_case(seed=0):
     """Coarse grid (0.3 mm, a0 = 0.15 mm, 2 a0 / h = 8 exactly): 10 slots per pair
     and 8^3 cubes."""
