@@ -63,6 +63,20 @@ def wide_window_case(seed=0):
     return geom, p0, elem, poses
 
 
+def coarse_window_case(seed=0):
+    """The largest forward window of 8^3 cubes and the largest sphere slot count at once:
+    0.557 mm spacing (a0 = 0.2785 mm, S = 16; an 8^3 cube's 181-sample distance range
+    plus the slots and the margin: W = 200, the 8^3 cap) on a 12 x 12 x 10 grid, 25
+    elements, 2 frames, Nt = 800."""
+    geom = synth.make_geom((10, 12, 12), 0.557, 25, 2, 800)
+    rng = np.random.default_rng(900 + seed)
+    p0 = rng.uniform(0, 1, size=(10, 12, 12)).astype(np.float32)
+    elem = synth.planar_array(5, 5, 1.0)
+    trng = np.random.default_rng(1000 + seed)
+    poses = synth.sweep_poses(2, 0.5, synth.top_face_z(geom) + 4.0, trng)
+    return geom, p0, elem, poses
+
+
 def coarse_case(seed=0):
     """Coarse grid (0.3 mm, a0 = 0.15 mm, 2 a0 / h = 8 exactly): 10 slots per pair
     and 8^3 cubes."""

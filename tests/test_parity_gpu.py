@@ -20,7 +20,8 @@ import torch
 import oracle
 from paper_2604_09643_b300 import binding, synth
 from tests.parity_cases import (REL_L2_POSE, REL_L2_SIG, coarse_case, gaussian, pose_residual, ragged_case,
-                                rel_l2, residual, sphere, tma_case, wide_window_case)
+                                rel_l2, residual, sphere, tma_case, wide_window_case,
+                                coarse_window_case)
 
 pytestmark = pytest.mark.gpu
 
@@ -49,6 +50,8 @@ CASES = {
     "sphere_s11_tma": sphere(tma_case, 0.18),
     # the 16^3 cubes' window cap: W = 128 (0.17 mm spacing), staged rows of 160 samples
     "wide_window": wide_window_case,
+    # the 8^3 cubes' window cap with the largest sphere slot count: W = 200, S = 16
+    "coarse_window": coarse_window_case,
     # Gaussian kernel (Eq. 1): slot counts S = floor(8 sigma / h) + 2 of 19, 8, 8, 12 and 32 (the largest compiled)
     "gauss_single_frame": gaussian(single_frame_case, 0.08),
     "gauss_ragged": gaussian(ragged_case, 0.03),
@@ -119,9 +122,9 @@ def test_pose_grad(ctx, case, masked):
     (a0 < h / 2, S = 2), whose pairs carry their whole weight in one or two
     samples, so that one pair taking the other one-sided derivative at a support
     edge moves a frame's gradient by about 1e-3 (the oracle's band there is 10-30%
-    of the rotation block, against 2% at S = 4); and so are the S = 16, S = 11 and
-    window-cap spheres, added with 4, 83 and 10 boundary terms within 1e-7 mm of the edge
-    and held to the band from the start."""
+    of the rotation block, against 2% at S = 4); and so are the S = 16, S = 11 and the two
+    window-cap cases, added with 4, 83, 10 and 1 boundary terms within 1e-7 mm of the
+    edge and held to the band (and strictly on their clean rows) from the start."""
     name, geom, p0, elem, poses, xw = case
     g = pose_residual(geom, p0, elem, poses)
     F, E = geom["n_frames"], geom["n_elem"]
@@ -133,7 +136,7 @@ def test_pose_grad(ctx, case, masked):
     got6, gotG = got6.cpu().numpy(), gotG.cpu().numpy()
     assert_status_ok(ctx)
     if name.endswith("ragged_cut") or name in ("sphere_ragged_s2", "sphere_coarse_s16", "sphere_s11_tma",
-                                               "wide_window"):
+                                               "wide_window", "coarse_window"):
         gm = g if mask is None else g * mask[:, :, None]
         mid, half = oracle.element_gradient_bounds(geom, p0, gm, xw, np.arange(F * E), EPS_KINK)
         _band_check(gotG.reshape(-1, 3), got6, mid, half,
