@@ -58,6 +58,7 @@ CASES = {
     "gauss_ragged_cut": lambda: gaussian(ragged_case, 0.03)(cut=True),
     "gauss_tma": gaussian(tma_case, 0.05),
     "gauss_coarse_s32": gaussian(coarse_case, 0.141),
+    "gauss_s32_tma": gaussian(tma_case, 0.141),  # the largest Gaussian on 16^3 cubes and the TMA paths
     # the smallest slot counts: a pulse narrower than a sample (S = 2) and S = 4
     "gauss_single_frame_s2": gaussian(single_frame_case, 0.004),
     "gauss_ragged_s4": gaussian(ragged_case, 0.01),
