@@ -9,7 +9,7 @@
 //                       bank-conflict free and no atomics are needed.  The
 //                       window (the cube's distance range for that element)
 //                       holds the running sum of the slot weights, so a pair
-//                       writes S - 1 slots (its weights sum to zero; 3 <= S <= 16);
+//                       writes S - 1 slots (its weights sum to zero; 3 <= S <= 12);
 //                       the flush differences it into a per-cube partial trace and
 //                       fwd_reduce_kernel sums the partials in a fixed order.
 //                       Voxels go in pairs along a row, in packed FP32.
@@ -181,12 +181,13 @@ __device__ __forceinline__ void gauss_boundaries2(float2 beta1, float h, const G
 // ------------------------------------------------------------------------
 // forward
 // ------------------------------------------------------------------------
-// The forward window holds the running sum of the slot weights for 3 <= S <= 16 (one
+// The forward window holds the running sum of the slot weights for 3 <= S <= 12 (one
 // read-modify-write fewer per pair) and the weights themselves otherwise: at S = 2 the
-// running sum would cancel worst, and for the widest pulses (S > 16) the running sums grow
-// to ~S/2 times the trace, whose rounding then passed the 1e-5 accuracy bound (1.2e-5 at
-// S = 32 on 16^3 cubes of a dense volume) for a saving of one write in S.
-__host__ __device__ constexpr bool fwd_running_sum(int S) { return S >= 3 && S <= 16; }
+// running sum would cancel worst, and for wide pulses the running sums grow with S
+// relative to the trace, and so does their rounding (on 16^3 cubes of a dense volume:
+// 3.0e-6 relative L2 at S = 4, 6.8e-6 at S = 11, 8.5e-6 at S = 16, 1.2e-5 at S = 32,
+// against 0.9e-6 at S = 32 with the weights), for a saving of one write in S.
+__host__ __device__ constexpr bool fwd_running_sum(int S) { return S >= 3 && S <= 12; }
 
 template <int C>
 __host__ __device__ constexpr int fwd_tile_bytes() { return C * C * C * 4; }
@@ -305,7 +306,7 @@ __device__ __forceinline__ bool fwd_tile(const CUtensorMap* p0map, const FwdPara
       const float Crow = fmaf(qy * Q.inv_hf, qy + R.m2uy, Cz);
       const float* prow = tile + (lz * C + ly) * C;
       // The pair's slot weights b_k - b_{k+1} (k = 0..S-1) sum to b_0 - b_S = 0, so for
-      // 3 <= S <= 16 the window holds their running sum, negated: slot k gets
+      // 3 <= S <= 12 the window holds their running sum, negated: slot k gets
       // b_{k+1} - b_0 for k = 0..S-2 and slot S-1 gets nothing.  That is S - 1
       // read-modify-writes instead of S through shared memory, which bounds this loop;
       // the flush takes the first difference (wider pulses write the weights).  Sphere: b_0 = a0^2, b_k = beta_k^2 inside, the last boundary

@@ -48,6 +48,7 @@ CASES = {
     "sphere_coarse_s16": sphere(coarse_case, 0.27),
     # a wide sphere on 16^3 cubes and the TMA paths: S = 11 (a0 = 0.18 mm at 0.1 mm spacing)
     "sphere_s11_tma": sphere(tma_case, 0.18),
+    "sphere_s16_tma": sphere(tma_case, 0.27),  # the largest running-sum window on 16^3 cubes
     # the 16^3 cubes' window cap: W = 128 (0.17 mm spacing), staged rows of 160 samples
     "wide_window": wide_window_case,
     # the 8^3 cubes' window cap with the largest sphere slot count: W = 200, S = 16
@@ -101,6 +102,7 @@ def test_forward(ctx, case):
     got = ctx.forward(geom, dev(p0), dev(elem), dev(poses)).cpu().numpy()
     assert_status_ok(ctx)
     err = rel_l2(got, ref)
+    print(f"forward {name}: {err:.2e}")
     assert err < REL_L2_SIG, (name, err)
 
 
@@ -123,9 +125,10 @@ def test_pose_grad(ctx, case, masked):
     (a0 < h / 2, S = 2), whose pairs carry their whole weight in one or two
     samples, so that one pair taking the other one-sided derivative at a support
     edge moves a frame's gradient by about 1e-3 (the oracle's band there is 10-30%
-    of the rotation block, against 2% at S = 4); and so are the S = 16, S = 11 and the two
-    window-cap cases, added with 4, 83, 10 and 1 boundary terms within 1e-7 mm of the
-    edge and held to the band (and strictly on their clean rows) from the start."""
+    of the rotation block, against 2% at S = 4); and so are the wide spheres (S = 16 on
+    8^3 and on 16^3 cubes, S = 11) and the two window-cap cases, added with 4, 83, 83, 10
+    and 1 boundary terms within 1e-7 mm of the edge and held to the band (and strictly on
+    their clean rows, where they have any) from the start."""
     name, geom, p0, elem, poses, xw = case
     g = pose_residual(geom, p0, elem, poses)
     F, E = geom["n_frames"], geom["n_elem"]
@@ -137,6 +140,7 @@ def test_pose_grad(ctx, case, masked):
     got6, gotG = got6.cpu().numpy(), gotG.cpu().numpy()
     assert_status_ok(ctx)
     if name.endswith("ragged_cut") or name in ("sphere_ragged_s2", "sphere_coarse_s16", "sphere_s11_tma",
+                                               "sphere_s16_tma",
                                                "wide_window", "coarse_window"):
         gm = g if mask is None else g * mask[:, :, None]
         mid, half = oracle.element_gradient_bounds(geom, p0, gm, xw, np.arange(F * E), EPS_KINK)
