@@ -113,6 +113,7 @@ def test_adjoint(ctx, case):
     got = ctx.adjoint(geom, dev(elem), dev(poses), dev(g)).cpu().numpy()
     assert_status_ok(ctx)
     err = rel_l2(got, ref)
+    print(f"adjoint {name}: {err:.2e}")
     assert err < REL_L2_SIG, (name, err)
 
 
