@@ -221,12 +221,13 @@ def make_workload(seed_offset=0, n_frames=64, workload="full_scan", sigma=None):
 def fwd_smem_bytes_per_pair(geom):
     """Algorithmic shared-memory bytes per voxel-element pair of the forward: the load and
     store (4 bytes each) of every window slot the pair writes -- S - 1 slots of the
-    running-sum window for S >= 3, the two slots of the direct dipole for S = 2, with
-    S = floor(2 sup / h) + 2 slots and sup = a0 or 4 sigma."""
+    running-sum window for 3 <= S <= 8, the S slot weights themselves otherwise (the
+    wider pulses, whose running sums would round too coarsely, and the dipole of S = 2),
+    with S = floor(2 sup / h) + 2 slots and sup = a0 or 4 sigma."""
     h = geom["c_mm_per_us"] / geom["fs_mhz"]
     sup = 4 * geom["sigma_mm"] if geom.get("kernel") == "gauss" else geom["a0_mm"]
     S = int(np.floor(2 * sup / h)) + 2
-    return 8 * (S - 1 if S >= 3 else 2)
+    return 8 * (S - 1 if 3 <= S <= 8 else S)
 
 
 def pairs_and_m(geom):
@@ -493,7 +494,7 @@ def run_native(args):
                                 "hfma2_bf16": binding.fp32_probe(local, packed=3)}
     # and the shared-memory read-modify-write rate of the forward's window pattern, the
     # forward's own roofline: algorithmic shared bytes = read + write of its window slots
-    # (S - 1 per pair for S >= 3, 2 for S = 2; 4 bytes each way)
+    # (S - 1 per pair for 3 <= S <= 8, else S; 4 bytes each way)
     smem_tbs = binding.smem_probe(local)
     out["smem_rmw_probe_tbs"] = smem_tbs
     if "fwd_cube" in per_kernel:

@@ -9,7 +9,7 @@
 //                       bank-conflict free and no atomics are needed.  The
 //                       window (the cube's distance range for that element)
 //                       holds the running sum of the slot weights, so a pair
-//                       writes S - 1 slots (its weights sum to zero; 3 <= S <= 12);
+//                       writes S - 1 slots (its weights sum to zero; 3 <= S <= 8);
 //                       the flush differences it into a per-cube partial trace and
 //                       fwd_reduce_kernel sums the partials in a fixed order.
 //                       Voxels go in pairs along a row, in packed FP32.
@@ -181,13 +181,14 @@ __device__ __forceinline__ void gauss_boundaries2(float2 beta1, float h, const G
 // ------------------------------------------------------------------------
 // forward
 // ------------------------------------------------------------------------
-// The forward window holds the running sum of the slot weights for 3 <= S <= 12 (one
+// The forward window holds the running sum of the slot weights for 3 <= S <= 8 (one
 // read-modify-write fewer per pair) and the weights themselves otherwise: at S = 2 the
-// running sum would cancel worst, and for wide pulses the running sums grow with S
-// relative to the trace, and so does their rounding (on 16^3 cubes of a dense volume:
-// 3.0e-6 relative L2 at S = 4, 6.8e-6 at S = 11, 8.5e-6 at S = 16, 1.2e-5 at S = 32,
-// against 0.9e-6 at S = 32 with the weights), for a saving of one write in S.
-__host__ __device__ constexpr bool fwd_running_sum(int S) { return S >= 3 && S <= 12; }
+// running sum would cancel worst, and for wider pulses the running sums (one-signed, so
+// they add up over a dense volume while the trace they difference to cancels) carry a
+// rounding error that grows with S: on 16^3 cubes of a dense volume 3.0e-6 relative L2
+// at S = 4, 6.8e-6 at S = 11, 7.0-8.0e-6 at S = 12, 8.5e-6 at S = 16 and 1.2e-5 at
+// S = 32 (the bound is 1e-5), against 0.7-0.9e-6 with the weights written directly.
+__host__ __device__ constexpr bool fwd_running_sum(int S) { return S >= 3 && S <= 8; }
 
 template <int C>
 __host__ __device__ constexpr int fwd_tile_bytes() { return C * C * C * 4; }
@@ -306,7 +307,7 @@ __device__ __forceinline__ bool fwd_tile(const CUtensorMap* p0map, const FwdPara
       const float Crow = fmaf(qy * Q.inv_hf, qy + R.m2uy, Cz);
       const float* prow = tile + (lz * C + ly) * C;
       // The pair's slot weights b_k - b_{k+1} (k = 0..S-1) sum to b_0 - b_S = 0, so for
-      // 3 <= S <= 12 the window holds their running sum, negated: slot k gets
+      // 3 <= S <= 8 the window holds their running sum, negated: slot k gets
       // b_{k+1} - b_0 for k = 0..S-2 and slot S-1 gets nothing.  That is S - 1
       // read-modify-writes instead of S through shared memory, which bounds this loop;
       // the flush takes the first difference (wider pulses write the weights).  Sphere: b_0 = a0^2, b_k = beta_k^2 inside, the last boundary
@@ -327,39 +328,51 @@ __device__ __forceinline__ bool fwd_tile(const CUtensorMap* p0map, const FwdPara
             float* sa = col + min(m.idx0, max_idx) * kWarp;
             float* sb = col + min(m.idx1, max_idx) * kWarp;
             const float2 s = mul2(pv, m.rs);
-            float2 c[S - 1];  // b_{k+1} - b_0
-            if constexpr (K == PASFM_KERNEL_GAUSS) {
+            if constexpr (!fwd_running_sum(S) && K == PASFM_KERNEL_GAUSS) {
+              // the slot weights themselves, b_k - b_{k+1} = E_{k+1} - E_k (E_0 = E_S = edge)
               float2 E[S];
               gauss_boundaries2<S>(m.beta1, Q.h, Q.gs, E);
+              float2 w[S];
+              w[0] = add2(E[1], f2(-Q.gs.e_clamp));
 #pragma unroll
-              for (int k = 0; k <= S - 2; ++k) c[k] = fma2(E[k + 1], f2(-1.f), f2(Q.gs.e_clamp));
+              for (int k = 1; k <= S - 2; ++k) w[k] = fma2(E[k], f2(-1.f), E[k + 1]);
+              w[S - 1] = fma2(E[S - 1], f2(-1.f), f2(Q.gs.e_clamp));
+#pragma unroll
+              for (int k = 0; k < S; ++k) sa[k * kWarp] = fmaf(s.x, w[k].x, sa[k * kWarp]);
+#pragma unroll
+              for (int k = 0; k < S; ++k) sb[k * kWarp] = fmaf(s.y, w[k].y, sb[k * kWarp]);
             } else {
-              float2 beta = m.beta1;
+              float2 c[S - 1];  // b_{k+1} - b_0
+              if constexpr (K == PASFM_KERNEL_GAUSS) {
+                float2 E[S];
+                gauss_boundaries2<S>(m.beta1, Q.h, Q.gs, E);
 #pragma unroll
-              for (int k = 0; k <= S - 2; ++k) {
-                if (k > 0) beta = add2(beta, f2(Q.h));
-                const float2 bc = (k == S - 2) ? min2(beta, Q.supf) : beta;
-                c[k] = fma2(bc, bc, f2(-Q.sup2));
+                for (int k = 0; k <= S - 2; ++k) c[k] = fma2(E[k + 1], f2(-1.f), f2(Q.gs.e_clamp));
+              } else {
+                float2 beta = m.beta1;
+#pragma unroll
+                for (int k = 0; k <= S - 2; ++k) {
+                  if (k > 0) beta = add2(beta, f2(Q.h));
+                  const float2 bc = (k == S - 2) ? min2(beta, Q.supf) : beta;
+                  c[k] = fma2(bc, bc, f2(-Q.sup2));
+                }
               }
-            }
-            if constexpr (fwd_running_sum(S)) {
+              if constexpr (fwd_running_sum(S)) {
 #pragma unroll
-              for (int k = 0; k <= S - 2; ++k) sa[k * kWarp] = fmaf(s.x, c[k].x, sa[k * kWarp]);
+                for (int k = 0; k <= S - 2; ++k) sa[k * kWarp] = fmaf(s.x, c[k].x, sa[k * kWarp]);
 #pragma unroll
-              for (int k = 0; k <= S - 2; ++k) sb[k * kWarp] = fmaf(s.y, c[k].y, sb[k * kWarp]);
-            } else {
-              // the slot weights themselves, b_k - b_{k+1}: -c_0, c_{k-1} - c_k, c_{S-2}
+                for (int k = 0; k <= S - 2; ++k) sb[k * kWarp] = fmaf(s.y, c[k].y, sb[k * kWarp]);
+              } else {
+                // the slot weights themselves, b_k - b_{k+1}: -c_0, c_{k-1} - c_k, c_{S-2}
+                float2 w[S];
+                w[0] = fma2(c[0], f2(-1.f), f2(0.f));
 #pragma unroll
-              for (int k = 0; k < S; ++k) {
-                const float2 w = k == 0 ? fma2(c[0], f2(-1.f), f2(0.f))
-                                        : (k == S - 1 ? c[S - 2] : fma2(c[k], f2(-1.f), c[k - 1]));
-                sa[k * kWarp] = fmaf(s.x, w.x, sa[k * kWarp]);
-              }
+                for (int k = 1; k <= S - 2; ++k) w[k] = fma2(c[k], f2(-1.f), c[k - 1]);
+                w[S - 1] = c[S - 2];
 #pragma unroll
-              for (int k = 0; k < S; ++k) {
-                const float2 w = k == 0 ? fma2(c[0], f2(-1.f), f2(0.f))
-                                        : (k == S - 1 ? c[S - 2] : fma2(c[k], f2(-1.f), c[k - 1]));
-                sb[k * kWarp] = fmaf(s.y, w.y, sb[k * kWarp]);
+                for (int k = 0; k < S; ++k) sa[k * kWarp] = fmaf(s.x, w[k].x, sa[k * kWarp]);
+#pragma unroll
+                for (int k = 0; k < S; ++k) sb[k * kWarp] = fmaf(s.y, w[k].y, sb[k * kWarp]);
               }
             }
           }

@@ -77,6 +77,20 @@ def coarse_window_case(seed=0):
     return geom, p0, elem, poses
 
 
+def aniso_case(seed=0):
+    """Anisotropic voxels (dz, dy, dx) = (0.12, 0.1, 0.08) mm on a 24 x 30 x 20 grid (x
+    fastest, nx % 4 == 0), 36 elements, 2 frames, Nt = 1024: every axis has its own
+    spacing, so a swapped axis or spacing anywhere shows."""
+    geom = synth.make_geom((20, 30, 24), (0.12, 0.1, 0.08), 36, 2, 1024)
+    rng = np.random.default_rng(1100 + seed)
+    p0 = synth.vessel_tree_phantom(geom, 6, rng)
+    p0 += rng.uniform(0, 0.02, size=p0.shape).astype(np.float32)
+    elem = synth.planar_array(6, 6, 0.5)
+    trng = np.random.default_rng(1200 + seed)
+    poses = synth.sweep_poses(2, 0.3, synth.top_face_z(geom) + 3.0, trng)
+    return geom, p0, elem, poses
+
+
 def coarse_case(seed=0):
     """Coarse grid (0.3 mm, a0 = 0.15 mm, 2 a0 / h = 8 exactly): 10 slots per pair
     and 8^3 cubes."""

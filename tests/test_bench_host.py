@@ -57,10 +57,12 @@ def test_clock_summary_parses_nvidia_smi_rows(tmp_path):
 
 
 def test_forward_shared_bytes_per_pair():
-    """24 bytes per pair on the full scan (S = 4: three running-sum slots), 88 for the
-    Gaussian at sigma = 0.05 mm (S = 12), 16 for a sphere narrower than a sample (S = 2)."""
+    """24 bytes per pair on the full scan (S = 4: three running-sum slots), 96 for the
+    Gaussian at sigma = 0.05 mm (S = 12: its twelve weights), 56 for the Gaussian at S = 8
+    (seven running-sum slots), 16 for a sphere narrower than a sample (S = 2)."""
     from paper_2604_09643_b300 import synth
     g = synth.make_geom((8, 8, 8), 0.1, 4, 1, 64)
     assert bench.fwd_smem_bytes_per_pair(g) == 24
-    assert bench.fwd_smem_bytes_per_pair(dict(g, kernel="gauss", sigma_mm=0.05)) == 88
+    assert bench.fwd_smem_bytes_per_pair(dict(g, kernel="gauss", sigma_mm=0.05)) == 96
+    assert bench.fwd_smem_bytes_per_pair(dict(g, kernel="gauss", sigma_mm=0.03)) == 56
     assert bench.fwd_smem_bytes_per_pair(dict(g, a0_mm=0.015)) == 16

@@ -21,7 +21,7 @@ import oracle
 from paper_2604_09643_b300 import binding, synth
 from tests.parity_cases import (REL_L2_POSE, REL_L2_SIG, coarse_case, gaussian, pose_residual, ragged_case,
                                 rel_l2, residual, sphere, tma_case, wide_window_case,
-                                coarse_window_case)
+                                coarse_window_case, aniso_case)
 
 pytestmark = pytest.mark.gpu
 
@@ -53,6 +53,8 @@ CASES = {
     "wide_window": wide_window_case,
     # the 8^3 cubes' window cap with the largest sphere slot count: W = 200, S = 16
     "coarse_window": coarse_window_case,
+    # anisotropic voxels (0.12, 0.1, 0.08 mm along z, y, x)
+    "aniso": aniso_case,
     # Gaussian kernel (Eq. 1): slot counts S = floor(8 sigma / h) + 2 of 19, 8, 8, 12 and 32 (the largest compiled)
     "gauss_single_frame": gaussian(single_frame_case, 0.08),
     "gauss_ragged": gaussian(ragged_case, 0.03),
@@ -60,6 +62,7 @@ CASES = {
     "gauss_tma": gaussian(tma_case, 0.05),
     "gauss_coarse_s32": gaussian(coarse_case, 0.141),
     "gauss_s32_tma": gaussian(tma_case, 0.141),  # the largest Gaussian on 16^3 cubes and the TMA paths
+    "gauss_aniso": gaussian(aniso_case, 0.05),
     # the smallest slot counts: a pulse narrower than a sample (S = 2) and S = 4
     "gauss_single_frame_s2": gaussian(single_frame_case, 0.004),
     "gauss_ragged_s4": gaussian(ragged_case, 0.01),
@@ -142,7 +145,7 @@ def test_pose_grad(ctx, case, masked):
     assert_status_ok(ctx)
     if name.endswith("ragged_cut") or name in ("sphere_ragged_s2", "sphere_coarse_s16", "sphere_s11_tma",
                                                "sphere_s16_tma",
-                                               "wide_window", "coarse_window"):
+                                               "wide_window", "coarse_window", "aniso"):
         gm = g if mask is None else g * mask[:, :, None]
         mid, half = oracle.element_gradient_bounds(geom, p0, gm, xw, np.arange(F * E), EPS_KINK)
         _band_check(gotG.reshape(-1, 3), got6, mid, half,
